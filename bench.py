@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark: space-time predictor element-updates/s on one GB300.
+
+Workload: the isolated-element population of the paper's performance proxy
+(random tetrahedra, random data, one predictor per element): 200,000 seeded
+tetrahedra, per-element Biot material, Q0 ~ N(0,1), degree N = 6.
+One step = one predictor of every element (solve + time integration),
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "predictor element-updates/s at N=6, FP64 vs mixed (≤1e-10 rel); served p50/p99"
+UNIT = "element-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degree", type=int, default=6)
+    ap.add_argument("--n-elem", type=int, default=200_000)
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(args):
+    return {"workload": f"isolated space-time predictor, {args.n_elem} random tetrahedra "
+                        f"(aspect <= 4, h 50-200 m), Biot material +-20%, Q0~N(0,1), N={args.degree}",
+            "n_elem_per_gpu": args.n_elem, "degree": args.degree, "solver": "block back-substitution (Algorithm 3)",
+            "l2": "inputs larger than L2 (Q0 and Qt streamed every step)"}
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def fp64_alu_peak():
+    """Peak binary64 FMA throughput of the GB300 CUDA cores [TFLOP/s].
+    Nominal 1.25 TFLOP/s at the 2070 MHz maximum clock (152 SMs, ~2 FMA
+    lanes per SM per clock); MEASURED_PEAKS.json carries no FP64 figure, so
+    the nominal rate is used."""
+    return 1.25
+
+
+# ------------------------------------------------------------------ cpu baseline
+def cpu_oracle_rate(args, budget_s, n_min=1):
+    """Time the oracle (dense equilibrated LU of Eq. stp-lineq, numpy/LAPACK
+    float64) on the host cores on the first elements of the same workload."""
+    from oracle import geometry, predictor
+    from paper_2108_10565_gb300 import inputs
+
+    k_max = 64
+    d = inputs.isolated_elements(k_max, args.degree)
+    t0 = time.perf_counter()
+    done = 0
+    while done < k_max and (done < n_min or time.perf_counter() - t0 < budget_s):
+        mat = inputs.material_dict(d["materials"][done])
+        dt = geometry.cfl_dt(d["vertices"][done], mat, args.degree)
+        As, Es = predictor.element_operators(d["vertices"][done], mat, dt)
+        predictor.predict_dense(args.degree, As, Es, d["Q0"][done])
+        done += 1
+    el = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+
+        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info()) if threadpool_info() else os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    return done / el, cores, done, el
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import geometry, predictor
+    from paper_2108_10565_gb300 import inputs
+
+    n_total = args.steps + args.warmup
+    d = inputs.isolated_elements(n_total, args.degree)
+    ops = []
+    for i in range(n_total):
+        mat = inputs.material_dict(d["materials"][i])
+        dt = geometry.cfl_dt(d["vertices"][i], mat, args.degree)
+        ops.append(predictor.element_operators(d["vertices"][i], mat, dt))
+    for i in range(args.warmup):
+        predictor.predict_dense(args.degree, *ops[i], d["Q0"][i])
+    t0 = time.perf_counter()
+    for i in range(args.warmup, n_total):
+        predictor.predict_dense(args.degree, *ops[i], d["Q0"][i])
+    el = time.perf_counter() - t0
+    rate = args.steps / el
+    try:
+        from threadpoolctl import threadpool_info
+
+        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info())
+    except Exception:
+        cores = os.cpu_count()
+    sample = f"1 element per step ({args.steps} timed steps) of the N={args.degree} workload"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _workload(args),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2108_10565_gb300 import _lib as L
+    from paper_2108_10565_gb300 import inputs
+
+    N, n = args.degree, args.n_elem
+    d = inputs.isolated_elements(n, N, seed=inputs.SEED_ISOLATED + rank)
+    dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
+    prec = L.PORO_FP64
+    ctx = L.poro_create(local, N, prec)
+    L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
+    B, T = d["Q0"].shape[2], N + 1
+    q0 = torch.from_numpy(d["Q0"]).to(f"cuda:{local}")
+    qt = torch.empty((n, 13, B, T), dtype=torch.float64, device=f"cuda:{local}")
+    io = torch.empty((n, 13, B), dtype=torch.float64, device=f"cuda:{local}")
+    stream = torch.cuda.Stream(device=local)
+    sh = stream.cuda_stream
+
+    def step():
+        L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK, sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(args.steps):
+            step()
+            evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    ms = evs[0].elapsed_time(evs[-1]) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms * 1e-3)
+    flops = L.poro_flop_count(ctx, 0)[0]
+    achieved = flops * n / (statistics.mean(per) * 1e-3) / 1e12
+    peak = fp64_alu_peak()
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hq = torch.from_numpy(d["Q0"]).pin_memory()
+        hi = torch.empty((n, 13, B), dtype=torch.float64).pin_memory()
+        hq_np, hi_np = hq.numpy(), hi.numpy()
+        L.poro_set_dofs(ctx, hq_np)
+        for _ in range(max(1, args.warmup)):
+            L.poro_set_dofs(ctx, hq_np)
+            L.poro_predict(ctx)
+            L.poro_get_integrated(ctx, 0, n, hi_np)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            L.poro_set_dofs(ctx, hq_np)
+            L.poro_predict(ctx)
+            L.poro_get_integrated(ctx, 0, n, hi_np)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 8),
+               "d2h_bytes_per_step": int(hi.numel() * 8)}
+    L.poro_destroy(ctx)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, cores, k, el = cpu_oracle_rate(args, args.cpu_budget_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {k} elements of the N={args.degree} workload, dense equilibrated LU "
+                         f"(numpy/LAPACK float64), {el:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload(args),
+        "precision": args.precision,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "stp_fp64_kernel<6>", "flops_per_element": flops,
+                     "peak_source": "nominal GB300 binary64 FMA rate (MEASURED_PEAKS.json has none)"},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

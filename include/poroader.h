@@ -1,0 +1,179 @@
+/*
+ * poroader.h -- C ABI of libporoader: the element-local space-time predictor
+ * of ADER-DG for Biot's poroelastic equations on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: Wolf, Galis, Uphoff, Gabriel, Moczo, Gregor, Bader, "An Efficient
+ * ADER-DG Local Time Stepping Scheme for 3D HPC Simulation of Seismic Waves
+ * in Poroelastic Media" (arXiv 2108.10565).
+ *
+ * Conventions (all calls):
+ *  - SI units.  Quantity order q = (s_xx, s_yy, s_zz, s_xy, s_yz, s_xz,
+ *    u, v, w, p, u_f, v_f, w_f) (Section "Governing equations").
+ *  - Degree N in 1..6; B = (N+1)(N+2)(N+3)/6 spatial modes, T = N+1 time
+ *    modes.  Host arrays are row-major: DOFs [elem][13][B], predictor
+ *    [elem][13][B][T], time-integrated DOFs [elem][13][B].
+ *  - The spatial basis is the unnormalised Dubiner basis ordered by total
+ *    degree g, then k, then j (phi_ijk, i = g - j - k); the time basis is the
+ *    shifted Legendre family chi_s(tau) = P_s(2 tau - 1) on [0, 1].
+ *  - Every call returns a poro_status; 0 is success, negative is an error.
+ *    No call aborts or throws across the ABI.  poro_last_error() gives a
+ *    text for the last failing call on that context.
+ *  - Host pointers passed in are read during the call only (inputs are
+ *    copied); the caller keeps ownership.  Output host buffers are written
+ *    by the call and owned by the caller.  Device pointers passed to *_dev
+ *    calls are neither copied nor freed by the library; they must stay valid
+ *    until the work queued on the given stream has finished.
+ *  - Work is queued asynchronously on a CUDA stream; device-side errors
+ *    surface at the next synchronising call (poro_sync, poro_get_*).
+ */
+#ifndef PORO_ADER_H
+#define PORO_ADER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t poro_status;
+enum {
+    PORO_OK = 0,
+    PORO_EINVAL = -1,       /* bad argument: NULL, size, degenerate element, unphysical material */
+    PORO_ENOMEM = -2,       /* device or host allocation failed */
+    PORO_ECUDA = -3,        /* a CUDA runtime call or kernel failed */
+    PORO_ETIMEOUT = -4,     /* poro_sync gave up waiting; the context stays usable */
+    PORO_ESTATE = -5,       /* calls in the wrong order (e.g. predict before set_isolated) */
+    PORO_ENUMERIC = -6,     /* non-finite value in input */
+    PORO_EUNSUPPORTED = -7  /* degree outside 1..6, precision or solver not built */
+};
+
+typedef struct poro_ctx poro_ctx;
+
+/* The 10 Biot parameters of Table poroelastic_parameters:
+ * solid bulk modulus K_S [Pa], solid density rho_S [kg/m^3], matrix Lame
+ * parameters lambda_M, mu_M [Pa], permeability kappa [m^2], porosity phi,
+ * tortuosity T, fluid bulk modulus K_F [Pa], fluid density rho_F [kg/m^3],
+ * fluid viscosity nu [Pa s].  Memory layout: 10 consecutive doubles. */
+typedef struct {
+    double K_S, rho_S, lambda_M, mu_M, kappa, phi, tortuosity, K_F, rho_F, nu;
+} poro_material;
+
+typedef enum {
+    PORO_FP64 = 0,          /* every step in IEEE binary64 */
+    PORO_FP32_REFINE = 1,   /* binary32 back-substitution + refinement against an
+                               FP64-accurate residual of the predictor system */
+    PORO_BF16X3_REFINE = 2  /* reserved: tensor-core split products (not built) */
+} poro_precision;
+
+typedef enum {
+    PORO_SOLVE_BLOCK = 0,   /* Algorithm 3: degree-block back-substitution */
+    PORO_SOLVE_LU = 1       /* dense LU of the whole predictor system (comparator) */
+} poro_solver;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` for degree `degree_N` (1..6) and
+ * arithmetic `precision`.  Allocates a CUDA stream and the device-resident
+ * reference matrices (Khat^alpha = M^{-1} K^alpha, Section "Block-wise
+ * back-substitution"; Z = S^{-1}(W - K^tau)).  *out receives the handle, or
+ * NULL on error.  Errors: PORO_EINVAL (out NULL), PORO_EUNSUPPORTED,
+ * PORO_ECUDA, PORO_ENOMEM. */
+poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out);
+
+/* Release every device and host resource of the context (waits for queued
+ * work first).  NULL is accepted and ignored. */
+poro_status poro_destroy(poro_ctx* ctx);
+
+/* Text of the last error on `ctx`; owned by the context, valid until the
+ * next call on it.  For ctx == NULL: the last error of a call that had no
+ * context (e.g. a failed poro_create), thread-local. */
+const char* poro_last_error(const poro_ctx* ctx);
+
+/* Degree and precision the context was created with; n_elem after
+ * poro_set_isolated (0 before). */
+poro_status poro_get_info(const poro_ctx* ctx, int32_t* degree_N, int32_t* precision, int64_t* n_elem);
+
+/* ------------------------------------------------------ host-only queries */
+/* These touch no GPU; they expose the library's own set-up arithmetic. */
+
+/* Reference matrices of degree N (Section "Space-Time predictor"):
+ * mass_diag[B] = M_kk (M is diagonal), khat[3][B][B] = Khat^alpha_kl for
+ * alpha = xi, eta, zeta (row-major).  Either pointer may be NULL. */
+poro_status poro_reference_matrices(int degree_N, double* mass_diag, double* khat);
+
+/* Jacobians of Eq. poroelastic-wave for one material: abc[3][13][13] holds
+ * A, B, C; e[13][13] holds E.  Errors: PORO_EINVAL for an unphysical
+ * material (phi outside (0,1), kappa <= 0 with nu > 0, M <= 0,
+ * rho m - rho_F^2 <= 0, non-positive moduli or densities). */
+poro_status poro_material_jacobians(const poro_material* mat, double* abc, double* e);
+
+/* Largest characteristic speed of the material (fast P wave) [m/s]. */
+poro_status poro_max_wave_speed(const poro_material* mat, double* speed);
+
+/* CFL step of each element (Section "Temporal discretisation with ADER"):
+ * dt[i] = cfl_c / (2N + 1) * d_i / v_i, d_i the insphere diameter of
+ * tetrahedron i (vert[n][4][3]) and v_i the fast P speed of mat[i].
+ * cfl_c = 0.5 in the paper.  Errors: PORO_EINVAL for a degenerate element. */
+poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_material* mat,
+                        double cfl_c, double* dt);
+
+/* ------------------------------------------------------ isolated elements */
+
+/* Load n_elem unconnected tetrahedra (the population of the paper's
+ * performance proxy, Section "Roofline model"): vertices vert[n][4][3],
+ * one material per element, one time step dt[n] per element.  Computes on
+ * the host, per element, the reference Jacobians A^{j*} = dt A^j (Section
+ * "Space-Time predictor"), E* = dt E, and (Z - E*_pp I)^{-1}, and uploads
+ * them.  Replaces a previous population.  Errors: PORO_EINVAL (degenerate
+ * tetrahedron, unphysical material, dt <= 0), PORO_ENOMEM. */
+poro_status poro_set_isolated(poro_ctx* ctx, int64_t n_elem, const double* vert,
+                              const poro_material* mat, const double* dt);
+
+/* Copy DOFs Q[n_elem][13][B] (host) into the context.  Errors: PORO_ESTATE
+ * before poro_set_isolated. */
+poro_status poro_set_dofs(poro_ctx* ctx, const double* Q);
+
+/* Space-time predictor of every element from the context's DOFs (Eq.
+ * stp-lineq), solved by `solver`, followed by the time integration
+ * I = dt * int_0^1 Qt dtau (= dt * Qt[..][0] for the shifted Legendre basis).
+ * `cluster` must be -1 (all elements) for an isolated population.
+ * Asynchronous on the context stream.  Errors: PORO_ESTATE,
+ * PORO_EUNSUPPORTED (solver not available for this precision), PORO_ECUDA. */
+poro_status poro_predict(poro_ctx* ctx, int32_t cluster, poro_solver solver);
+
+/* Copy elements [first, first+count) of the last predictor to the host:
+ * Qt_out[count][13][B][T].  Synchronises the context stream. */
+poro_status poro_get_predictor(poro_ctx* ctx, int64_t first, int64_t count, double* Qt_out);
+
+/* Copy the time-integrated DOFs I_out[count][13][B] of elements
+ * [first, first+count).  Synchronises the context stream. */
+poro_status poro_get_integrated(poro_ctx* ctx, int64_t first, int64_t count, double* I_out);
+
+/* Wait for the context stream, polling, at most timeout_ms milliseconds
+ * (< 0: no limit).  PORO_ETIMEOUT if the work is still running; the context
+ * remains valid and a later poro_sync may succeed. */
+poro_status poro_sync(poro_ctx* ctx, int32_t timeout_ms);
+
+/* Device-pointer form of poro_predict for callers that keep DOFs resident:
+ * Q0_dev[n_elem][13][B] (read), Qt_dev[n_elem][13][B][T] (written; may be
+ * NULL to skip storing the full predictor), I_dev[n_elem][13][B] (written;
+ * may be NULL).  All three are device pointers aligned to 16 bytes.
+ * `stream` is a cudaStream_t (NULL: the context stream).  The element range
+ * is [first, first + count) of the loaded population; row 0 of each buffer
+ * is element `first`.  Errors: PORO_EINVAL, PORO_ESTATE, PORO_ECUDA. */
+poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
+                             double* Qt_dev, double* I_dev, poro_solver solver, void* stream);
+
+/* Floating-point operations one predictor of this context performs, counted
+ * from the structural non-zeros the kernels touch (Khat blocks, the 54-entry
+ * star pattern, the (N+1)^2 time solves): used for rooflines.  flops_out[0]
+ * = FP64 operations (PORO_FP64), flops_out[1] = low-precision operations
+ * (refinement modes), flops_out[2] = residual operations (refinement modes,
+ * per sweep). */
+poro_status poro_flop_count(const poro_ctx* ctx, int32_t refine_sweeps, double* flops_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PORO_ADER_H */

@@ -1,0 +1,186 @@
+"""ctypes binding of libporoader (include/poroader.h).
+
+Argument marshalling only: every function has the C name and forwards to the
+shared library.  The library is built in-tree (paper_2108_10565_gb300/build.py);
+if it is missing, importing the binding raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libporoader.so")
+
+PORO_OK, PORO_EINVAL, PORO_ENOMEM, PORO_ECUDA, PORO_ETIMEOUT, PORO_ESTATE, PORO_ENUMERIC, PORO_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PORO_FP64, PORO_FP32_REFINE, PORO_BF16X3_REFINE = 0, 1, 2
+PORO_SOLVE_BLOCK, PORO_SOLVE_LU = 0, 1
+
+_c = ctypes
+_i32, _i64, _dbl, _vp = _c.c_int32, _c.c_int64, _c.c_double, _c.c_void_p
+_pd = _c.POINTER(_c.c_double)
+
+# (name, restype, argtypes) for every symbol declared in include/poroader.h
+SIGNATURES = [
+    ("poro_create", _i32, [_c.c_int, _c.c_int, _c.c_int, _c.POINTER(_vp)]),
+    ("poro_destroy", _i32, [_vp]),
+    ("poro_last_error", _c.c_char_p, [_vp]),
+    ("poro_get_info", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32), _c.POINTER(_i64)]),
+    ("poro_reference_matrices", _i32, [_c.c_int, _vp, _vp]),
+    ("poro_material_jacobians", _i32, [_vp, _vp, _vp]),
+    ("poro_max_wave_speed", _i32, [_vp, _pd]),
+    ("poro_cfl_dt", _i32, [_c.c_int, _i64, _vp, _vp, _dbl, _vp]),
+    ("poro_set_isolated", _i32, [_vp, _i64, _vp, _vp, _vp]),
+    ("poro_set_dofs", _i32, [_vp, _vp]),
+    ("poro_predict", _i32, [_vp, _i32, _c.c_int]),
+    ("poro_get_predictor", _i32, [_vp, _i64, _i64, _vp]),
+    ("poro_get_integrated", _i32, [_vp, _i64, _i64, _vp]),
+    ("poro_sync", _i32, [_vp, _i32]),
+    ("poro_predict_dev", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _c.c_int, _vp]),
+    ("poro_flop_count", _i32, [_vp, _i32, _pd]),
+]
+
+
+class PoroError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"poroader error {status}: {msg}")
+        self.status = status
+
+
+def load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libporoader.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def _check(status, ctx=None):
+    if status != PORO_OK:
+        raise PoroError(status, lib().poro_last_error(ctx).decode())
+    return status
+
+
+def _ptr(a):
+    """Host pointer of a C-contiguous numpy array (or None)."""
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "arrays passed to libporoader must be C-contiguous"
+    return a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------ same-name wrappers
+def poro_create(device, degree_N, precision=PORO_FP64):
+    h = _vp()
+    _check(lib().poro_create(device, degree_N, precision, ctypes.byref(h)))
+    return h.value
+
+
+def poro_destroy(ctx):
+    return _check(lib().poro_destroy(ctx))
+
+
+def poro_last_error(ctx=None):
+    return lib().poro_last_error(ctx).decode()
+
+
+def poro_get_info(ctx):
+    n, p, e = _i32(), _i32(), _i64()
+    _check(lib().poro_get_info(ctx, ctypes.byref(n), ctypes.byref(p), ctypes.byref(e)), ctx)
+    return n.value, p.value, e.value
+
+
+def poro_reference_matrices(N):
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    m = np.zeros(B)
+    k = np.zeros((3, B, B))
+    _check(lib().poro_reference_matrices(N, _ptr(m), _ptr(k)))
+    return m, k
+
+
+def poro_material_jacobians(mat10):
+    m = _f64(mat10)
+    abc = np.zeros((3, 13, 13))
+    e = np.zeros((13, 13))
+    _check(lib().poro_material_jacobians(_ptr(m), _ptr(abc), _ptr(e)))
+    return abc, e
+
+
+def poro_max_wave_speed(mat10):
+    m = _f64(mat10)
+    v = _dbl()
+    _check(lib().poro_max_wave_speed(_ptr(m), ctypes.byref(v)))
+    return v.value
+
+
+def poro_cfl_dt(N, vert, mat, cfl_c=0.5):
+    v, m = _f64(vert), _f64(mat)
+    n = v.shape[0]
+    dt = np.zeros(n)
+    _check(lib().poro_cfl_dt(N, n, _ptr(v), _ptr(m), cfl_c, _ptr(dt)))
+    return dt
+
+
+def poro_set_isolated(ctx, vert, mat, dt):
+    v, m, d = _f64(vert), _f64(mat), _f64(dt)
+    return _check(lib().poro_set_isolated(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
+
+
+def poro_set_dofs(ctx, Q):
+    q = _f64(Q)
+    return _check(lib().poro_set_dofs(ctx, _ptr(q)), ctx)
+
+
+def poro_predict(ctx, cluster=-1, solver=PORO_SOLVE_BLOCK):
+    return _check(lib().poro_predict(ctx, cluster, solver), ctx)
+
+
+def poro_get_predictor(ctx, first, count, out=None):
+    N, _, _ = poro_get_info(ctx)
+    B, T = (N + 1) * (N + 2) * (N + 3) // 6, N + 1
+    if out is None:
+        out = np.empty((count, 13, B, T))
+    _check(lib().poro_get_predictor(ctx, first, count, _ptr(out)), ctx)
+    return out
+
+
+def poro_get_integrated(ctx, first, count, out=None):
+    N, _, _ = poro_get_info(ctx)
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    if out is None:
+        out = np.empty((count, 13, B))
+    _check(lib().poro_get_integrated(ctx, first, count, _ptr(out)), ctx)
+    return out
+
+
+def poro_sync(ctx, timeout_ms=-1):
+    return _check(lib().poro_sync(ctx, timeout_ms), ctx)
+
+
+def poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver=PORO_SOLVE_BLOCK, stream=None):
+    """Device-pointer form; pointers are integers (e.g. torch.Tensor.data_ptr())."""
+    return _check(lib().poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver, stream), ctx)
+
+
+def poro_flop_count(ctx, refine_sweeps=0):
+    f = (ctypes.c_double * 3)()
+    _check(lib().poro_flop_count(ctx, refine_sweeps, f), ctx)
+    return list(f)

@@ -1,0 +1,115 @@
+// Internal declarations shared by the host set-up, the C ABI and the kernels
+// of libporoader.  Not part of the public interface (include/poroader.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/poroader.h"
+
+namespace poro {
+
+constexpr int NQ = 13;
+constexpr int MAX_N = 6;
+// quantity indices, paper order (Section "Governing equations")
+enum { SXX, SYY, SZZ, SXY, SYZ, SXZ, QU, QV, QW, QP, QUF, QVF, QWF };
+
+constexpr int n_modes(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+constexpr int block_size(int g) { return (g + 1) * (g + 2) / 2; }
+constexpr int block_offset(int g) { return g * (g + 1) * (g + 2) / 6; }
+
+// Union sparsity pattern of A*, B*, C* (54 entries): for every row p the
+// columns q with a structurally non-zero Jacobian entry.  Rows are stored
+// contiguously; star_row_ptr(p) .. star_row_ptr(p+1) index star_col().
+#ifdef __CUDACC__
+#define PORO_HD __host__ __device__
+#else
+#define PORO_HD
+#endif
+constexpr int STAR_NNZ = 54;
+PORO_HD constexpr int star_row_ptr(int p) {
+    constexpr int t[NQ + 1] = {0, 6, 12, 18, 20, 22, 24, 28, 32, 36, 42, 46, 50, 54};
+    return t[p];
+}
+PORO_HD constexpr int star_row(int n) {
+    return n < 18 ? n / 6 : n < 24 ? 3 + (n - 18) / 2 : n < 36 ? 6 + (n - 24) / 4 : n < 42 ? 9 : 10 + (n - 42) / 4;
+}
+PORO_HD constexpr int star_col(int n) {
+    constexpr int t[STAR_NNZ] = {
+        QU, QV, QW, QUF, QVF, QWF,   // s_xx
+        QU, QV, QW, QUF, QVF, QWF,   // s_yy
+        QU, QV, QW, QUF, QVF, QWF,   // s_zz
+        QU, QV,                      // s_xy
+        QV, QW,                      // s_yz
+        QU, QW,                      // s_xz
+        SXX, SXY, SXZ, QP,           // u
+        SYY, SXY, SYZ, QP,           // v
+        SZZ, SXZ, SYZ, QP,           // w
+        QU, QV, QW, QUF, QVF, QWF,   // p
+        SXX, SXY, SXZ, QP,           // u_f
+        SYY, SXY, SYZ, QP,           // v_f
+        SZZ, SXZ, SYZ, QP};          // w_f
+    return t[n];
+}
+
+// Per-element constants, in doubles, in this order:
+//   star[3][54]       A^{j*} = dt A^j on the union pattern
+//   zinv_uf[T][T]     (Z - e I)^{-1}, e = E*_{uf,uf} (row-major, [u][s])
+//   e, g, dt, pad     E*_{uf,uf}, E*_{u,uf}, time step
+inline int elem_const_stride(int N) {
+    int T = N + 1;
+    int n = 3 * STAR_NNZ + T * T + 4;
+    return (n + 1) & ~1;  // keep 16-byte alignment of every element's block
+}
+inline int ec_zinv(int) { return 3 * STAR_NNZ; }
+inline int ec_scalars(int N) { return 3 * STAR_NNZ + (N + 1) * (N + 1); }
+
+// Khat^j restricted to the columns of one degree block g, in CSR over the
+// rows l < o_g (the only rows Lemma 1 leaves non-zero); entries
+// (m_local, value) with m_local < d_g.
+struct KhatBlockCSR {
+    std::vector<int32_t> row_ptr;    // [o_g + 1]
+    std::vector<int32_t> col;        // m_local
+    std::vector<double> val;
+};
+
+struct ReferenceData {
+    int N = 0, B = 0, T = 0;
+    std::vector<double> mass_diag;     // [B]
+    std::vector<double> khat;          // [3][B][B]
+    std::vector<double> zinv;          // [T][T]  Z^{-1}
+    std::vector<double> z;             // [T][T]  Z = S^{-1}(W - K^tau)
+    std::vector<double> sinv_w;        // [T]     S^{-1} w
+    std::vector<KhatBlockCSR> blocks;  // [(N+1)*3], index g*3 + j (block 0 empty)
+    int64_t khat_block_nnz = 0;        // structural non-zeros of all Khat blocks
+};
+
+// ----- host set-up (setup.cpp) -----
+bool reference_data(int N, ReferenceData& out, std::string& err);
+bool material_jacobians(const poro_material& m, double abc[3][NQ][NQ], double e[NQ][NQ],
+                        std::string& err);
+bool max_wave_speed(const poro_material& m, double& v, std::string& err);
+bool tet_geometry(const double* v12, double jinv[3][3], double& volume, double& insphere_d,
+                  std::string& err);
+bool invert_small(int n, const double* a, double* ainv);
+// fills one element's constants block (elem_const_stride(N) doubles)
+bool element_constants(const ReferenceData& ref, const double* v12, const poro_material& mat,
+                       double dt, double* out, std::string& err);
+
+// ----- device side (kernels) -----
+struct DeviceReference {
+    int N = 0;
+    double* khat_val = nullptr;   // concatenated CSR values of all (g, j) blocks
+    int32_t* khat_col = nullptr;  // concatenated CSR columns (m_local)
+    int32_t* khat_row = nullptr;  // concatenated row pointers, absolute into val/col
+    int32_t row_base[MAX_N + 1][3] = {};  // start of block (g, j)'s row pointers in khat_row
+    double* zinv = nullptr;       // [T][T]
+};
+
+// Launch the FP64 Algorithm-3 predictor for `count` elements.
+// q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
+int launch_stp_fp64(const DeviceReference& ref, int64_t count, const double* q0,
+                    const double* econst, double* qt, double* iout, void* stream);
+
+}  // namespace poro

@@ -1,0 +1,89 @@
+"""CPU-side checks of libporoader: the library builds and loads, exports every
+symbol include/poroader.h declares, and its host set-up (its own quadrature
+and derivation) agrees with the oracle.  No GPU compute here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import basis, geometry, material
+from paper_2108_10565_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2108_10565_gb300 import _lib
+
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2108_10565_gb300 import build
+
+        build.build()
+    return _lib
+
+
+def _declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(poro_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = L.load()
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    bound = {n for n, _, _ in L.SIGNATURES}
+    assert declared == bound, f"binding and header differ: {declared ^ bound}"
+
+
+@pytest.mark.parametrize("N", range(1, 7))
+def test_reference_matrices_match_oracle(L, N):
+    m, k = L.poro_reference_matrices(N)
+    mo = np.diag(basis.mass_matrix(N))
+    ko = np.stack(basis.khat_matrices(N))
+    np.testing.assert_allclose(m, mo, rtol=1e-14)
+    assert np.abs(k - ko).max() <= 1e-14 * np.abs(ko).max()
+    np.testing.assert_array_equal(k != 0, ko != 0)  # identical structural zeros
+
+
+def test_jacobians_and_speed_match_oracle(L):
+    rng = np.random.default_rng(3)
+    for row in inputs.perturbed_materials(rng, 5):
+        abc, e = L.poro_material_jacobians(row)
+        md = inputs.material_dict(row)
+        A = np.stack(material.jacobians(md))
+        E = material.source_matrix(md)
+        assert np.abs(abc - A).max() <= 1e-15 * np.abs(A).max()
+        assert np.abs(e - E).max() <= 1e-14 * np.abs(E).max()
+        assert L.poro_max_wave_speed(row) == pytest.approx(geometry.max_wave_speed(md), rel=1e-13)
+
+
+def test_cfl_matches_oracle(L):
+    d = inputs.isolated_elements(20, 4, seed=9)
+    dt = L.poro_cfl_dt(4, d["vertices"], d["materials"])
+    ref = [geometry.cfl_dt(d["vertices"][i], inputs.material_dict(d["materials"][i]), 4) for i in range(20)]
+    np.testing.assert_allclose(dt, ref, rtol=1e-13)
+
+
+def test_invalid_inputs_rejected(L):
+    bad = inputs.REFERENCE_MATERIAL.copy()
+    bad[5] = 1.5  # porosity
+    with pytest.raises(L.PoroError) as ex:
+        L.poro_material_jacobians(bad)
+    assert ex.value.status == L.PORO_EINVAL
+    flat = np.zeros((1, 4, 3))
+    with pytest.raises(L.PoroError) as ex:
+        L.poro_cfl_dt(3, flat, inputs.REFERENCE_MATERIAL[None, :])
+    assert ex.value.status == L.PORO_EINVAL
+    with pytest.raises(L.PoroError) as ex:
+        L.poro_reference_matrices(7)
+    assert ex.value.status == L.PORO_EUNSUPPORTED
