@@ -35,7 +35,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=6)
     ap.add_argument("--n-elem", type=int, default=200_000)
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--refine", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -95,15 +96,6 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
-
-
-# ------------------------------------------------------------------ peaks
-def fp64_alu_peak():
-    """Peak binary64 FMA throughput of the GB300 CUDA cores [TFLOP/s].
-    Nominal 1.25 TFLOP/s at the 2070 MHz maximum clock (152 SMs, ~2 FMA
-    lanes per SM per clock); MEASURED_PEAKS.json carries no FP64 figure, so
-    the nominal rate is used."""
-    return 1.25
 
 
 # ------------------------------------------------------------------ cpu baseline
@@ -172,6 +164,22 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+# FP32-pipe instructions per double-word multiply-add of the refinement
+# residual (exact product by FMA, TwoSum, low-word accumulation).
+DW_OPS_PER_MAC = 11.5
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """binary32 FMA peak: 152 SMs x 128 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz):
+    """binary64 FMA peak: nominal 1.25 TFLOP/s at 2070 MHz (152 SMs, 2 FMA
+    lanes per SM per clock), scaled to the sampled clock."""
+    return 1.25 * sm_mhz / 2070.0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -186,55 +194,98 @@ def run_ours(args):
     from paper_2108_10565_gb300 import inputs
 
     N, n = args.degree, args.n_elem
+    dev = f"cuda:{local}"
     d = inputs.isolated_elements(n, N, seed=inputs.SEED_ISOLATED + rank)
     dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
-    prec = L.PORO_FP64
-    ctx = L.poro_create(local, N, prec)
-    L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
     B, T = d["Q0"].shape[2], N + 1
-    q0 = torch.from_numpy(d["Q0"]).to(f"cuda:{local}")
-    qt = torch.empty((n, 13, B, T), dtype=torch.float64, device=f"cuda:{local}")
-    io = torch.empty((n, 13, B), dtype=torch.float64, device=f"cuda:{local}")
+    q0 = torch.from_numpy(d["Q0"]).to(dev)
     stream = torch.cuda.Stream(device=local)
     sh = stream.cuda_stream
+    forms = {"fp64": (L.PORO_FP64, 0), "mixed": (L.PORO_FP32_REFINE, args.refine)}
+    order = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res, qts = {}, {}
+    for name in order:
+        prec, sweeps = forms[name]
+        ctx = L.poro_create(local, N, prec)
+        if prec == L.PORO_FP32_REFINE:
+            L.poro_set_refinement(ctx, sweeps)
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
+        qt = torch.empty((n, 13, B, T), dtype=torch.float64, device=dev)
+        io = torch.empty((n, 13, B), dtype=torch.float64, device=dev)
 
-    def step():
-        L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK, sh)
+        def step():
+            L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK, sh)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    time.sleep(0.3)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    with torch.cuda.stream(stream):
-        evs[0].record(stream)
-        for k in range(args.steps):
+        for _ in range(args.warmup):
             step()
-            evs[k + 1].record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    ms = evs[0].elapsed_time(evs[-1]) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world / (ms * 1e-3)
-    flops = L.poro_flop_count(ctx, 0)[0]
-    achieved = flops * n / (statistics.mean(per) * 1e-3) / 1e12
-    peak = fp64_alu_peak()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        time.sleep(0.3)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for k in range(args.steps):
+                step()
+                evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+        ms = evs[0].elapsed_time(evs[-1]) / args.steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        f = L.poro_flop_count(ctx, sweeps)
+        res[name] = dict(ctx=ctx, ms=ms, per=per, clocks=clocks, flops=f, sweeps=sweeps, prec=prec)
+        qts[name] = qt
+    # accuracy of the mixed form against the FP64 form on every element
+    err = None
+    if "fp64" in qts and "mixed" in qts:
+        a, b = qts["mixed"], qts["fp64"]
+        e = (torch.linalg.vector_norm((a - b).reshape(n, -1), dim=1)
+             / torch.linalg.vector_norm(b.reshape(n, -1), dim=1)).double().cpu().numpy()
+        err = {"vs": "fp64 kernel (pinned to the oracle at 1e-12)", "median": float(np.median(e)),
+               "p99": float(np.quantile(e, 0.99)), "max": float(e.max())}
+    del qts
 
-    # end to end through the C ABI with host buffers (pinned)
+    def roofline(name):
+        r = res[name]
+        mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
+        t = statistics.mean(r["per"]) * 1e-3
+        if r["prec"] == L.PORO_FP64:
+            ach = r["flops"][0] * n / t / 1e12
+            peak = fp64_alu_peak_tflops(mhz)
+            return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": f"stp_fp64_kernel<{N}>", "flops_per_element": r["flops"][0],
+                    "peak_source": "binary64 FMA pipe: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled clock"}
+        f_lp, f_res = r["flops"][1], r["flops"][2]
+        ach = (f_lp + f_res) * n / t / 1e12
+        # fastest this arithmetic runs on the binary32 pipe: low-precision FMAs
+        # 1 instruction per 2 flops, residual multiply-adds DW_OPS_PER_MAC
+        # instructions per 2 flops, 152 x 128 instructions per clock
+        t_min = (f_lp / 2 + DW_OPS_PER_MAC * f_res / 2) * n / (152 * 128 * mhz * 1e6)
+        peak = (f_lp + f_res) * n / t_min / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}>",
+                "flops_per_element": {"binary32_sweeps": f_lp, "residual_double_word": f_res},
+                "peak_source": f"binary32 pipe issue rate (152 SM x 128 lanes x {mhz:.0f} MHz) for this mix: "
+                               f"1 instr per FMA, {DW_OPS_PER_MAC} instr per double-word MAC; "
+                               f"binary32 FMA peak {fp32_alu_peak_tflops(mhz):.1f} TFLOP/s"}
+
+    head = "mixed" if ("mixed" in res and (err is None or err["max"] <= 1e-10)) else "fp64"
+    hr = res[head]
+    value = n * world / (hr["ms"] * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), headline form
     e2e = None
     if not args.no_e2e:
+        ctx = hr["ctx"]
         hq = torch.from_numpy(d["Q0"]).pin_memory()
         hi = torch.empty((n, 13, B), dtype=torch.float64).pin_memory()
         hq_np, hi_np = hq.numpy(), hi.numpy()
-        L.poro_set_dofs(ctx, hq_np)
         for _ in range(max(1, args.warmup)):
             L.poro_set_dofs(ctx, hq_np)
             L.poro_predict(ctx)
@@ -248,12 +299,13 @@ def run_ours(args):
             L.poro_get_integrated(ctx, 0, n, hi_np)
         e2e_s = (time.perf_counter() - t0) / args.steps
         if world > 1:
-            t = torch.tensor([e2e_s], device=f"cuda:{local}")
+            t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 8),
-               "d2h_bytes_per_step": int(hi.numel() * 8)}
-    L.poro_destroy(ctx)
+               "d2h_bytes_per_step": int(hi.numel() * 8), "form": head}
+    for r in res.values():
+        L.poro_destroy(r["ctx"])
 
     if rank != 0:
         if world > 1:
@@ -266,16 +318,19 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {k} elements of the N={args.degree} workload, dense equilibrated LU "
                          f"(numpy/LAPACK float64), {el:.1f} s"}
+    forms_out = {}
+    for name, r in res.items():
+        forms_out[name] = {"value": n * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
+                           "refine_sweeps": r["sweeps"] if name == "mixed" else None,
+                           "roofline": roofline(name), "clocks": r["clocks"]}
+    cfg = _workload(args)
+    cfg["form"] = head
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _workload(args),
-        "precision": args.precision,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "stp_fp64_kernel<6>", "flops_per_element": flops,
-                     "peak_source": "nominal GB300 binary64 FMA rate (MEASURED_PEAKS.json has none)"},
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": args.steps,
+        "warmup": args.warmup, "ms_per_step": hr["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+        "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": err,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
     }
     print(json.dumps(out))
     if world > 1:

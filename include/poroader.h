@@ -90,6 +90,13 @@ poro_status poro_destroy(poro_ctx* ctx);
  * context (e.g. a failed poro_create), thread-local. */
 const char* poro_last_error(const poro_ctx* ctx);
 
+/* Number of refinement sweeps of a PORO_FP32_REFINE context (0, 1 or 2;
+ * default 1): each sweep forms the residual of the predictor system in
+ * double-binary32 arithmetic (error-free products and sums, ~2^-48 relative)
+ * and solves for the correction with the binary32 back-substitution.
+ * Errors: PORO_EUNSUPPORTED for a PORO_FP64 context, PORO_EINVAL. */
+poro_status poro_set_refinement(poro_ctx* ctx, int32_t sweeps);
+
 /* Degree and precision the context was created with; n_elem after
  * poro_set_isolated (0 before). */
 poro_status poro_get_info(const poro_ctx* ctx, int32_t* degree_N, int32_t* precision, int64_t* n_elem);

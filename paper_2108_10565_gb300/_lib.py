@@ -39,6 +39,7 @@ SIGNATURES = [
     ("poro_sync", _i32, [_vp, _i32]),
     ("poro_predict_dev", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _c.c_int, _vp]),
     ("poro_flop_count", _i32, [_vp, _i32, _pd]),
+    ("poro_set_refinement", _i32, [_vp, _i32]),
 ]
 
 
@@ -178,6 +179,10 @@ def poro_sync(ctx, timeout_ms=-1):
 def poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver=PORO_SOLVE_BLOCK, stream=None):
     """Device-pointer form; pointers are integers (e.g. torch.Tensor.data_ptr())."""
     return _check(lib().poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver, stream), ctx)
+
+
+def poro_set_refinement(ctx, sweeps):
+    return _check(lib().poro_set_refinement(ctx, sweeps), ctx)
 
 
 def poro_flop_count(ctx, refine_sweeps=0):

@@ -1,0 +1,174 @@
+// Device building blocks of the degree-block back-substitution (Section
+// "Block-wise back-substitution", Algorithm 3), templated on the arithmetic
+// type so the binary64 kernel and the binary32 sweeps of the refinement
+// kernel run the same code.
+//
+// Shared-memory layout of one element's b / Q tensor: quantity p at offset
+// p * QS, mode l at l * T, time mode u at u, where the quantity stride QS is
+// B * T padded so that QS = T (mod 32): the 13 T lanes (p, u) of one mode then
+// fall on consecutive 4-byte banks (conflict-free).  The star products X use
+// the same rule with the block size d_g in place of B.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "poro_internal.h"
+
+namespace poro {
+
+__host__ __device__ constexpr int bank_stride(int n, int T) { return n + ((T - n % 32) + 32) % 32; }
+
+template <int N>
+struct Alg3Shape {
+    static constexpr int B = n_modes(N);
+    static constexpr int T = N + 1;
+    static constexpr int QBT = NQ * B * T;                 // dense size (global layout)
+    static constexpr int QS = bank_stride(B * T, T);       // shared quantity stride
+    static constexpr int SQ = NQ * QS;                     // shared size of b / Q
+    static constexpr int DMAX = block_size(N);
+    static constexpr int XSMAX = bank_stride(DMAX * T, T);
+    static constexpr int PT = NQ * T;                      // (p, u) pairs of one mode
+    static constexpr int PUL = (PT + 31) / 32;             // pairs per lane
+};
+
+// Khat^j block CSR (rows l < o_g, columns m_local of block g) for one precision
+template <class Real>
+struct KhatBlocks {
+    const Real* val;
+    const int32_t* col;
+    const int32_t* row;
+    int32_t row_base[MAX_N + 1][3];
+};
+
+template <int T, class Real>
+__device__ __forceinline__ void solve_row(Real* row, const Real* Zi) {
+    Real x[T];
+#pragma unroll
+    for (int s = 0; s < T; ++s) x[s] = row[s];
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        Real acc = Real(0);
+#pragma unroll
+        for (int s = 0; s < T; ++s) acc = fma(Zi[u * T + s], x[s], acc);
+        row[u] = acc;
+    }
+}
+
+// b[p,l,u] = (S^{-1} w)_u q0[p,l] with (S^{-1} w)_u = (2u+1)(-1)^u
+template <int N, int NT, class Real, class In>
+__device__ __forceinline__ void init_rhs(Real* bq, const In* q0) {
+    using S = Alg3Shape<N>;
+    for (int i = threadIdx.x; i < NQ * S::B; i += NT) {
+        const Real v = (Real)q0[i];
+        const int p = i / S::B, l = i % S::B;
+        Real* row = bq + p * S::QS + l * S::T;
+#pragma unroll
+        for (int u = 0; u < S::T; ++u) row[u] = Real((2 * u + 1) * ((u & 1) ? -1 : 1)) * v;
+    }
+}
+
+// In-place sweep: on entry bq holds b, on exit the solution Q.  X is a
+// scratch area of JX * 13 * XSMAX values in shared memory; star[3][54] the
+// element's reference Jacobians on the union pattern; zuf = (Z - e I)^{-1},
+// zin = Z^{-1}; gcoup = E*_{u,uf}.  JX directions are handled per pass
+// (1 or 3).  Ends with a barrier.
+template <int N, int NT, class Real, int JX>
+__device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf, const Real* zin,
+                           const Real gcoup, const KhatBlocks<Real>& K) {
+    using S = Alg3Shape<N>;
+    constexpr int B = S::B, T = S::T, QS = S::QS, PT = S::PT, PUL = S::PUL, NW = NT / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int lp[PUL], lu[PUL];
+#pragma unroll
+    for (int k = 0; k < PUL; ++k) {
+        const int pu = lane + 32 * k;
+        lp[k] = pu < PT ? pu / T : 0;
+        lu[k] = pu < PT ? pu % T : 0;
+    }
+#pragma unroll 1
+    for (int g = N; g >= 0; --g) {
+        const int o = block_offset(g), d = block_size(g);
+        // time solves of block g: 7 plain rows (6 stresses, p) and 3 coupled
+        // pairs (u_f then u, v_f then v, w_f then w) per mode
+        for (int it = tid; it < 10 * d; it += NT) {
+            const int kind = it / d, m = o + it % d;
+            if (kind < 7) {
+                const int p = kind < 6 ? kind : QP;
+                solve_row<T>(bq + p * QS + m * T, zin);
+            } else {
+                const int i = kind - 7;
+                Real* rf = bq + (QUF + i) * QS + m * T;
+                Real* rv = bq + (QU + i) * QS + m * T;
+                solve_row<T>(rf, zuf);
+#pragma unroll
+                for (int u = 0; u < T; ++u) rv[u] = fma(gcoup, rf[u], rv[u]);
+                solve_row<T>(rv, zin);
+            }
+        }
+        __syncthreads();
+        if (g == 0) break;
+        const int XS = bank_stride(d * T, T);
+#pragma unroll 1
+        for (int jb = 0; jb < 3; jb += JX) {
+            // X^j[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u]
+            for (int it = tid; it < d * T; it += NT) {
+                const int ml = it / T, u = it % T;
+                Real qv[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) qv[q] = bq[q * QS + (o + ml) * T + u];
+#pragma unroll
+                for (int jj = 0; jj < JX; ++jj) {
+                    const Real* sj = star + (jb + jj) * STAR_NNZ;
+                    Real acc[NQ];
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p) acc[p] = Real(0);
+#pragma unroll
+                    for (int n = 0; n < STAR_NNZ; ++n)
+                        acc[star_row(n)] = fma(sj[n], qv[star_col(n)], acc[star_row(n)]);
+                    Real* xj = X + jj * NQ * S::XSMAX + ml * T + u;
+#pragma unroll
+                    for (int p = 0; p < NQ; ++p) xj[p * XS] = acc[p];
+                }
+            }
+            __syncthreads();
+            // b[p, l, u] -= sum_j sum_m Khat^j[l, o+m] X^j[p, m, u], l < o;
+            // one warp per row l, each lane owns PUL (p, u) pairs
+            int xo[PUL];
+#pragma unroll
+            for (int k = 0; k < PUL; ++k) xo[k] = lp[k] * XS + lu[k];
+            for (int l = warp; l < o; l += NW) {
+                Real acc[PUL];
+#pragma unroll
+                for (int k = 0; k < PUL; ++k) acc[k] = Real(0);
+#pragma unroll
+                for (int jj = 0; jj < JX; ++jj) {
+                    const int32_t* rp = K.row + K.row_base[g][jb + jj] + l;
+                    const int n0 = __ldg(rp), n1 = __ldg(rp + 1);
+                    const Real* xj = X + jj * NQ * S::XSMAX;
+                    int n = n0;
+                    for (; n + 1 < n1; n += 2) {
+                        const Real v0 = __ldg(K.val + n), v1 = __ldg(K.val + n + 1);
+                        const int m0 = __ldg(K.col + n) * T, m1 = __ldg(K.col + n + 1) * T;
+#pragma unroll
+                        for (int k = 0; k < PUL; ++k) {
+                            acc[k] = fma(v0, xj[xo[k] + m0], acc[k]);
+                            acc[k] = fma(v1, xj[xo[k] + m1], acc[k]);
+                        }
+                    }
+                    if (n < n1) {
+                        const Real v0 = __ldg(K.val + n);
+                        const int m0 = __ldg(K.col + n) * T;
+#pragma unroll
+                        for (int k = 0; k < PUL; ++k) acc[k] = fma(v0, xj[xo[k] + m0], acc[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PUL; ++k)
+                    if (lane + 32 * k < PT) bq[lp[k] * QS + l * T + lu[k]] -= acc[k];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace poro

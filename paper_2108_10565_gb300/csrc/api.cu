@@ -21,6 +21,8 @@ struct poro_ctx {
     cudaStream_t stream = nullptr;
     poro::ReferenceData ref;
     poro::DeviceReference dref;
+    poro::MixedReference mref;
+    int refine = 1;
     int64_t n_elem = 0;
     int stride = 0;
     double* d_econst = nullptr;
@@ -66,6 +68,11 @@ void free_population(poro_ctx* c) {
 }
 
 void free_reference(poro_ctx* c) {
+    dfree(c->mref.khat_val_f32);
+    dfree(c->mref.res_row);
+    dfree(c->mref.res_col);
+    dfree(c->mref.res_val);
+    dfree(c->mref.zinv_f32);
     dfree(c->dref.khat_val);
     dfree(c->dref.khat_col);
     dfree(c->dref.khat_row);
@@ -132,7 +139,49 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
         return e == cudaErrorMemoryAllocation ? fail(nullptr, PORO_ENOMEM, "poro_create: out of device memory")
                                               : cuda_fail(nullptr, e, "poro_create: upload");
     }
+    if (precision == PORO_FP32_REFINE) {
+        // binary32 copies for the sweeps and the (hi, lo) full-row CSR of the residual
+        const int B = c->B, T = c->T;
+        std::vector<float> vf(val.begin(), val.end()), zf(c->ref.zinv.begin(), c->ref.zinv.end());
+        std::vector<int32_t> rrow, rcol;
+        std::vector<float> rval;
+        for (int j = 0; j < 3; ++j) {
+            rrow.push_back((int32_t)rcol.size());
+            for (int l = 0; l < B; ++l) {
+                for (int m = 0; m < B; ++m) {
+                    const double v = c->ref.khat[((size_t)j * B + l) * B + m];
+                    if (v != 0.0) {
+                        const float h = (float)v;
+                        rcol.push_back(m);
+                        rval.push_back(h);
+                        rval.push_back((float)(v - (double)h));
+                    }
+                }
+                rrow.push_back((int32_t)rcol.size());
+            }
+        }
+        (void)T;
+        c->mref.base = &c->dref;
+        if ((e = upload((void**)&c->mref.khat_val_f32, vf.data(), vf.size() * sizeof(float))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_row, rrow.data(), rrow.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_col, rcol.data(), rcol.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_val, rval.data(), rval.size() * sizeof(float))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.zinv_f32, zf.data(), zf.size() * sizeof(float))) != cudaSuccess) {
+            free_reference(c);
+            cudaStreamDestroy(c->stream);
+            delete c;
+            return cuda_fail(nullptr, e, "poro_create: upload (mixed)");
+        }
+    }
     *out = c;
+    return PORO_OK;
+}
+
+poro_status poro_set_refinement(poro_ctx* c, int32_t sweeps) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_refinement: ctx is NULL");
+    if (c->prec != PORO_FP32_REFINE) return fail(c, PORO_EUNSUPPORTED, "poro_set_refinement: context is not mixed precision");
+    if (sweeps < 0 || sweeps > 2) return fail(c, PORO_EINVAL, "poro_set_refinement: sweeps must be 0, 1 or 2");
+    c->refine = sweeps;
     return PORO_OK;
 }
 
@@ -246,7 +295,7 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     if (c->prec == PORO_FP64) {
         rc = poro::launch_stp_fp64(c->dref, count, q0, ec, qt, iout, st);
     } else {
-        return fail(c, PORO_EUNSUPPORTED, "predict: precision not built");
+        rc = poro::launch_stp_mixed(c->mref, c->refine, count, q0, ec, qt, iout, st);
     }
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "predict: kernel launch");
     return PORO_OK;
@@ -330,8 +379,9 @@ poro_status poro_flop_count(const poro_ctx* c, int32_t refine_sweeps, double* f)
     const double alg3 = s3 + s4a + s4b + s15;
     f[0] = alg3;
     f[1] = alg3 * (1 + refine_sweeps);
-    // residual: diagonal time blocks + coupling + star/Khat products of all modes
-    f[2] = (2.0 * NQ * B * T * T + 2.0 * 6 * B * T + s4a + s4b) * refine_sweeps;
+    // residual per sweep: diagonal time blocks, E* diagonal and coupling,
+    // star products of all modes and the Khat products, in double-binary32
+    f[2] = (2.0 * NQ * B * T * T + 2.0 * 6 * B * T + 2.0 * 3 * poro::STAR_NNZ * B * T + s4b) * refine_sweeps;
     return PORO_OK;
 }
 

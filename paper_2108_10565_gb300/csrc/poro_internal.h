@@ -57,13 +57,12 @@ PORO_HD constexpr int star_col(int n) {
 //   star[3][54]       A^{j*} = dt A^j on the union pattern
 //   zinv_uf[T][T]     (Z - e I)^{-1}, e = E*_{uf,uf} (row-major, [u][s])
 //   e, g, dt, pad     E*_{uf,uf}, E*_{u,uf}, time step
-inline int elem_const_stride(int N) {
-    int T = N + 1;
-    int n = 3 * STAR_NNZ + T * T + 4;
-    return (n + 1) & ~1;  // keep 16-byte alignment of every element's block
+PORO_HD constexpr int elem_const_stride(int N) {
+    // keep 16-byte alignment of every element's block
+    return (3 * STAR_NNZ + (N + 1) * (N + 1) + 4 + 1) & ~1;
 }
-inline int ec_zinv(int) { return 3 * STAR_NNZ; }
-inline int ec_scalars(int N) { return 3 * STAR_NNZ + (N + 1) * (N + 1); }
+PORO_HD constexpr int ec_zinv(int) { return 3 * STAR_NNZ; }
+PORO_HD constexpr int ec_scalars(int N) { return 3 * STAR_NNZ + (N + 1) * (N + 1); }
 
 // Khat^j restricted to the columns of one degree block g, in CSR over the
 // rows l < o_g (the only rows Lemma 1 leaves non-zero); entries
@@ -106,6 +105,21 @@ struct DeviceReference {
     int32_t row_base[MAX_N + 1][3] = {};  // start of block (g, j)'s row pointers in khat_row
     double* zinv = nullptr;       // [T][T]
 };
+
+// Extra device data of the mixed-precision (refinement) path.
+struct MixedReference {
+    const DeviceReference* base = nullptr;
+    float* khat_val_f32 = nullptr;  // block CSR values in binary32 (same col/row as base)
+    int32_t* res_row = nullptr;     // [3][B+1] full-row CSR of Khat^j, absolute offsets
+    int32_t* res_col = nullptr;     // column m
+    float* res_val = nullptr;       // [nnz][2] Khat split into (hi, lo) binary32 words
+    float* zinv_f32 = nullptr;      // [T][T]
+};
+
+// Launch the mixed-precision predictor (binary32 sweeps, `refine` residual
+// corrections in double-binary32) for `count` elements.
+int launch_stp_mixed(const MixedReference& ref, int refine, int64_t count, const double* q0,
+                     const double* econst, double* qt, double* iout, void* stream);
 
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).

@@ -21,7 +21,7 @@
 // warp-wide FMA does useful work.
 #include <cuda_runtime.h>
 
-#include "poro_internal.h"
+#include "alg3_device.cuh"
 
 namespace poro {
 namespace {
@@ -33,48 +33,28 @@ struct K1Params {
     double* iout;
     int64_t count;
     int stride;
-    const double* khat_val;
-    const int32_t* khat_col;
-    const int32_t* khat_row;
-    int32_t row_base[MAX_N + 1][3];
+    KhatBlocks<double> khat;
     const double* zinv;
 };
 
-template <int T>
-__device__ __forceinline__ void solve_row(double* row, const double* Zi) {
-    double x[T];
-#pragma unroll
-    for (int s = 0; s < T; ++s) x[s] = row[s];
-#pragma unroll
-    for (int u = 0; u < T; ++u) {
-        double acc = 0.0;
-#pragma unroll
-        for (int s = 0; s < T; ++s) acc = fma(Zi[u * T + s], x[s], acc);
-        row[u] = acc;
-    }
-}
-
 template <int N>
-struct K1Shape {
-    static constexpr int B = n_modes(N);
-    static constexpr int T = N + 1;
-    static constexpr int QBT = NQ * B * T;
-    static constexpr int DMAX = block_size(N);
-    static constexpr int PU = ((NQ * T + 31) / 32) * 32;  // (p,u) lanes per Khat row, padded
+struct K1Shape : Alg3Shape<N> {
+    using A = Alg3Shape<N>;
     static constexpr int NT = N >= 5 ? 256 : (N == 4 ? 128 : 64);
-    // shared layout (doubles): bq[QBT] | X[13*DMAX*T] | star[162] | zuf[T*T] | sc[4] | zin[T*T]
-    static constexpr int OFF_X = QBT;
-    static constexpr int OFF_STAR = OFF_X + NQ * DMAX * T;
+    static constexpr int T_ = N + 1;
+    // shared layout (doubles): bq[13*QS] | X[13*XSMAX] | star[162] | zuf[T*T] | sc[4] | zin[T*T]
+    static constexpr int OFF_X = A::SQ;
+    static constexpr int OFF_STAR = OFF_X + NQ * A::XSMAX;
     static constexpr int OFF_ZUF = OFF_STAR + 3 * STAR_NNZ;
-    static constexpr int OFF_SC = OFF_ZUF + T * T;
+    static constexpr int OFF_SC = OFF_ZUF + T_ * T_;
     static constexpr int OFF_ZIN = OFF_SC + 4;
-    static constexpr int SMEM_DOUBLES = OFF_ZIN + T * T;
+    static constexpr int SMEM_DOUBLES = OFF_ZIN + T_ * T_;
 };
 
 template <int N>
 __global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params P) {
     using S = K1Shape<N>;
-    constexpr int B = S::B, T = S::T, NT = S::NT;
+    constexpr int B = S::B, T = S::T, NT = S::NT, QS = S::QS;
     extern __shared__ double sm[];
     double* bq = sm;
     double* X = sm + S::OFF_X;
@@ -90,80 +70,18 @@ __global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params
         // element constants: star[162], zinv_uf[T*T], e, g, dt, pad are contiguous
         for (int i = tid; i < 3 * STAR_NNZ + T * T + 4; i += NT) star[i] = ec[i];
         for (int i = tid; i < T * T; i += NT) zin[i] = P.zinv[i];
-        // S1: b[p,l,u] = (S^{-1} w)_u Q0[p,l],  (S^{-1} w)_u = (2u+1)(-1)^u
-        for (int i = tid; i < NQ * B; i += NT) {
-            const double v = q0[i];
-#pragma unroll
-            for (int u = 0; u < T; ++u) bq[i * T + u] = (double)((2 * u + 1) * ((u & 1) ? -1 : 1)) * v;
-        }
+        init_rhs<N, NT>(bq, q0);
         __syncthreads();
-        const double gcoup = sc[1];
-
-#pragma unroll 1
-        for (int g = N; g >= 0; --g) {
-            const int o = block_offset(g), d = block_size(g);
-            // S3: time solves of block g (10 work kinds per mode)
-            for (int it = tid; it < 10 * d; it += NT) {
-                const int kind = it / d, m = o + it % d;
-                if (kind < 7) {
-                    const int p = kind < 6 ? kind : QP;
-                    solve_row<T>(bq + (p * B + m) * T, zin);
-                } else {
-                    const int i = kind - 7;
-                    double* rf = bq + ((QUF + i) * B + m) * T;
-                    double* rv = bq + ((QU + i) * B + m) * T;
-                    solve_row<T>(rf, zuf);
-#pragma unroll
-                    for (int u = 0; u < T; ++u) rv[u] = fma(gcoup, rf[u], rv[u]);
-                    solve_row<T>(rv, zin);
-                }
-            }
-            __syncthreads();
-            if (g == 0) break;
-#pragma unroll 1
-            for (int j = 0; j < 3; ++j) {
-                const double* sj = star + j * STAR_NNZ;
-                // S4a: X[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u]
-                for (int it = tid; it < d * T; it += NT) {
-                    const int ml = it / T, u = it % T;
-                    double qv[NQ];
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) qv[q] = bq[(q * B + o + ml) * T + u];
-                    double acc[NQ];
-#pragma unroll
-                    for (int p = 0; p < NQ; ++p) acc[p] = 0.0;
-#pragma unroll
-                    for (int n = 0; n < STAR_NNZ; ++n)
-                        acc[star_row(n)] = fma(sj[n], qv[star_col(n)], acc[star_row(n)]);
-#pragma unroll
-                    for (int p = 0; p < NQ; ++p) X[(p * d + ml) * T + u] = acc[p];
-                }
-                __syncthreads();
-                // S4b: b[p, l, u] -= sum_m Khat^j[l, o+m] X[p, m, u]  for l < o
-                const int32_t* rp = P.khat_row + P.row_base[g][j];
-                for (int it = tid; it < o * S::PU; it += NT) {
-                    const int l = it / S::PU, pu = it % S::PU;  // l is warp-uniform
-                    if (pu < NQ * T) {
-                        const int p = pu / T, u = pu % T;
-                        const int n0 = __ldg(rp + l), n1 = __ldg(rp + l + 1);
-                        double acc = 0.0;
-                        for (int n = n0; n < n1; ++n)
-                            acc = fma(__ldg(P.khat_val + n), X[(p * d + __ldg(P.khat_col + n)) * T + u], acc);
-                        bq[(p * B + l) * T + u] -= acc;
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        // S5: outputs
+        alg3_sweep<N, NT, double, 1>(bq, X, star, zuf, zin, sc[1], P.khat);
+        // time integration and outputs (global layout [p][l][u], dense)
         const double dt = sc[2];
         if (P.iout) {
             double* io = P.iout + e * (int64_t)(NQ * B);
-            for (int i = tid; i < NQ * B; i += NT) io[i] = dt * bq[i * T];
+            for (int i = tid; i < NQ * B; i += NT) io[i] = dt * bq[(i / B) * QS + (i % B) * T];
         }
         if (P.qt) {
             double* qo = P.qt + e * (int64_t)S::QBT;
-            for (int i = tid; i < S::QBT; i += NT) qo[i] = bq[i];
+            for (int i = tid; i < S::QBT; i += NT) qo[i] = bq[(i / (B * T)) * QS + i % (B * T)];
         }
         __syncthreads();
     }
@@ -180,11 +98,11 @@ int launch_n(const DeviceReference& ref, int64_t count, const double* q0, const 
     P.iout = iout;
     P.count = count;
     P.stride = elem_const_stride(N);
-    P.khat_val = ref.khat_val;
-    P.khat_col = ref.khat_col;
-    P.khat_row = ref.khat_row;
+    P.khat.val = ref.khat_val;
+    P.khat.col = ref.khat_col;
+    P.khat.row = ref.khat_row;
     for (int g = 0; g <= MAX_N; ++g)
-        for (int j = 0; j < 3; ++j) P.row_base[g][j] = ref.row_base[g][j];
+        for (int j = 0; j < 3; ++j) P.khat.row_base[g][j] = ref.row_base[g][j];
     P.zinv = ref.zinv;
     const size_t smem = sizeof(double) * S::SMEM_DOUBLES;
     cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,

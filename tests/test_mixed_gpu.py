@@ -1,0 +1,106 @@
+"""GPU parity of the mixed-precision predictor (binary32 Algorithm 3 +
+refinement against a double-binary32 residual) against the FP64 oracle.
+
+Accuracy goal: relative L2 per element <= 1e-10 after refinement (one sweep
+and two sweeps); without refinement the binary32 solve alone is ~1e-6 (shown,
+so the tolerance tests the refinement and not the binary32 solve).
+"""
+import numpy as np
+import pytest
+
+from _oracle_cases import oracle_predictor, population, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-10
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_10565_gb300 import _lib
+
+    return _lib
+
+
+def _run(L, d, sweeps):
+    ctx = L.poro_create(0, d["N"], L.PORO_FP32_REFINE)
+    try:
+        L.poro_set_refinement(ctx, sweeps)
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"])
+        L.poro_predict(ctx)
+        n = d["Q0"].shape[0]
+        return L.poro_get_predictor(ctx, 0, n), L.poro_get_integrated(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+
+
+@pytest.mark.parametrize("N,n,n_dense", [(1, 33, 33), (2, 33, 33), (3, 33, 8), (4, 17, 3), (5, 11, 1), (6, 9, 1)])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_mixed_refined_matches_oracle(L, N, n, n_dense, sweeps):
+    d = population(n, N, seed=300 + N)
+    qt, iout = _run(L, d, sweeps)
+    errs = []
+    for i in range(n):
+        ref = oracle_predictor(d, i, dense=i < n_dense)
+        errs.append(rel_l2(qt[i], ref))
+        np.testing.assert_allclose(iout[i], d["dt"][i] * qt[i][:, :, 0], rtol=0, atol=1e-300)
+    assert max(errs) <= TOL_MIXED, f"max rel err {max(errs):.3e}"
+
+
+def test_unrefined_is_binary32_level(L):
+    """Refinement is what brings the error down: the binary32 sweep alone is
+    far from 1e-10 (and not garbage)."""
+    d = population(9, 5, seed=11)
+    qt, _ = _run(L, d, 0)
+    errs = [rel_l2(qt[i], oracle_predictor(d, i)) for i in range(9)]
+    assert 1e-9 < max(errs) < 1e-3
+
+
+@pytest.mark.parametrize("visc", [0.0, 100.0])
+def test_mixed_inviscid_and_very_stiff(L, visc):
+    d = population(7, 6, seed=17, viscosity_scale=visc)
+    qt, _ = _run(L, d, 1)
+    for i in range(7):
+        assert rel_l2(qt[i], oracle_predictor(d, i)) <= TOL_MIXED
+
+
+def test_mixed_full_size_against_fp64(L):
+    """The benchmark workload (200,000 elements, N = 6) in the bench's launch
+    configuration: every element against the FP64 kernel (itself pinned to
+    the oracle at 1e-12), and sampled elements against the oracle."""
+    import torch
+
+    from paper_2108_10565_gb300 import inputs
+
+    N, n = 6, 200_000
+    d = inputs.isolated_elements(n, N)
+    dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
+    q0 = torch.from_numpy(d["Q0"]).cuda()
+    B = q0.shape[2]
+    out = {}
+    for prec in (L.PORO_FP64, L.PORO_FP32_REFINE):
+        ctx = L.poro_create(0, N, prec)
+        try:
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
+            qt = torch.empty((n, 13, B, N + 1), dtype=torch.float64, device="cuda")
+            L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), None,
+                               stream=torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            out[prec] = qt
+        finally:
+            L.poro_destroy(ctx)
+    a, b = out[L.PORO_FP32_REFINE], out[L.PORO_FP64]
+    err = (torch.linalg.vector_norm((a - b).reshape(n, -1), dim=1)
+           / torch.linalg.vector_norm(b.reshape(n, -1), dim=1)).cpu().numpy()
+    assert np.isfinite(err).all()
+    assert err.max() <= TOL_MIXED, f"max {err.max():.3e} median {np.median(err):.3e}"
+    rng = np.random.default_rng(1)
+    for i in [0, n - 1] + list(rng.choice(n, 4, replace=False)):
+        sub = {"N": N, "vertices": d["vertices"][i:i + 1], "materials": d["materials"][i:i + 1],
+               "Q0": d["Q0"][i:i + 1], "dt": dt[i:i + 1]}
+        assert rel_l2(a[i].cpu().numpy(), oracle_predictor(sub, 0)) <= TOL_MIXED
