@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-lu", action="store_true")
+    ap.add_argument("--lu-n6", type=int, default=4, help="elements factored at N=6 for the LU comparator")
+    ap.add_argument("--lu-n3", type=int, default=1024, help="elements factored at N=3 for the LU comparator")
     return ap.parse_args()
 
 
@@ -180,6 +183,56 @@ def fp64_alu_peak_tflops(sm_mhz):
     return 1.25 * sm_mhz / 2070.0
 
 
+def lu_comparator(L, torch, dev, local, args, hbm_gbs):
+    """Block back-substitution vs the dense-LU comparator (factors
+    precomputed; the paper's comparison of Table flop-count)."""
+    from paper_2108_10565_gb300 import inputs
+
+    out = {}
+    for N, n in ((6, args.lu_n6), (3, args.lu_n3)):
+        if n <= 0:
+            continue
+        d = inputs.isolated_elements(n, N, seed=inputs.SEED_ISOLATED + 17)
+        dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
+        ctx = L.poro_create(local, N, L.PORO_FP64)
+        try:
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            L.poro_lu_factor(ctx, 0, n)
+            t_fac = time.perf_counter() - t0
+            q0 = torch.from_numpy(d["Q0"]).to(dev)
+            B = q0.shape[2]
+            qt = torch.empty((n, 13, B, N + 1), dtype=torch.float64, device=dev)
+            st = torch.cuda.Stream(device=local)
+            times = {}
+            for name, solver in (("lu_solve", L.PORO_SOLVE_LU), ("block", L.PORO_SOLVE_BLOCK)):
+                for _ in range(2):
+                    L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), None, solver, st.cuda_stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 3
+                with torch.cuda.stream(st):
+                    e0.record(st)
+                    for _ in range(reps):
+                        L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), None, solver, st.cuda_stream)
+                    e1.record(st)
+                torch.cuda.synchronize()
+                times[name] = e0.elapsed_time(e1) / reps * 1e-3
+            s_unk = 13 * B * (N + 1)
+            ceiling = hbm_gbs * 1e9 / (8.0 * s_unk * s_unk)
+            out[f"N{N}"] = {
+                "elements": n, "unknowns": s_unk, "factor_bytes_per_element": 8 * s_unk * s_unk,
+                "factor_s_per_element": t_fac / n,
+                "lu_solve_elements_per_s": n / times["lu_solve"],
+                "lu_solve_hbm_ceiling_elements_per_s": ceiling,
+                "block_fp64_elements_per_s_same_batch": n / times["block"],
+                "block_over_lu_solve": times["lu_solve"] / times["block"],
+            }
+        finally:
+            L.poro_destroy(ctx)
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -306,6 +359,14 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hi.numel() * 8), "form": head}
     for r in res.values():
         L.poro_destroy(r["ctx"])
+    lu = None
+    if not args.no_lu and world == 1:
+        hbm = 6792.1
+        try:
+            hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except Exception:
+            pass
+        lu = lu_comparator(L, torch, dev, local, args, hbm)
 
     if rank != 0:
         if world > 1:
@@ -331,6 +392,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
         "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": err,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
+        "lu_comparator": lu,
     }
     print(json.dumps(out))
     if world > 1:

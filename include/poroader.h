@@ -172,6 +172,27 @@ poro_status poro_sync(poro_ctx* ctx, int32_t timeout_ms);
 poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
                              double* Qt_dev, double* I_dev, poro_solver solver, void* stream);
 
+/* ------------------------------------------------------ dense-LU comparator */
+/* The approach Section "Block-wise back-substitution" replaces: the whole
+ * predictor system of an element (s = 13 B (N+1) unknowns) factored once,
+ * P Y = L U with partial pivoting in binary64 after power-of-two row and
+ * column equilibration, then two triangular solves per predictor (2 s^2
+ * flops, s^2 doubles of factors per element; Table flop-count). */
+
+/* Device bytes poro_lu_factor needs for `count` elements of degree N. */
+poro_status poro_lu_bytes(int degree_N, int64_t count, size_t* bytes);
+
+/* Assemble, equilibrate and factor the predictor systems of elements
+ * [first, first + count) (count <= 65535) into a context-owned device buffer
+ * (replaces a previous factorisation; synchronous).  Afterwards
+ * poro_predict / poro_predict_dev with PORO_SOLVE_LU solve those elements.
+ * Errors: PORO_ENOMEM (factors do not fit), PORO_ENUMERIC (zero pivot),
+ * PORO_ESTATE, PORO_EINVAL. */
+poro_status poro_lu_factor(poro_ctx* ctx, int64_t first, int64_t count);
+
+/* Free the factor buffer. */
+poro_status poro_lu_release(poro_ctx* ctx);
+
 /* Floating-point operations one predictor of this context performs, counted
  * from the structural non-zeros the kernels touch (Khat blocks, the 54-entry
  * star pattern, the (N+1)^2 time solves): used for rooflines.  flops_out[0]

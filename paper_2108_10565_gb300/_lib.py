@@ -40,6 +40,9 @@ SIGNATURES = [
     ("poro_predict_dev", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _c.c_int, _vp]),
     ("poro_flop_count", _i32, [_vp, _i32, _pd]),
     ("poro_set_refinement", _i32, [_vp, _i32]),
+    ("poro_lu_bytes", _i32, [_c.c_int, _i64, _c.POINTER(_c.c_size_t)]),
+    ("poro_lu_factor", _i32, [_vp, _i64, _i64]),
+    ("poro_lu_release", _i32, [_vp]),
 ]
 
 
@@ -183,6 +186,20 @@ def poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver=PORO_SOLVE
 
 def poro_set_refinement(ctx, sweeps):
     return _check(lib().poro_set_refinement(ctx, sweeps), ctx)
+
+
+def poro_lu_bytes(N, count):
+    b = ctypes.c_size_t()
+    _check(lib().poro_lu_bytes(N, count, ctypes.byref(b)))
+    return b.value
+
+
+def poro_lu_factor(ctx, first, count):
+    return _check(lib().poro_lu_factor(ctx, first, count), ctx)
+
+
+def poro_lu_release(ctx):
+    return _check(lib().poro_lu_release(ctx), ctx)
 
 
 def poro_flop_count(ctx, refine_sweeps=0):

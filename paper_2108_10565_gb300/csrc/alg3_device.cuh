@@ -76,7 +76,7 @@ template <int N, int NT, class Real, int JX>
 __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf, const Real* zin,
                            const Real gcoup, const KhatBlocks<Real>& K) {
     using S = Alg3Shape<N>;
-    constexpr int B = S::B, T = S::T, QS = S::QS, PT = S::PT, PUL = S::PUL, NW = NT / 32;
+    constexpr int T = S::T, QS = S::QS, PT = S::PT, PUL = S::PUL, NW = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int lp[PUL], lu[PUL];
 #pragma unroll

@@ -22,6 +22,9 @@ struct poro_ctx {
     poro::ReferenceData ref;
     poro::DeviceReference dref;
     poro::MixedReference mref;
+    poro::LUReference lref;
+    poro::LUScratch lu;
+    int64_t lu_first = 0, lu_count = 0;
     int refine = 1;
     int64_t n_elem = 0;
     int stride = 0;
@@ -58,7 +61,10 @@ cudaError_t upload(void** dst, const void* src, size_t bytes) {
     return e;
 }
 
+void free_lu(poro_ctx* c);
+
 void free_population(poro_ctx* c) {
+    free_lu(c);
     dfree(c->d_econst);
     dfree(c->d_q0);
     dfree(c->d_qt);
@@ -67,7 +73,21 @@ void free_population(poro_ctx* c) {
     c->have_dofs = c->have_pred = false;
 }
 
+void free_lu(poro_ctx* c) {
+    dfree(c->lu.A);
+    dfree(c->lu.piv);
+    dfree(c->lu.perm);
+    dfree(c->lu.R);
+    dfree(c->lu.C);
+    dfree(c->lu.bad);
+    c->lu_first = c->lu_count = 0;
+}
+
 void free_reference(poro_ctx* c) {
+    dfree(c->lref.z);
+    dfree(c->lref.krow);
+    dfree(c->lref.kcol);
+    dfree(c->lref.kval);
     dfree(c->mref.khat_val_f32);
     dfree(c->mref.res_row);
     dfree(c->mref.res_col);
@@ -138,6 +158,35 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
         delete c;
         return e == cudaErrorMemoryAllocation ? fail(nullptr, PORO_ENOMEM, "poro_create: out of device memory")
                                               : cuda_fail(nullptr, e, "poro_create: upload");
+    }
+    {
+        // full-row CSR of Khat^j in binary64 and Z for the dense-LU comparator
+        const int B = c->B;
+        std::vector<int32_t> lrow, lcol;
+        std::vector<double> lval;
+        for (int j = 0; j < 3; ++j) {
+            lrow.push_back((int32_t)lcol.size());
+            for (int l = 0; l < B; ++l) {
+                for (int m = 0; m < B; ++m) {
+                    const double v = c->ref.khat[((size_t)j * B + l) * B + m];
+                    if (v != 0.0) {
+                        lcol.push_back(m);
+                        lval.push_back(v);
+                    }
+                }
+                lrow.push_back((int32_t)lcol.size());
+            }
+        }
+        c->lref.N = degree_N;
+        if ((e = upload((void**)&c->lref.z, c->ref.z.data(), c->ref.z.size() * sizeof(double))) != cudaSuccess ||
+            (e = upload((void**)&c->lref.krow, lrow.data(), lrow.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->lref.kcol, lcol.data(), lcol.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->lref.kval, lval.data(), lval.size() * sizeof(double))) != cudaSuccess) {
+            free_reference(c);
+            cudaStreamDestroy(c->stream);
+            delete c;
+            return cuda_fail(nullptr, e, "poro_create: upload (LU)");
+        }
     }
     if (precision == PORO_FP32_REFINE) {
         // binary32 copies for the sweeps and the (hi, lo) full-row CSR of the residual
@@ -288,10 +337,16 @@ poro_status poro_set_dofs(poro_ctx* c, const double* Q) {
 
 static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, const double* q0, double* qt,
                                     double* iout, poro_solver solver, cudaStream_t st) {
-    if (solver != PORO_SOLVE_BLOCK)
-        return fail(c, PORO_EUNSUPPORTED, "predict: solver not available in this build");
     const double* ec = c->d_econst + first * c->stride;
     int rc = 0;
+    if (solver == PORO_SOLVE_LU) {
+        if (count > 0 && (first < c->lu_first || first + count > c->lu_first + c->lu_count))
+            return fail(c, PORO_ESTATE, "predict (LU): elements not factored; call poro_lu_factor first");
+        rc = poro::launch_lu_solve(c->lref, count, c->lu, first - c->lu_first, q0, ec, qt, iout, st);
+        if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "predict (LU): kernel launch");
+        return PORO_OK;
+    }
+    if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
     if (c->prec == PORO_FP64) {
         rc = poro::launch_stp_fp64(c->dref, count, q0, ec, qt, iout, st);
     } else {
@@ -323,6 +378,63 @@ poro_status poro_predict_dev(poro_ctx* c, int64_t first, int64_t count, const do
     cudaSetDevice(c->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     return dispatch_predict(c, first, count, q0, qt, iout, solver, st);
+}
+
+poro_status poro_lu_bytes(int degree_N, int64_t count, size_t* bytes) {
+    if (degree_N < 1 || degree_N > poro::MAX_N) return fail(nullptr, PORO_EUNSUPPORTED, "poro_lu_bytes: degree");
+    if (count < 0 || !bytes) return fail(nullptr, PORO_EINVAL, "poro_lu_bytes: bad argument");
+    *bytes = poro::lu_scratch_bytes(degree_N, count);
+    return PORO_OK;
+}
+
+poro_status poro_lu_factor(poro_ctx* c, int64_t first, int64_t count) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_lu_factor: ctx is NULL");
+    if (!c->d_econst) return fail(c, PORO_ESTATE, "poro_lu_factor: no element population loaded");
+    if (first < 0 || count < 0 || first + count > c->n_elem || count > 65535)
+        return fail(c, PORO_EINVAL, "poro_lu_factor: element range outside the population (or > 65535)");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_lu(c);
+    const size_t s = (size_t)NQ * c->B * c->T;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&c->lu.A, (size_t)count * s * s * sizeof(double) + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.piv, (size_t)count * s * sizeof(int32_t) + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.perm, (size_t)count * s * sizeof(int32_t) + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.R, (size_t)count * s * sizeof(double) + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.C, (size_t)count * s * sizeof(double) + 16)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.bad, sizeof(int32_t))) != cudaSuccess) {
+        free_lu(c);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_lu_factor: factors do not fit in HBM")
+                                              : cuda_fail(c, e, "poro_lu_factor");
+    }
+    int rc = poro::launch_lu_factor(c->lref, count, c->d_econst + first * c->stride, c->lu, c->stream);
+    if (rc != 0) {
+        free_lu(c);
+        return cuda_fail(c, (cudaError_t)rc, "poro_lu_factor: kernel launch");
+    }
+    int32_t bad = 0;
+    e = cudaMemcpyAsync(&bad, c->lu.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_lu(c);
+        return cuda_fail(c, e, "poro_lu_factor");
+    }
+    if (bad) {
+        free_lu(c);
+        return fail(c, PORO_ENUMERIC, "poro_lu_factor: zero pivot (singular predictor system)");
+    }
+    c->lu_first = first;
+    c->lu_count = count;
+    return PORO_OK;
+}
+
+poro_status poro_lu_release(poro_ctx* c) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_lu_release: ctx is NULL");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_lu(c);
+    return PORO_OK;
 }
 
 poro_status poro_sync(poro_ctx* c, int32_t timeout_ms) {

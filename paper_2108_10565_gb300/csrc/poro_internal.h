@@ -121,6 +121,28 @@ struct MixedReference {
 int launch_stp_mixed(const MixedReference& ref, int refine, int64_t count, const double* q0,
                      const double* econst, double* qt, double* iout, void* stream);
 
+// Dense-LU comparator: reference data and per-batch scratch (factors,
+// pivots, permutation, equilibration factors, singularity flag).
+struct LUReference {
+    int N = 0;
+    double* z = nullptr;       // [T][T] Z = S^{-1}(W - K^tau)
+    int32_t* krow = nullptr;   // [3][B+1] full-row CSR of Khat^j, absolute offsets
+    int32_t* kcol = nullptr;
+    double* kval = nullptr;
+};
+struct LUScratch {
+    double* A = nullptr;       // [count][s][s] factors L\U of P R Y' C
+    int32_t* piv = nullptr;    // [count][s]
+    int32_t* perm = nullptr;   // [count][s]
+    double* R = nullptr;       // [count][s]
+    double* C = nullptr;       // [count][s]
+    int32_t* bad = nullptr;    // 1 if a zero pivot occurred
+};
+size_t lu_scratch_bytes(int N, int64_t count);
+int launch_lu_factor(const LUReference& ref, int64_t count, const double* econst, LUScratch& w, void* stream);
+int launch_lu_solve(const LUReference& ref, int64_t count, const LUScratch& w, int64_t offset, const double* q0,
+                    const double* econst, double* qt, double* iout, void* stream);
+
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
 int launch_stp_fp64(const DeviceReference& ref, int64_t count, const double* q0,
