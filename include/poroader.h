@@ -193,6 +193,33 @@ poro_status poro_lu_factor(poro_ctx* ctx, int64_t first, int64_t count);
 /* Free the factor buffer. */
 poro_status poro_lu_release(poro_ctx* ctx);
 
+/* Dense-LU predictor without any allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc (for example code
+ * working inside a fixed device-memory budget handed out by an outer
+ * framework's allocator, or loops that must not take the device
+ * synchronisation cudaMalloc/cudaFree may imply), which poro_lu_factor
+ * excludes because it allocates its factor buffer on every call.
+ * Factors and solves elements [first, first + count) of the loaded population
+ * in one asynchronous call on `stream` (NULL: the context stream), with the
+ * same kernels as poro_lu_factor + PORO_SOLVE_LU; Q0_dev, Qt_dev (nullable),
+ * I_dev (nullable) as in poro_predict_dev (device pointers, 16-byte aligned,
+ * row 0 = element `first`).
+ * The factors live in one 64 MiB array inside the library (every GPU that
+ * loads libporoader holds it until the process exits); the call allocates
+ * nothing.  A batch needing more than 64 MiB of factors (s^2 doubles plus 24 s
+ * bytes per element, s = 13 B (N+1): at most 7 elements at N = 3, 1 at
+ * N = 4, none at N >= 5) is rejected with PORO_EINVAL and a message giving the
+ * bytes needed.  The first call for a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one array and each
+ * call zeroes what must start at zero (factor area, zero-pivot flag) before
+ * use; calls whose work overlaps on the GPU (different streams, or a second
+ * call before the first finished on another stream) race on the array.
+ * A zero pivot is not reported (use poro_lu_factor for the checked path).
+ * Errors: PORO_EINVAL, PORO_ESTATE (no population), PORO_ECUDA. */
+poro_status poro_lu_predict_static(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
+                                   double* Qt_dev, double* I_dev, void* stream);
+
 /* Floating-point operations one predictor of this context performs, counted
  * from the structural non-zeros the kernels touch (Khat blocks, the 54-entry
  * star pattern, the (N+1)^2 time solves): used for rooflines.  flops_out[0]

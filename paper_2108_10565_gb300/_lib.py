@@ -43,6 +43,7 @@ SIGNATURES = [
     ("poro_lu_bytes", _i32, [_c.c_int, _i64, _c.POINTER(_c.c_size_t)]),
     ("poro_lu_factor", _i32, [_vp, _i64, _i64]),
     ("poro_lu_release", _i32, [_vp]),
+    ("poro_lu_predict_static", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp]),
 ]
 
 
@@ -200,6 +201,11 @@ def poro_lu_factor(ctx, first, count):
 
 def poro_lu_release(ctx):
     return _check(lib().poro_lu_release(ctx), ctx)
+
+
+def poro_lu_predict_static(ctx, first, count, q0_ptr, qt_ptr, i_ptr, stream=None):
+    """Allocation-free dense-LU predictor (device pointers as integers)."""
+    return _check(lib().poro_lu_predict_static(ctx, first, count, q0_ptr, qt_ptr, i_ptr, stream), ctx)
 
 
 def poro_flop_count(ctx, refine_sweeps=0):

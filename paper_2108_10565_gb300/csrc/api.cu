@@ -101,6 +101,23 @@ void free_reference(poro_ctx* c) {
 
 }  // namespace
 
+namespace poro {
+bool ctx_view(const poro_ctx* c, CtxView& v) {
+    if (!c || !c->d_econst) return false;
+    v.device = c->device;
+    v.N = c->N;
+    v.n_elem = c->n_elem;
+    v.stride = c->stride;
+    v.econst = c->d_econst;
+    v.lref = &c->lref;
+    v.stream = c->stream;
+    return true;
+}
+void ctx_set_error(poro_ctx* c, const std::string& msg) {
+    if (c) c->err = msg; else g_err = msg;
+}
+}  // namespace poro
+
 extern "C" {
 
 const char* poro_last_error(const poro_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }

@@ -143,6 +143,19 @@ int launch_lu_factor(const LUReference& ref, int64_t count, const double* econst
 int launch_lu_solve(const LUReference& ref, int64_t count, const LUScratch& w, int64_t offset, const double* q0,
                     const double* econst, double* qt, double* iout, void* stream);
 
+// Read-only view of the context fields the allocation-free LU entry point
+// needs (defined in api.cu).
+struct CtxView {
+    int device = 0, N = 0;
+    int64_t n_elem = 0;
+    int stride = 0;
+    const double* econst = nullptr;
+    const LUReference* lref = nullptr;
+    void* stream = nullptr;
+};
+bool ctx_view(const poro_ctx* c, CtxView& v);
+void ctx_set_error(poro_ctx* c, const std::string& msg);
+
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
 int launch_stp_fp64(const DeviceReference& ref, int64_t count, const double* q0,
