@@ -114,3 +114,96 @@ def _blockwise(fn, rng, n, shape):
 
 def material_dict(row):
     return {k: float(v) for k, v in zip(PARAM_NAMES, row)}
+
+
+# ---------------------------------------------------------------- meshes
+SEED_CFG0 = 2108105650
+
+
+def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, True, True),
+                  tags=None):
+    """Structured tetrahedral mesh: an n[0] x n[1] x n[2] grid of boxes, each
+    cut into the 6 Kuhn tetrahedra around its main diagonal (a
+    translation-invariant split, so the mesh is conforming, also across
+    periodic boundaries).
+
+    Returns dict(vertices [nv][3], tets [ne][4] (vertex ids), neighbors
+    [ne][4] (element across face i, the face opposite local vertex i; -1 on
+    a boundary), face_tag [ne][4] (0 interior/periodic, 1 free surface,
+    2 absorbing)).  `tags` maps a boundary side ('x-', 'x+', ..., 'z+') to a
+    tag for non-periodic directions (default absorbing)."""
+    n = (n, n, n) if np.isscalar(n) else tuple(n)
+    for ax in range(3):
+        if periodic[ax] and n[ax] < 3:
+            raise ValueError("a periodic direction needs at least 3 boxes (wrapped faces would coincide)")
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    h = (hi - lo) / np.asarray(n)
+    nx, ny, nz = n
+    gi = np.arange(nx + 1)[:, None, None]
+    gj = np.arange(ny + 1)[None, :, None]
+    gk = np.arange(nz + 1)[None, None, :]
+
+    def vid(i, j, k):
+        return (i * (ny + 1) + j) * (nz + 1) + k
+
+    vert = np.stack(np.broadcast_arrays(lo[0] + gi * h[0], lo[1] + gj * h[1], lo[2] + gk * h[2]), -1).reshape(-1, 3)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                for pm in perms:
+                    c = [i, j, k]
+                    ids = [vid(*c)]
+                    for ax in pm:
+                        c[ax] += 1
+                        ids.append(vid(*c))
+                    tets.append(ids)
+    tets = np.array(tets, dtype=np.int64)
+    # face matching on wrapped vertex keys
+    ijk = np.stack(np.unravel_index(np.arange(vert.shape[0]), (nx + 1, ny + 1, nz + 1)), -1)
+    wrapped = ijk.copy()
+    for ax, m in enumerate(n):
+        if periodic[ax]:
+            wrapped[:, ax] %= m
+    wkey = (wrapped[:, 0] * (ny + 1) + wrapped[:, 1]) * (nz + 1) + wrapped[:, 2]
+    ne = tets.shape[0]
+    nb = -np.ones((ne, 4), dtype=np.int64)
+    seen = {}
+    for e in range(ne):
+        for f in range(4):
+            key = tuple(sorted(wkey[tets[e, [v for v in range(4) if v != f]]]))
+            if key in seen:
+                e2, f2 = seen.pop(key)
+                nb[e, f], nb[e2, f2] = e2, e
+            else:
+                seen[key] = (e, f)
+    tag = np.zeros((ne, 4), dtype=np.int32)
+    tags = tags or {}
+    for (e, f) in seen.values():
+        fv = ijk[tets[e, [v for v in range(4) if v != f]]]
+        side = None
+        for ax, name in enumerate("xyz"):
+            if np.all(fv[:, ax] == 0):
+                side = name + "-"
+            elif np.all(fv[:, ax] == n[ax]):
+                side = name + "+"
+        tag[e, f] = tags.get(side, 2)
+    return dict(vertices=vert, tets=tets, neighbors=nb, face_tag=tag)
+
+
+def config0_scenario():
+    """Plain method, small: unit cube, 4^3 boxes x 6 = 384 tetrahedra, periodic,
+    degree 2, 50 steps, homogeneous sandstone-like material, pressure point
+    source at the centre with a Ricker wavelet f0 = 10 kHz, t0 = 1e-4 s
+    (10 Hz scaled from km to m), 4 receivers at seeded positions in
+    [0.1, 0.9]^3, Q0 = 0."""
+    mesh = kuhn_box_mesh(4)
+    rng = np.random.Generator(np.random.PCG64(SEED_CFG0))
+    rec = rng.uniform(0.1, 0.9, (4, 3))
+    w = np.zeros(13)
+    w[9] = 1.0
+    ne = mesh["tets"].shape[0]
+    return dict(mesh=mesh, N=2, n_steps=50, materials=np.tile(REFERENCE_MATERIAL, (ne, 1)),
+                source=dict(x=np.array([0.5, 0.5, 0.5]), w=w, f0=1.0e4, t0=1.0e-4, amplitude=1.0),
+                receivers=rec, Q0=np.zeros((ne, 13, 10)))

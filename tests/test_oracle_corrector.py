@@ -1,0 +1,222 @@
+"""Pins of the oracle's corrector, flux and source against closed forms and
+invariants (CPU only)."""
+from math import factorial
+
+import numpy as np
+import pytest
+from scipy.special import roots_legendre
+
+from oracle import basis, corrector, flux, material
+from paper_2108_10565_gb300 import inputs
+
+
+def _mat(seed=None, nu_scale=1.0):
+    if seed is None:
+        row = inputs.REFERENCE_MATERIAL.copy()
+    else:
+        row = inputs.perturbed_materials(np.random.default_rng(seed), 1)[0]
+    m = inputs.material_dict(row)
+    m["nu"] *= nu_scale
+    return m
+
+
+def _scale(An):
+    """Diagonal similarity making A_n well scaled: stresses and pressure in
+    units of the largest entry ratio (sqrt of max stress-row entry over max
+    velocity-row entry), velocities unscaled."""
+    big = np.abs(An[[0, 1, 2, 3, 4, 5, 9]]).max()
+    small = np.abs(An[[6, 7, 8, 10, 11, 12]]).max()
+    s = np.ones(13)
+    s[[0, 1, 2, 3, 4, 5, 9]] = np.sqrt(big / small)
+    return s
+
+
+def _balrel(a, b, An):
+    """|a - b| measured in the well-scaled frame of A_n (rows of the flux
+    matrices differ by ~14 orders of magnitude in physical units)."""
+    d = _scale(An)
+    As = An * d[None, :] / d[:, None]
+    return np.abs((a - b) * d[None, :] / d[:, None]).max() / np.abs(As).max()
+
+
+N3 = [np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, -1.0]), np.array([1.0, 2.0, -2.0]) / 3.0]
+
+
+# ---------------------------------------------------------------- P11: fluxes
+def _upwind_reference(An):
+    """A_n^+ and A_n^- from the characteristic decomposition, in the
+    well-scaled frame, in complex arithmetic."""
+    d = _scale(An)
+    lam, V = np.linalg.eig(An * d[None, :] / d[:, None])
+    Vi = np.linalg.inv(V)
+    Ap = ((V * np.maximum(lam.real, 0)) @ Vi).real * d[:, None] / d[None, :]
+    Am = ((V * np.minimum(lam.real, 0)) @ Vi).real * d[:, None] / d[None, :]
+    return Ap, Am
+
+
+@pytest.mark.parametrize("n", N3)
+def test_homogeneous_flux_is_upwind(n):
+    m = _mat(1)
+    Fm, Fp = flux.flux_matrices(m, m, n)
+    An = flux.normal_jacobian(m, n)
+    Ap, Am = _upwind_reference(An)
+    assert _balrel(Fm, Ap, An) < 1e-13 and _balrel(Fp, Am, An) < 1e-13
+    assert _balrel(Fm + Fp, An, An) < 1e-14
+
+
+@pytest.mark.parametrize("n", N3)
+def test_interface_conditions_hold(n):
+    """Different materials on both sides: the Godunov states satisfy the 8
+    open-pore conditions, and F^- q_L + F^+ q_R = A_n^L q*_L."""
+    mL, mR = _mat(2), _mat(3, nu_scale=0.0)
+    mR["mu_M"] *= 0.5
+    rng = np.random.default_rng(4)
+    qL, qR = rng.standard_normal(13), rng.standard_normal(13)
+    sL, sR = flux.godunov_states(mL, mR, n, qL, qR)
+    C = flux.interface_rows(n)
+    scale = np.abs(C @ sL).max() + np.abs(C @ qL).max()
+    assert np.abs(C @ sL - C @ sR).max() < 1e-12 * scale
+    Fm, Fp = flux.flux_matrices(mL, mR, n)
+    AL = flux.normal_jacobian(mL, n)
+    assert np.allclose(Fm @ qL + Fp @ qR, AL @ sL, rtol=1e-10, atol=1e-10 * np.abs(AL @ sL).max())
+
+
+@pytest.mark.parametrize("n", N3)
+def test_free_surface_state(n):
+    """Free surface: q* = q_L + R^- alpha has zero traction and pressure."""
+    m = _mat(5)
+    Fm, Fp = flux.flux_matrices(m, None, n, "free_surface")
+    assert np.all(Fp == 0)
+    An = flux.normal_jacobian(m, n)
+    q = np.random.default_rng(6).standard_normal(13)
+    # q* = q_L + R^- alpha with R^- a real basis of the incoming waves
+    d = _scale(An)
+    lam, V = np.linalg.eig(An * d[None, :] / d[:, None])
+    Vi = np.linalg.inv(V)
+    Pm = ((V * (lam.real < -1e-6 * np.abs(lam).max())) @ Vi).real
+    Rm = np.linalg.svd(Pm)[0][:, :4] * d[:, None]
+    Cf = flux.traction_pressure_rows(n)
+    alpha = -np.linalg.solve(Cf @ Rm, Cf @ q)
+    qs = q + Rm @ alpha
+    assert np.abs(Cf @ qs).max() < 1e-10 * np.abs(Cf @ q).max()
+    assert np.allclose(Fm @ q, An @ qs, rtol=1e-10, atol=1e-12 * np.abs(An @ qs).max())
+
+
+def test_absorbing_has_no_incoming_waves():
+    """Absorbing: F^- = A_n^+ (outgoing characteristics only), and F^- maps
+    every incoming eigenvector to zero."""
+    m = _mat(7)
+    n = N3[2]
+    Fm, Fp = flux.flux_matrices(m, None, n, "absorbing")
+    assert np.all(Fp == 0)
+    An = flux.normal_jacobian(m, n)
+    Ap, Am = _upwind_reference(An)
+    assert _balrel(Fm, Ap, An) < 1e-13
+    # incoming waves: F^- A_n^- = 0 (in the well-scaled frame of A_n)
+    d = _scale(An)
+    sc = d[None, :] / d[:, None]
+    amax = np.abs(An * sc).max()
+    assert np.abs((Fm * sc) @ (Am * sc)).max() < 1e-13 * amax ** 2
+
+
+# ---------------------------------------------------------------- quadrature, source
+def test_triangle_quadrature_monomials():
+    for N in (1, 3, 6):
+        pts, w = corrector.triangle_quadrature(N)
+        assert w.sum() == pytest.approx(0.5, rel=1e-15)
+        for i in range(2 * N + 2):
+            for j in range(2 * N + 2 - i):
+                exact = factorial(i) * factorial(j) / factorial(i + j + 2)
+                assert np.sum(w * pts[:, 0] ** i * pts[:, 1] ** j) == pytest.approx(exact, rel=1e-12)
+
+
+def test_ricker_antiderivative():
+    f0, t0 = 10.0, 0.1
+    x, w = roots_legendre(20)
+    for a, b in ((0.0, 0.05), (0.08, 0.12), (0.1, 0.3)):
+        quad = 0.0
+        edges = np.linspace(a, b, 21)       # composite 20-point Gauss, 20 panels
+        for a1, b1 in zip(edges[:-1], edges[1:]):
+            t = a1 + (b1 - a1) * (x + 1) / 2
+            s = (1 - 2 * (np.pi * f0 * (t - t0)) ** 2) * np.exp(-(np.pi * f0 * (t - t0)) ** 2)
+            quad += (b1 - a1) / 2 * np.sum(w * s)
+        got = corrector.ricker_antiderivative(b, f0, t0) - corrector.ricker_antiderivative(a, f0, t0)
+        assert got == pytest.approx(quad, rel=1e-13, abs=1e-17)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_point_source_is_discrete_delta(N):
+    """sum_k phi_k(xi_s) / M_kk int phi_k p = p(xi_s) for p of degree <= N:
+    the projected point source reproduces point evaluation."""
+    rng = np.random.default_rng(N)
+    xi_s = rng.dirichlet([2, 2, 2, 2])[1:]
+    c = rng.standard_normal(basis.n_modes(N))
+    M = np.diag(basis.mass_matrix(N))
+    # int phi_k p = M_kk c_k for p = sum c_l phi_l (orthogonality)
+    proj = np.sum(corrector.basis_values(N, xi_s)[0] / M * (M * c))
+    assert proj == pytest.approx(corrector.basis_values(N, xi_s)[0] @ c, rel=1e-12)
+
+
+# ---------------------------------------------------------------- P8: invariants of a periodic run
+def _pade(k, m, z):
+    num = sum(factorial(k + m - j) * factorial(k) / (factorial(k + m) * factorial(j) * factorial(k - j)) * z ** j
+              for j in range(k + 1))
+    den = sum(factorial(k + m - j) * factorial(m) / (factorial(k + m) * factorial(j) * factorial(m - j)) * (-z) ** j
+              for j in range(m + 1))
+    return num / den
+
+
+@pytest.fixture(scope="module")
+def periodic_sim():
+    mesh = inputs.kuhn_box_mesh(3)
+    ne = mesh["tets"].shape[0]
+    return corrector.GTSSimulation(mesh, np.tile(inputs.REFERENCE_MATERIAL, (ne, 1)), 2)
+
+
+def _face_term_scale(sim, Q):
+    """Largest single-face flux contribution to any DOF in one step (the face
+    terms of a uniform state cancel around each element; rounding is
+    relative to them)."""
+    I = sim.dt * Q
+    sc = np.zeros(13)
+    for e in range(sim.ne):
+        for (area, phiL, phiR, Fm, Fp, r) in sim.face[e]:
+            t = np.abs(Fm @ (I[e] @ phiL.T)).max(axis=1) * 2 * area / sim.detJ[e] / sim.M[0]
+            sc = np.maximum(sc, t)
+    return sc
+
+
+def test_periodic_uniform_state(periodic_sim):
+    """Spatially uniform data on a periodic homogeneous mesh: fluxes and
+    volume terms vanish; sigma and p stay constant and the Darcy pair evolves
+    by the (N, N+1) Pade approximant: u_f -> R(e) u_f, u -> u + g/e (R-1) u_f
+    (up to rounding of the cancelling face terms)."""
+    sim = periodic_sim
+    Q = np.zeros((sim.ne, 13, sim.B))
+    Q[:, :, 0] = np.arange(1.0, 14.0)
+    Q1 = sim.step(Q, 0.0)
+    tol = 1e-13 * _face_term_scale(sim, Q)
+    e, g = sim.E[0, 10, 10] * sim.dt, sim.E[0, 6, 10] * sim.dt
+    R = _pade(2, 3, e)
+    want = Q[:, :, 0].copy()
+    want[:, 10:] = R * Q[:, 10:, 0]
+    want[:, 6:9] = Q[:, 6:9, 0] + g / e * (R - 1) * Q[:, 10:, 0]
+    assert np.all(np.abs(Q1[:, :, 0] - want) <= tol[None, :] + 1e-14 * np.abs(want))
+    assert np.all(np.abs(Q1[:, :, 1:]) <= tol[None, :, None])
+    # the Darcy pair has no large cancelling terms on its own scale: tight check
+    assert np.abs(Q1[:, 10:, 0] / (R * Q[:, 10:, 0]) - 1).max() < 1e-9
+
+
+def test_periodic_conservation(periodic_sim):
+    """Random data: the volume-weighted means of the stresses and the
+    pressure are conserved (the fluxes telescope, no source), up to rounding
+    of the per-element updates."""
+    sim = periodic_sim
+    rng = np.random.default_rng(8)
+    Q = rng.standard_normal((sim.ne, 13, sim.B))
+    Q1 = sim.step(Q, 0.0)
+    vol = sim.detJ / 6
+    for q in (0, 1, 2, 3, 4, 5, 9):
+        change = np.sum(vol * (Q1[:, q, 0] - Q[:, q, 0]))
+        scale = np.sum(vol * np.abs(Q1[:, q, 0] - Q[:, q, 0]))
+        assert abs(change) <= 1e-12 * scale
