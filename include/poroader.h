@@ -67,6 +67,12 @@ typedef enum {
 } poro_precision;
 
 typedef enum {
+    PORO_FACE_INTERIOR = 0,     /* interior or periodic face (a neighbour is given) */
+    PORO_FACE_FREE_SURFACE = 1, /* sigma n = 0, p = 0 (Section "Free surface") */
+    PORO_FACE_ABSORBING = 2     /* no incoming waves (Section "Homogeneous full-space") */
+} poro_face;
+
+typedef enum {
     PORO_SOLVE_BLOCK = 0,   /* Algorithm 3: degree-block back-substitution */
     PORO_SOLVE_LU = 1       /* dense LU of the whole predictor system (comparator) */
 } poro_solver;
@@ -171,6 +177,73 @@ poro_status poro_sync(poro_ctx* ctx, int32_t timeout_ms);
  * is element `first`.  Errors: PORO_EINVAL, PORO_ESTATE, PORO_ECUDA. */
 poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
                              double* Qt_dev, double* I_dev, poro_solver solver, void* stream);
+
+/* ------------------------------------------------------ meshes, corrector, time stepping */
+/* A conforming tetrahedral mesh (Section "Spatial discretisation"):
+ * xyz[n_vert][3] vertex coordinates, tet[n_elem][4] vertex ids, nb[n_elem][4]
+ * the element across face i (the face opposite local vertex i) or -1 on a
+ * boundary, face_tag[n_elem][4] a poro_face value (boundary faces must be
+ * PORO_FACE_FREE_SURFACE or PORO_FACE_ABSORBING; periodicity is expressed
+ * through nb, the faces of periodic neighbours matching up to a translation).
+ * Inputs are copied.  Replaces any previous population.  Errors: PORO_EINVAL. */
+poro_status poro_set_mesh(poro_ctx* ctx, int64_t n_vert, const double* xyz, int64_t n_elem, const int64_t* tet,
+                          const int64_t* nb, const int32_t* face_tag);
+
+/* One material per element (constant per element, Section "Spatial
+ * discretisation").  Errors: PORO_ESTATE (no mesh), PORO_EINVAL. */
+poro_status poro_set_materials(poro_ctx* ctx, const poro_material* mat);
+
+/* Time steps (Section "Temporal discretisation with ADER"): every element's
+ * CFL step cfl_c/(2N+1) d/v; with max_clusters = 1 (global time stepping) all
+ * elements use the smallest.  Builds the element constants, the face data
+ * (neighbour face, vertex permutation, outward normal, area) and the Godunov
+ * flux solvers of every face, and zeroes the DOFs.  dt_min_out (nullable)
+ * receives the step, cluster_out[n_elem] (nullable) the cluster of each
+ * element.  Errors: PORO_ESTATE, PORO_EINVAL (non-conforming face),
+ * PORO_EUNSUPPORTED (max_clusters > 1: local time stepping not built). */
+poro_status poro_set_clusters(poro_ctx* ctx, double cfl_c, int32_t max_clusters, double* dt_min_out,
+                              int32_t* cluster_out);
+
+/* Point source with a Ricker wavelet s(t) = A (1 - 2a^2) exp(-a^2),
+ * a = pi f0 (t - t0), acting on the quantities with weights w[13]
+ * (Section "Homogeneous full-space"); located in the lowest-numbered element
+ * containing xyz.  Each step adds w_p phi_k(xi_s) / (|J| M_kk) times the
+ * exact integral of s over the step.  After poro_set_clusters.
+ * Errors: PORO_EINVAL (outside the mesh), PORO_ESTATE. */
+poro_status poro_add_point_source(poro_ctx* ctx, const double xyz[3], const double w[13], double f0, double t0,
+                                  double amplitude);
+
+/* Receiver at xyz: q_p(x_r) = sum_l Q_pl phi_l(xi_r) sampled at the end of
+ * every step.  *id_out receives its index. */
+poro_status poro_add_receiver(poro_ctx* ctx, const double xyz[3], int32_t* id_out);
+
+/* Advance from the current time by whole steps while t + dt <= t_end:
+ * predictor of every element (the context's precision, Algorithm 3), the
+ * corrector of Eq. semi_discrete over the step (volume, Darcy source term,
+ * Godunov flux with the neighbours' time-integrated predictors), point
+ * sources and receivers.  Synchronises at the end and collects the new
+ * seismogram samples. */
+poro_status poro_advance(poro_ctx* ctx, double t_end);
+
+/* One corrector pass of all elements from the last predictor (low-level). */
+poro_status poro_correct(poro_ctx* ctx, int32_t cluster);
+
+/* DOFs Q_out[n_elem][13][B] (synchronises). */
+poro_status poro_get_dofs(poro_ctx* ctx, double* Q_out);
+
+/* Samples of receiver rec: up to cap times t_out[cap] and values
+ * q_out[cap][13]; *n_out = number of samples recorded. */
+poro_status poro_get_seismogram(poro_ctx* ctx, int32_t rec, int64_t cap, double* t_out, double* q_out,
+                                int64_t* n_out);
+
+/* Current simulation time and step. */
+poro_status poro_get_time(const poro_ctx* ctx, double* t, double* dt);
+
+/* Host-only: the Godunov flux solver matrices of one face with unit outward
+ * normal n[3] (A_n^L q* = Fm q_L + Fp q_R, both [13][13] row-major); kind a
+ * poro_face value; mR is required for PORO_FACE_INTERIOR. */
+poro_status poro_flux_matrices(const poro_material* mL, const poro_material* mR, const double n[3], int32_t kind,
+                               double* Fm, double* Fp);
 
 /* ------------------------------------------------------ dense-LU comparator */
 /* The approach Section "Block-wise back-substitution" replaces: the whole

@@ -44,6 +44,17 @@ SIGNATURES = [
     ("poro_lu_factor", _i32, [_vp, _i64, _i64]),
     ("poro_lu_release", _i32, [_vp]),
     ("poro_lu_predict_static", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    ("poro_set_mesh", _i32, [_vp, _i64, _vp, _i64, _vp, _vp, _vp]),
+    ("poro_set_materials", _i32, [_vp, _vp]),
+    ("poro_set_clusters", _i32, [_vp, _dbl, _i32, _pd, _vp]),
+    ("poro_add_point_source", _i32, [_vp, _vp, _vp, _dbl, _dbl, _dbl]),
+    ("poro_add_receiver", _i32, [_vp, _vp, _c.POINTER(_i32)]),
+    ("poro_advance", _i32, [_vp, _dbl]),
+    ("poro_correct", _i32, [_vp, _i32]),
+    ("poro_get_dofs", _i32, [_vp, _vp]),
+    ("poro_get_seismogram", _i32, [_vp, _i32, _i64, _vp, _vp, _c.POINTER(_i64)]),
+    ("poro_get_time", _i32, [_vp, _pd, _pd]),
+    ("poro_flux_matrices", _i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
 ]
 
 
@@ -206,6 +217,82 @@ def poro_lu_release(ctx):
 def poro_lu_predict_static(ctx, first, count, q0_ptr, qt_ptr, i_ptr, stream=None):
     """Allocation-free dense-LU predictor (device pointers as integers)."""
     return _check(lib().poro_lu_predict_static(ctx, first, count, q0_ptr, qt_ptr, i_ptr, stream), ctx)
+
+
+def poro_set_mesh(ctx, vertices, tets, neighbors, face_tag):
+    v = _f64(vertices)
+    t = np.ascontiguousarray(tets, dtype=np.int64)
+    nb = np.ascontiguousarray(neighbors, dtype=np.int64)
+    tg = np.ascontiguousarray(face_tag, dtype=np.int32)
+    return _check(lib().poro_set_mesh(ctx, v.shape[0], _ptr(v), t.shape[0], _ptr(t), _ptr(nb), _ptr(tg)), ctx)
+
+
+def poro_set_materials(ctx, mat):
+    m = _f64(mat)
+    return _check(lib().poro_set_materials(ctx, _ptr(m)), ctx)
+
+
+def poro_set_clusters(ctx, cfl_c=0.5, max_clusters=1, n_elem=None):
+    dt = _dbl()
+    cl = np.zeros(n_elem, dtype=np.int32) if n_elem else None
+    _check(lib().poro_set_clusters(ctx, cfl_c, max_clusters, ctypes.byref(dt), _ptr(cl)), ctx)
+    return dt.value, cl
+
+
+def poro_add_point_source(ctx, xyz, w, f0, t0, amplitude=1.0):
+    x, ww = _f64(xyz), _f64(w)
+    return _check(lib().poro_add_point_source(ctx, _ptr(x), _ptr(ww), f0, t0, amplitude), ctx)
+
+
+def poro_add_receiver(ctx, xyz):
+    x = _f64(xyz)
+    i = _i32()
+    _check(lib().poro_add_receiver(ctx, _ptr(x), ctypes.byref(i)), ctx)
+    return i.value
+
+
+def poro_advance(ctx, t_end):
+    return _check(lib().poro_advance(ctx, t_end), ctx)
+
+
+def poro_correct(ctx, cluster=-1):
+    return _check(lib().poro_correct(ctx, cluster), ctx)
+
+
+def poro_get_dofs(ctx, out=None):
+    N, _, n = poro_get_info(ctx)
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    if out is None:
+        out = np.empty((n, 13, B))
+    _check(lib().poro_get_dofs(ctx, _ptr(out)), ctx)
+    return out
+
+
+def poro_get_seismogram(ctx, rec):
+    n = _i64()
+    _check(lib().poro_get_seismogram(ctx, rec, 0, None, None, ctypes.byref(n)), ctx)
+    t = np.empty(n.value)
+    q = np.empty((n.value, 13))
+    _check(lib().poro_get_seismogram(ctx, rec, n.value, _ptr(t), _ptr(q), ctypes.byref(n)), ctx)
+    return t, q
+
+
+def poro_get_time(ctx):
+    t, dt = _dbl(), _dbl()
+    _check(lib().poro_get_time(ctx, ctypes.byref(t), ctypes.byref(dt)), ctx)
+    return t.value, dt.value
+
+
+def poro_flux_matrices(matL, matR, n, kind):
+    mL = _f64(matL)
+    mR = _f64(matR) if matR is not None else None
+    nn = _f64(n)
+    Fm, Fp = np.zeros((13, 13)), np.zeros((13, 13))
+    _check(lib().poro_flux_matrices(_ptr(mL), _ptr(mR), _ptr(nn), kind, _ptr(Fm), _ptr(Fp)))
+    return Fm, Fp
+
+
+PORO_FACE_INTERIOR, PORO_FACE_FREE_SURFACE, PORO_FACE_ABSORBING = 0, 1, 2
 
 
 def poro_flop_count(ctx, refine_sweeps=0):

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -34,6 +35,27 @@ struct poro_ctx {
     double* d_iout = nullptr;
     bool have_dofs = false, have_pred = false;
     std::string err;
+    // ---- mesh mode (corrector, sources, receivers, time stepping)
+    bool mesh_mode = false, have_mat = false, ready = false;
+    std::vector<double> h_xyz;
+    std::vector<int64_t> h_tet, h_nb;
+    std::vector<int32_t> h_tag;
+    std::vector<poro_material> h_mat;
+    double dt = 0.0, t = 0.0;
+    poro::CorrectorData cd;
+    int32_t *d_nb = nullptr, *d_tab = nullptr, *d_vrow = nullptr, *d_vcol = nullptr;
+    double *d_fc = nullptr, *d_fF = nullptr, *d_Floc = nullptr, *d_Fnb = nullptr, *d_vval = nullptr,
+           *d_minv = nullptr;
+    struct Source {
+        int64_t elem;
+        double* d_coef;
+        double f0, t0;
+    };
+    std::vector<Source> sources;
+    std::vector<int64_t> rec_elem;
+    std::vector<double> rec_phi;
+    std::vector<std::vector<double>> seis_q;   // per receiver [n][13]
+    std::vector<double> seis_t;
 };
 
 namespace {
@@ -63,8 +85,25 @@ cudaError_t upload(void** dst, const void* src, size_t bytes) {
 
 void free_lu(poro_ctx* c);
 
+void free_mesh_device(poro_ctx* c) {
+    dfree(c->d_nb);
+    dfree(c->d_tab);
+    dfree(c->d_vrow);
+    dfree(c->d_vcol);
+    dfree(c->d_fc);
+    dfree(c->d_fF);
+    dfree(c->d_Floc);
+    dfree(c->d_Fnb);
+    dfree(c->d_vval);
+    dfree(c->d_minv);
+    for (auto& s : c->sources) dfree(s.d_coef);
+    c->sources.clear();
+    c->ready = false;
+}
+
 void free_population(poro_ctx* c) {
     free_lu(c);
+    free_mesh_device(c);
     dfree(c->d_econst);
     dfree(c->d_q0);
     dfree(c->d_qt);
@@ -311,19 +350,7 @@ poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_
     return PORO_OK;
 }
 
-poro_status poro_set_isolated(poro_ctx* c, int64_t n, const double* vert, const poro_material* mat,
-                              const double* dt) {
-    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated: ctx is NULL");
-    if (n < 0 || (n > 0 && (!vert || !mat || !dt))) return fail(c, PORO_EINVAL, "poro_set_isolated: bad argument");
-    cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
-    free_population(c);
-    std::vector<double> ec((size_t)n * c->stride);
-    for (int64_t i = 0; i < n; ++i) {
-        std::string err;
-        if (!poro::element_constants(c->ref, vert + 12 * i, mat[i], dt[i], ec.data() + (size_t)i * c->stride, err))
-            return fail(c, PORO_EINVAL, "poro_set_isolated: element " + std::to_string(i) + ": " + err);
-    }
+static poro_status upload_population(poro_ctx* c, int64_t n, const std::vector<double>& ec) {
     const size_t nd = (size_t)n * NQ * c->B;
     cudaError_t e;
     if ((e = upload((void**)&c->d_econst, ec.data(), ec.size() * sizeof(double))) != cudaSuccess ||
@@ -331,11 +358,28 @@ poro_status poro_set_isolated(poro_ctx* c, int64_t n, const double* vert, const 
         (e = cudaMalloc((void**)&c->d_qt, nd * c->T * sizeof(double) + 16)) != cudaSuccess ||
         (e = cudaMalloc((void**)&c->d_iout, nd * sizeof(double) + 16)) != cudaSuccess) {
         free_population(c);
-        return e == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_isolated: out of device memory")
-                                              : cuda_fail(c, e, "poro_set_isolated");
+        return e == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "population: out of device memory")
+                                              : cuda_fail(c, e, "population");
     }
     c->n_elem = n;
     return PORO_OK;
+}
+
+poro_status poro_set_isolated(poro_ctx* c, int64_t n, const double* vert, const poro_material* mat,
+                              const double* dt) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated: ctx is NULL");
+    if (n < 0 || (n > 0 && (!vert || !mat || !dt))) return fail(c, PORO_EINVAL, "poro_set_isolated: bad argument");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    c->mesh_mode = false;
+    std::vector<double> ec((size_t)n * c->stride);
+    for (int64_t i = 0; i < n; ++i) {
+        std::string err;
+        if (!poro::element_constants(c->ref, vert + 12 * i, mat[i], dt[i], ec.data() + (size_t)i * c->stride, err))
+            return fail(c, PORO_EINVAL, "poro_set_isolated: element " + std::to_string(i) + ": " + err);
+    }
+    return upload_population(c, n, ec);
 }
 
 poro_status poro_set_dofs(poro_ctx* c, const double* Q) {
@@ -511,6 +555,415 @@ poro_status poro_flop_count(const poro_ctx* c, int32_t refine_sweeps, double* f)
     // residual per sweep: diagonal time blocks, E* diagonal and coupling,
     // star products of all modes and the Khat products, in double-binary32
     f[2] = (2.0 * NQ * B * T * T + 2.0 * 6 * B * T + 2.0 * 3 * poro::STAR_NNZ * B * T + s4b) * refine_sweeps;
+    return PORO_OK;
+}
+
+// ------------------------------------------------------------ mesh mode
+poro_status poro_set_mesh(poro_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem, const int64_t* tet,
+                          const int64_t* nb, const int32_t* face_tag) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_mesh: ctx is NULL");
+    if (n_vert <= 0 || n_elem <= 0 || !xyz || !tet || !nb || !face_tag)
+        return fail(c, PORO_EINVAL, "poro_set_mesh: empty mesh or NULL array");
+    for (int64_t i = 0; i < 4 * n_elem; ++i) {
+        if (tet[i] < 0 || tet[i] >= n_vert) return fail(c, PORO_EINVAL, "poro_set_mesh: vertex index out of range");
+        if (nb[i] < -1 || nb[i] >= n_elem) return fail(c, PORO_EINVAL, "poro_set_mesh: neighbour index out of range");
+        if (nb[i] < 0 && face_tag[i] != PORO_FACE_FREE_SURFACE && face_tag[i] != PORO_FACE_ABSORBING)
+            return fail(c, PORO_EINVAL, "poro_set_mesh: boundary face needs a free-surface or absorbing tag");
+    }
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    c->h_xyz.assign(xyz, xyz + 3 * n_vert);
+    c->h_tet.assign(tet, tet + 4 * n_elem);
+    c->h_nb.assign(nb, nb + 4 * n_elem);
+    c->h_tag.assign(face_tag, face_tag + 4 * n_elem);
+    c->h_mat.clear();
+    c->mesh_mode = true;
+    c->have_mat = false;
+    c->rec_elem.clear();
+    c->rec_phi.clear();
+    c->seis_q.clear();
+    c->seis_t.clear();
+    c->t = 0.0;
+    return PORO_OK;
+}
+
+poro_status poro_set_materials(poro_ctx* c, const poro_material* mat) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_materials: ctx is NULL");
+    if (!c->mesh_mode) return fail(c, PORO_ESTATE, "poro_set_materials: no mesh");
+    if (!mat) return fail(c, PORO_EINVAL, "poro_set_materials: NULL");
+    const int64_t ne = (int64_t)c->h_tet.size() / 4;
+    for (int64_t i = 0; i < ne; ++i) {
+        double v;
+        std::string err;
+        if (!poro::max_wave_speed(mat[i], v, err))
+            return fail(c, PORO_EINVAL, "poro_set_materials: element " + std::to_string(i) + ": " + err);
+    }
+    c->h_mat.assign(mat, mat + ne);
+    c->have_mat = true;
+    return PORO_OK;
+}
+
+namespace {
+void elem_vertices(const poro_ctx* c, int64_t e, double v[12]) {
+    for (int k = 0; k < 4; ++k)
+        for (int d = 0; d < 3; ++d) v[3 * k + d] = c->h_xyz[3 * c->h_tet[4 * e + k] + d];
+}
+
+// element containing x: the lowest id whose barycentric coordinates are all >= -1e-12
+bool locate_point(const poro_ctx* c, const double x[3], int64_t& elem, double xi[3]) {
+    const int64_t ne = (int64_t)c->h_tet.size() / 4;
+    for (int64_t e = 0; e < ne; ++e) {
+        double v[12], jinv[3][3], vol, dins;
+        std::string err;
+        elem_vertices(c, e, v);
+        if (!poro::tet_geometry(v, jinv, vol, dins, err)) continue;
+        double r[3];
+        for (int d = 0; d < 3; ++d) r[d] = x[d] - v[d];
+        for (int j = 0; j < 3; ++j) xi[j] = jinv[j][0] * r[0] + jinv[j][1] * r[1] + jinv[j][2] * r[2];
+        const double b0 = 1.0 - xi[0] - xi[1] - xi[2];
+        if (b0 >= -1e-12 && xi[0] >= -1e-12 && xi[1] >= -1e-12 && xi[2] >= -1e-12) {
+            elem = e;
+            return true;
+        }
+    }
+    return false;
+}
+}  // namespace
+
+poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, double* dt_min_out,
+                              int32_t* cluster_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_clusters: ctx is NULL");
+    if (!c->mesh_mode || !c->have_mat) return fail(c, PORO_ESTATE, "poro_set_clusters: mesh and materials first");
+    if (!(cfl_c > 0.0) || max_clusters < 1) return fail(c, PORO_EINVAL, "poro_set_clusters: bad argument");
+    if (max_clusters != 1) return fail(c, PORO_EUNSUPPORTED, "poro_set_clusters: local time stepping not built");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    const int64_t ne = (int64_t)c->h_tet.size() / 4;
+    const int N = c->N, B = c->B;
+    std::vector<double> detJ(ne);
+    double dtmin = 1e300;
+    for (int64_t e = 0; e < ne; ++e) {
+        double v[12], jinv[3][3], vol, dins, sp;
+        std::string err;
+        elem_vertices(c, e, v);
+        if (!poro::tet_geometry(v, jinv, vol, dins, err) || !poro::max_wave_speed(c->h_mat[e], sp, err))
+            return fail(c, PORO_EINVAL, "poro_set_clusters: element " + std::to_string(e) + ": " + err);
+        detJ[e] = 6.0 * vol;
+        dtmin = std::min(dtmin, cfl_c / (2 * N + 1) * dins / sp);
+    }
+    std::vector<double> ec((size_t)ne * c->stride);
+    for (int64_t e = 0; e < ne; ++e) {
+        double v[12];
+        std::string err;
+        elem_vertices(c, e, v);
+        if (!poro::element_constants(c->ref, v, c->h_mat[e], dtmin, ec.data() + (size_t)e * c->stride, err))
+            return fail(c, PORO_EINVAL, "poro_set_clusters: element " + std::to_string(e) + ": " + err);
+    }
+    poro_status st = upload_population(c, ne, ec);
+    if (st != PORO_OK) return st;
+    cudaMemsetAsync(c->d_q0, 0, (size_t)ne * NQ * B * sizeof(double), c->stream);
+    // faces: neighbour face, vertex permutation, normal, area, flux solvers
+    std::vector<int32_t> nb(4 * ne), tab(4 * ne);
+    std::vector<double> fc(4 * ne), fF((size_t)ne * 4 * 2 * NQ * NQ);
+    std::map<std::string, std::vector<double>> cache;
+    for (int64_t e = 0; e < ne; ++e) {
+        double v[12];
+        elem_vertices(c, e, v);
+        for (int f = 0; f < 4; ++f) {
+            int fv[3], n_ = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != f) fv[n_++] = k;
+            const double* p0 = v + 3 * fv[0];
+            const double* p1 = v + 3 * fv[1];
+            const double* p2 = v + 3 * fv[2];
+            double a[3], b[3], nr[3];
+            for (int d = 0; d < 3; ++d) {
+                a[d] = p1[d] - p0[d];
+                b[d] = p2[d] - p0[d];
+            }
+            nr[0] = a[1] * b[2] - a[2] * b[1];
+            nr[1] = a[2] * b[0] - a[0] * b[2];
+            nr[2] = a[0] * b[1] - a[1] * b[0];
+            const double len = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+            double dotv = 0;
+            for (int d = 0; d < 3; ++d) {
+                nr[d] /= len;
+                dotv += nr[d] * (v[3 * f + d] - p0[d]);
+            }
+            if (dotv > 0)
+                for (int d = 0; d < 3; ++d) nr[d] = -nr[d];
+            fc[4 * e + f] = len / detJ[e];  // 2 |S_f| / |J| with |S_f| = len / 2
+            const int64_t r = c->h_nb[4 * e + f];
+            nb[4 * e + f] = (int32_t)r;
+            tab[4 * e + f] = -1;
+            int kind = r >= 0 ? PORO_FACE_INTERIOR : c->h_tag[4 * e + f];
+            if (r >= 0) {
+                // neighbour face whose vertices equal ours up to one translation
+                double w[12];
+                elem_vertices(c, r, w);
+                double scale = 0;
+                for (int k = 0; k < 12; ++k) scale = std::max(scale, std::fabs(v[k]));
+                const double tol = 1e-9 * (1.0 + scale);
+                for (int h = 0; h < 4 && tab[4 * e + f] < 0; ++h) {
+                    int hv[3], m_ = 0;
+                    for (int k = 0; k < 4; ++k)
+                        if (k != h) hv[m_++] = k;
+                    double sh[3];
+                    for (int d = 0; d < 3; ++d)
+                        sh[d] = (w[3 * hv[0] + d] + w[3 * hv[1] + d] + w[3 * hv[2] + d] - p0[d] - p1[d] - p2[d]) / 3.0;
+                    int perm[3];
+                    bool ok = true;
+                    const double* ps[3] = {p0, p1, p2};
+                    for (int i = 0; i < 3 && ok; ++i) {
+                        perm[i] = -1;
+                        for (int j = 0; j < 3; ++j) {
+                            double dd = 0;
+                            for (int d = 0; d < 3; ++d) dd = std::max(dd, std::fabs(w[3 * hv[j] + d] - ps[i][d] - sh[d]));
+                            if (dd < tol) perm[i] = j;
+                        }
+                        ok = perm[i] >= 0;
+                    }
+                    if (ok && perm[0] != perm[1] && perm[1] != perm[2] && perm[0] != perm[2])
+                        tab[4 * e + f] = f * 24 + h * 6 + poro::face_permutation_index(perm);
+                }
+                if (tab[4 * e + f] < 0)
+                    return fail(c, PORO_EINVAL, "poro_set_clusters: non-conforming face at element " + std::to_string(e));
+            }
+            std::string key(reinterpret_cast<const char*>(&c->h_mat[e]), sizeof(poro_material));
+            if (r >= 0) key.append(reinterpret_cast<const char*>(&c->h_mat[r]), sizeof(poro_material));
+            key.append(reinterpret_cast<const char*>(nr), sizeof(nr));
+            key.append(reinterpret_cast<const char*>(&kind), sizeof(kind));
+            auto itc = cache.find(key);
+            double* dst = fF.data() + ((size_t)(4 * e + f) * 2) * NQ * NQ;
+            if (itc == cache.end()) {
+                std::vector<double> F(2 * NQ * NQ);
+                std::string err;
+                if (!poro::flux_solver(c->h_mat[e], r >= 0 ? &c->h_mat[r] : nullptr, nr, kind, F.data(),
+                                       F.data() + NQ * NQ, err))
+                    return fail(c, PORO_ENUMERIC, "poro_set_clusters: flux at element " + std::to_string(e) + ": " + err);
+                itc = cache.emplace(key, std::move(F)).first;
+            }
+            std::memcpy(dst, itc->second.data(), sizeof(double) * 2 * NQ * NQ);
+        }
+    }
+    // volume CSR: Kv^j_kl = M_ll Khat^j_lk / M_kk
+    std::vector<int32_t> vrow, vcol;
+    std::vector<double> vval, minv(B);
+    for (int j = 0; j < 3; ++j) {
+        for (int k = 0; k < B; ++k) {
+            vrow.push_back((int32_t)vcol.size());
+            for (int l = 0; l < B; ++l) {
+                const double kh = c->ref.khat[((size_t)j * B + l) * B + k];
+                if (kh != 0.0) {
+                    vcol.push_back(l);
+                    vval.push_back(c->ref.mass_diag[l] * kh / c->ref.mass_diag[k]);
+                }
+            }
+        }
+        vrow.push_back((int32_t)vcol.size());
+    }
+    // absolute row offsets per direction: rows of direction j start at j*(B+1)
+    for (int k = 0; k < B; ++k) minv[k] = 1.0 / c->ref.mass_diag[k];
+    std::vector<double> Floc, Fnb;
+    poro::face_matrices(N, Floc, Fnb);
+    cudaError_t er;
+    if ((er = upload((void**)&c->d_nb, nb.data(), nb.size() * sizeof(int32_t))) != cudaSuccess ||
+        (er = upload((void**)&c->d_tab, tab.data(), tab.size() * sizeof(int32_t))) != cudaSuccess ||
+        (er = upload((void**)&c->d_fc, fc.data(), fc.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_fF, fF.data(), fF.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_vrow, vrow.data(), vrow.size() * sizeof(int32_t))) != cudaSuccess ||
+        (er = upload((void**)&c->d_vcol, vcol.data(), vcol.size() * sizeof(int32_t))) != cudaSuccess ||
+        (er = upload((void**)&c->d_vval, vval.data(), vval.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_minv, minv.data(), minv.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_Floc, Floc.data(), Floc.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_Fnb, Fnb.data(), Fnb.size() * sizeof(double))) != cudaSuccess) {
+        free_population(c);
+        return er == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_clusters: out of device memory")
+                                               : cuda_fail(c, er, "poro_set_clusters");
+    }
+    poro::CorrectorData& d = c->cd;
+    d.N = N;
+    d.econst = c->d_econst;
+    d.iout = c->d_iout;
+    d.q = c->d_q0;
+    d.nb = c->d_nb;
+    d.tab = c->d_tab;
+    d.fc = c->d_fc;
+    d.fF = c->d_fF;
+    d.Floc = c->d_Floc;
+    d.Fnb = c->d_Fnb;
+    d.vrow = c->d_vrow;
+    d.vcol = c->d_vcol;
+    d.vval = c->d_vval;
+    d.minv = c->d_minv;
+    c->dt = dtmin;
+    c->t = 0.0;
+    c->have_dofs = true;
+    c->ready = true;
+    c->seis_q.assign(c->rec_elem.size(), std::vector<double>());
+    c->seis_t.clear();
+    if (dt_min_out) *dt_min_out = dtmin;
+    if (cluster_out)
+        for (int64_t e = 0; e < ne; ++e) cluster_out[e] = 0;
+    er = cudaStreamSynchronize(c->stream);
+    if (er != cudaSuccess) return cuda_fail(c, er, "poro_set_clusters");
+    return PORO_OK;
+}
+
+poro_status poro_add_point_source(poro_ctx* c, const double xyz[3], const double w[13], double f0, double t0,
+                                  double amplitude) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_add_point_source: ctx is NULL");
+    if (!c->ready) return fail(c, PORO_ESTATE, "poro_add_point_source: call poro_set_clusters first");
+    if (!xyz || !w || !(f0 > 0.0)) return fail(c, PORO_EINVAL, "poro_add_point_source: bad argument");
+    int64_t e;
+    double xi[3];
+    if (!locate_point(c, xyz, e, xi)) return fail(c, PORO_EINVAL, "poro_add_point_source: point outside the mesh");
+    double v[12], jinv[3][3], vol, dins;
+    std::string err;
+    elem_vertices(c, e, v);
+    poro::tet_geometry(v, jinv, vol, dins, err);
+    std::vector<double> phi(c->B), coef((size_t)NQ * c->B);
+    poro::basis_at(c->N, xi, phi.data());
+    for (int p = 0; p < NQ; ++p)
+        for (int k = 0; k < c->B; ++k)
+            coef[p * c->B + k] = amplitude * w[p] * phi[k] / (6.0 * vol * c->ref.mass_diag[k]);
+    poro_ctx::Source s{e, nullptr, f0, t0};
+    cudaError_t er = upload((void**)&s.d_coef, coef.data(), coef.size() * sizeof(double));
+    if (er != cudaSuccess) return cuda_fail(c, er, "poro_add_point_source");
+    c->sources.push_back(s);
+    return PORO_OK;
+}
+
+poro_status poro_add_receiver(poro_ctx* c, const double xyz[3], int32_t* id_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_add_receiver: ctx is NULL");
+    if (!c->mesh_mode) return fail(c, PORO_ESTATE, "poro_add_receiver: no mesh");
+    if (!xyz) return fail(c, PORO_EINVAL, "poro_add_receiver: NULL");
+    int64_t e;
+    double xi[3];
+    if (!locate_point(c, xyz, e, xi)) return fail(c, PORO_EINVAL, "poro_add_receiver: point outside the mesh");
+    std::vector<double> phi(c->B);
+    poro::basis_at(c->N, xi, phi.data());
+    c->rec_elem.push_back(e);
+    c->rec_phi.insert(c->rec_phi.end(), phi.begin(), phi.end());
+    c->seis_q.emplace_back();
+    if (id_out) *id_out = (int32_t)c->rec_elem.size() - 1;
+    return PORO_OK;
+}
+
+static double ricker_integral(double t, double f0, double t0) {
+    const double a = 3.14159265358979323846 * f0 * (t - t0);
+    return (t - t0) * std::exp(-a * a);
+}
+
+poro_status poro_advance(poro_ctx* c, double t_end) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_advance: ctx is NULL");
+    if (!c->ready) return fail(c, PORO_ESTATE, "poro_advance: call poro_set_clusters first");
+    cudaSetDevice(c->device);
+    const int64_t n_steps = (int64_t)std::floor((t_end - c->t) / c->dt + 1e-9);
+    if (n_steps <= 0) return PORO_OK;
+    const int nrec = (int)c->rec_elem.size();
+    int64_t* d_re = nullptr;
+    double *d_rp = nullptr, *d_seis = nullptr;
+    cudaError_t er = cudaSuccess;
+    if (nrec > 0) {
+        if ((er = upload((void**)&d_re, c->rec_elem.data(), nrec * sizeof(int64_t))) != cudaSuccess ||
+            (er = upload((void**)&d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
+            (er = cudaMalloc((void**)&d_seis, (size_t)nrec * n_steps * NQ * sizeof(double))) != cudaSuccess) {
+            dfree(d_re);
+            dfree(d_rp);
+            return cuda_fail(c, er, "poro_advance");
+        }
+    }
+    int rc = 0;
+    for (int64_t k = 0; k < n_steps && rc == 0; ++k) {
+        poro_status s = dispatch_predict(c, 0, c->n_elem, c->d_q0, nullptr, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
+        if (s != PORO_OK) {
+            rc = -1;
+            break;
+        }
+        rc = poro::launch_corrector(c->cd, nullptr, c->n_elem, c->stream);
+        const double t0 = c->t + k * c->dt, t1 = t0 + c->dt;
+        for (auto& src : c->sources)
+            if (rc == 0)
+                rc = poro::launch_point_source(c->N, c->d_q0, src.elem, src.d_coef,
+                                               ricker_integral(t1, src.f0, src.t0) - ricker_integral(t0, src.f0, src.t0),
+                                               c->stream);
+        if (rc == 0 && nrec > 0)
+            rc = poro::launch_receivers(c->N, c->d_q0, nrec, d_re, d_rp, d_seis + (size_t)k * NQ, n_steps * NQ,
+                                        c->stream);
+    }
+    if (rc == 0) er = cudaStreamSynchronize(c->stream);
+    std::vector<double> h;
+    if (rc == 0 && er == cudaSuccess && nrec > 0) {
+        h.resize((size_t)nrec * n_steps * NQ);
+        er = cudaMemcpy(h.data(), d_seis, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    dfree(d_re);
+    dfree(d_rp);
+    dfree(d_seis);
+    if (rc == -1) return PORO_ECUDA;
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch");
+    if (er != cudaSuccess) return cuda_fail(c, er, "poro_advance");
+    for (int r = 0; r < nrec; ++r)
+        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * n_steps * NQ,
+                            h.begin() + (size_t)(r + 1) * n_steps * NQ);
+    for (int64_t k = 0; k < n_steps; ++k) c->seis_t.push_back(c->t + (k + 1) * c->dt);
+    c->t += n_steps * c->dt;
+    c->have_pred = true;
+    return PORO_OK;
+}
+
+poro_status poro_correct(poro_ctx* c, int32_t cluster) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_correct: ctx is NULL");
+    if (!c->ready || !c->have_pred) return fail(c, PORO_ESTATE, "poro_correct: mesh set-up and a predictor first");
+    if (cluster != -1 && cluster != 0) return fail(c, PORO_EINVAL, "poro_correct: no such cluster");
+    cudaSetDevice(c->device);
+    int rc = poro::launch_corrector(c->cd, nullptr, c->n_elem, c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_correct");
+    return PORO_OK;
+}
+
+poro_status poro_get_dofs(poro_ctx* c, double* Q_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_dofs: ctx is NULL");
+    if (!c->d_q0 || !c->have_dofs) return fail(c, PORO_ESTATE, "poro_get_dofs: no DOFs");
+    if (!Q_out) return fail(c, PORO_EINVAL, "poro_get_dofs: NULL");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpyAsync(Q_out, c->d_q0, (size_t)c->n_elem * NQ * c->B * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "poro_get_dofs");
+    return PORO_OK;
+}
+
+poro_status poro_get_seismogram(poro_ctx* c, int32_t rec, int64_t cap, double* t_out, double* q_out, int64_t* n_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_seismogram: ctx is NULL");
+    if (rec < 0 || rec >= (int32_t)c->rec_elem.size()) return fail(c, PORO_EINVAL, "poro_get_seismogram: no such receiver");
+    const int64_t n = (int64_t)c->seis_t.size();
+    if (n_out) *n_out = n;
+    const int64_t m = std::min(n, cap);
+    if (m > 0 && (!t_out || !q_out)) return fail(c, PORO_EINVAL, "poro_get_seismogram: NULL output");
+    for (int64_t k = 0; k < m; ++k) {
+        t_out[k] = c->seis_t[k];
+        for (int p = 0; p < NQ; ++p) q_out[k * NQ + p] = c->seis_q[rec][k * NQ + p];
+    }
+    return PORO_OK;
+}
+
+poro_status poro_get_time(const poro_ctx* c, double* t, double* dt) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_time: ctx is NULL");
+    if (t) *t = c->t;
+    if (dt) *dt = c->dt;
+    return PORO_OK;
+}
+
+poro_status poro_flux_matrices(const poro_material* mL, const poro_material* mR, const double n[3], int32_t kind,
+                               double* Fm, double* Fp) {
+    if (!mL || !n || !Fm || !Fp) return fail(nullptr, PORO_EINVAL, "poro_flux_matrices: NULL argument");
+    if (kind == PORO_FACE_INTERIOR && !mR) return fail(nullptr, PORO_EINVAL, "poro_flux_matrices: interior needs mR");
+    std::string err;
+    if (!poro::flux_solver(*mL, mR, n, kind, Fm, Fp, err)) return fail(nullptr, PORO_EINVAL, err);
     return PORO_OK;
 }
 

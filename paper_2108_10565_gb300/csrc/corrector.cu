@@ -1,0 +1,152 @@
+// Corrector of the ADER-DG scheme (Eq. semi_discrete integrated over one
+// time step, Section "Temporal discretisation with ADER"), point source and
+// receivers, binary64.
+//
+// For element e with time-integrated predictor I (13 x B):
+//   dQ_pk = sum_j sum_l Kv^j_kl (A^j I)_pl              volume, Kv^j = M^{-1} K^{jT}
+//         + (E I)_pk                                    Darcy source term
+//         - sum_f c_f / M_kk [ sum_l Floc^f_kl (F^- I^e)_pl
+//                            + sum_l Fnb^{f,h,s}_kl (F^+ I^nb)_pl ]   Godunov flux
+// with A^j = A^{j*} / dt and E = E* / dt from the element constants,
+// c_f = 2 |S_f| / |J|, Floc^f / Fnb the face mass matrices of the local face
+// and of the (neighbour face h, vertex permutation s) pair.  One CTA per
+// element; the DOFs are updated in place (neighbours read I only).
+#include <cuda_runtime.h>
+
+#include "poro_internal.h"
+
+namespace poro {
+namespace {
+
+constexpr int CNT = 128;
+
+__global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, const int32_t* elems, int64_t count) {
+    const int N = D.N, B = n_modes(N), QB = NQ * B;
+    const int stride = elem_const_stride(N);
+    extern __shared__ double sm[];
+    double* I = sm;            // [13][B]
+    double* Y = I + QB;        // [13][B]
+    double* dQ = Y + QB;       // [13][B]
+    double* In = dQ + QB;      // [13][B]
+    __shared__ double F[NQ * NQ];
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const int64_t e = elems ? elems[it] : it;
+        const double* ec = D.econst + e * stride;
+        const double dt = ec[ec_scalars(N) + 2];
+        const double ev = ec[ec_scalars(N)] / dt, gv = ec[ec_scalars(N) + 1] / dt;
+        for (int i = threadIdx.x; i < QB; i += CNT) {
+            I[i] = D.iout[e * QB + i];
+            dQ[i] = 0.0;
+        }
+        __syncthreads();
+        // volume: X^j = A^j I (54-entry star pattern), dQ += Kv^j X^j
+        for (int j = 0; j < 3; ++j) {
+            const double* sj = ec + j * STAR_NNZ;
+            for (int l = threadIdx.x; l < B; l += CNT) {
+                double qv[NQ], acc[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    qv[q] = I[q * B + l];
+                    acc[q] = 0.0;
+                }
+#pragma unroll
+                for (int n = 0; n < STAR_NNZ; ++n) acc[star_row(n)] = fma(sj[n], qv[star_col(n)], acc[star_row(n)]);
+#pragma unroll
+                for (int p = 0; p < NQ; ++p) Y[p * B + l] = acc[p] / dt;
+            }
+            __syncthreads();
+            const int32_t* vr = D.vrow + j * (B + 1);
+            for (int i = threadIdx.x; i < QB; i += CNT) {
+                const int p = i / B, k = i % B;
+                double acc = 0.0;
+                for (int n = vr[k]; n < vr[k + 1]; ++n) acc = fma(D.vval[n], Y[p * B + D.vcol[n]], acc);
+                dQ[i] += acc;
+            }
+            __syncthreads();
+        }
+        // Darcy source term E I: u rows from u_f, u_f rows from u_f
+        for (int i = threadIdx.x; i < 6 * B; i += CNT) {
+            const int r = i / B, k = i % B;
+            if (r < 3) dQ[(QU + r) * B + k] += gv * I[(QUF + r) * B + k];
+            else dQ[(QUF + r - 3) * B + k] += ev * I[(QUF + r - 3) * B + k];
+        }
+        __syncthreads();
+        // faces
+        for (int f = 0; f < 4; ++f) {
+            const int64_t nbr = D.nb[e * 4 + f];
+            const double cf = D.fc[e * 4 + f];
+            const double* Fm = D.fF + ((e * 4 + f) * 2) * NQ * NQ;
+            for (int side = 0; side < (nbr >= 0 ? 2 : 1); ++side) {
+                const double* src = I;
+                if (side == 1) {
+                    for (int i = threadIdx.x; i < QB; i += CNT) In[i] = D.iout[nbr * QB + i];
+                    src = In;
+                }
+                for (int i = threadIdx.x; i < NQ * NQ; i += CNT) F[i] = Fm[side * NQ * NQ + i];
+                __syncthreads();
+                for (int i = threadIdx.x; i < QB; i += CNT) {
+                    const int p = i / B, l = i % B;
+                    double acc = 0.0;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) acc = fma(F[p * NQ + q], src[q * B + l], acc);
+                    Y[i] = acc;
+                }
+                __syncthreads();
+                const double* Fmat = side == 0 ? D.Floc + (size_t)f * B * B
+                                               : D.Fnb + (size_t)D.tab[e * 4 + f] * B * B;
+                for (int i = threadIdx.x; i < QB; i += CNT) {
+                    const int p = i / B, k = i % B;
+                    const double* row = Fmat + (size_t)k * B;
+                    double acc = 0.0;
+                    for (int l = 0; l < B; ++l) acc = fma(__ldg(row + l), Y[p * B + l], acc);
+                    dQ[i] -= cf * D.minv[k] * acc;
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < QB; i += CNT) D.q[e * QB + i] += dQ[i];
+        __syncthreads();
+    }
+}
+
+__global__ void point_source_kernel(int QB, double* q, int64_t elem, const double* coef, double amp) {
+    for (int i = threadIdx.x; i < QB; i += blockDim.x) q[elem * QB + i] += amp * coef[i];
+}
+
+// out[r * stride_out + p] = sum_l Q[e_r][p][l] phi_r[l]
+__global__ void receiver_kernel(int B, const double* q, int32_t nrec, const int64_t* elems, const double* phi,
+                                double* out, int64_t stride_out) {
+    const int r = blockIdx.x, p = threadIdx.x;
+    if (r >= nrec || p >= NQ) return;
+    const double* qe = q + elems[r] * (int64_t)(NQ * B) + p * B;
+    double acc = 0.0;
+    for (int l = 0; l < B; ++l) acc = fma(qe[l], phi[r * B + l], acc);
+    out[r * stride_out + p] = acc;
+}
+
+}  // namespace
+
+int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+    if (count <= 0) return 0;
+    const int B = n_modes(d.N);
+    const size_t smem = sizeof(double) * 4 * NQ * B;
+    cudaError_t err = cudaFuncSetAttribute(corrector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
+    corrector_kernel<<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count);
+    return (int)cudaGetLastError();
+}
+
+int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream) {
+    point_source_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(NQ * n_modes(N), q, elem, coef, amp);
+    return (int)cudaGetLastError();
+}
+
+int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems, const double* phi, double* out,
+                     int64_t stride_out, void* stream) {
+    if (nrec <= 0) return 0;
+    receiver_kernel<<<nrec, 32, 0, (cudaStream_t)stream>>>(n_modes(N), q, nrec, elems, phi, out, stride_out);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace poro

@@ -96,6 +96,18 @@ bool invert_small(int n, const double* a, double* ainv);
 bool element_constants(const ReferenceData& ref, const double* v12, const poro_material& mat,
                        double dt, double* out, std::string& err);
 
+// ----- corrector set-up (mesh.cpp) -----
+// Godunov flux solver matrices of one face: A_n^L q* = Fm q_L + Fp q_R.
+// kind: PORO_FACE_INTERIOR (mR required), PORO_FACE_FREE_SURFACE, PORO_FACE_ABSORBING.
+bool flux_solver(const poro_material& mL, const poro_material* mR, const double n[3], int kind, double* Fm,
+                 double* Fp, std::string& err);
+// phi_l(xi) for all l (singularity-free homogenised recurrences)
+void basis_at(int N, const double xi[3], double* phi);
+// Floc[4][B][B] = int_face phi_k phi_l, Fnb[4][4][6][B][B] = int_face phi_k(L) phi_l(R)
+// for local face f, neighbour face h, vertex permutation s
+void face_matrices(int N, std::vector<double>& Floc, std::vector<double>& Fnb);
+int face_permutation_index(const int p[3]);
+
 // ----- device side (kernels) -----
 struct DeviceReference {
     int N = 0;
@@ -155,6 +167,29 @@ struct CtxView {
 };
 bool ctx_view(const poro_ctx* c, CtxView& v);
 void ctx_set_error(poro_ctx* c, const std::string& msg);
+
+// Corrector (Eq. semi_discrete integrated over one step) for `count`
+// elements starting at `first` of the mesh.
+struct CorrectorData {
+    int N = 0;
+    const double* econst = nullptr;   // [ne][stride] (stars with dt, e, g, dt)
+    const double* iout = nullptr;     // [ne][13][B] time-integrated predictor
+    double* q = nullptr;              // [ne][13][B] DOFs, updated in place
+    const int32_t* nb = nullptr;      // [ne][4]
+    const int32_t* tab = nullptr;     // [ne][4] neighbour table index f*24 + h*6 + s, or -1
+    const double* fc = nullptr;       // [ne][4] 2 |S_f| / |J|
+    const double* fF = nullptr;       // [ne][4][2][169] flux solver matrices
+    const double* Floc = nullptr;     // [4][B][B]
+    const double* Fnb = nullptr;      // [96][B][B]
+    const int32_t* vrow = nullptr;    // volume CSR rows [3][B+1] (absolute)
+    const int32_t* vcol = nullptr;
+    const double* vval = nullptr;     // Kv^j_kl = M_ll Khat^j_lk / M_kk
+    const double* minv = nullptr;     // [B] 1 / M_kk
+};
+int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
+int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
+int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems, const double* phi, double* out,
+                     int64_t stride_out, void* stream);
 
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).

@@ -1,0 +1,96 @@
+"""GPU parity of full ADER-DG runs (predictor + corrector + source +
+receivers, global time stepping) against the oracle's plain run.
+
+Tolerance: seismograms <= 1e-9 relative L2 per (receiver, quantity) over all
+samples (absolute, relative to the largest trace of the receiver, for traces
+that stay ~0), final DOFs <= 1e-10 relative."""
+import numpy as np
+import pytest
+
+from oracle import corrector
+from paper_2108_10565_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_10565_gb300 import _lib
+
+    return _lib
+
+
+def _gpu_run(L, mesh, mats, N, n_steps, source, receivers, Q0=None, precision=0):
+    ctx = L.poro_create(0, N, precision)
+    try:
+        L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+        L.poro_set_materials(ctx, mats)
+        dt, _ = L.poro_set_clusters(ctx, 0.5, 1)
+        if Q0 is not None:
+            L.poro_set_dofs(ctx, Q0)
+        if source is not None:
+            L.poro_add_point_source(ctx, source["x"], source["w"], source["f0"], source["t0"], source["amplitude"])
+        for x in receivers:
+            L.poro_add_receiver(ctx, x)
+        L.poro_advance(ctx, (n_steps + 0.5) * dt)
+        seis = [L.poro_get_seismogram(ctx, r) for r in range(len(receivers))]
+        return dt, L.poro_get_dofs(ctx), seis
+    finally:
+        L.poro_destroy(ctx)
+
+
+def _check_seis(seis_gpu, seis_ref, tol=1e-9):
+    for r, (t, q) in enumerate(seis_gpu):
+        ref = seis_ref[r]
+        assert q.shape == ref.shape
+        scale = np.abs(ref).max()
+        for p in range(13):
+            nr = np.linalg.norm(ref[:, p])
+            err = np.linalg.norm(q[:, p] - ref[:, p])
+            if nr > 1e-6 * scale:
+                assert err <= tol * nr, f"receiver {r} quantity {p}: {err / nr:.3e}"
+            else:
+                assert err <= tol * scale
+
+
+def test_periodic_point_source_run(L):
+    """The small periodic scenario: unit cube, 384 tetrahedra, N = 2, pressure
+    point source at the centre (a mesh vertex), 4 receivers, 50 steps."""
+    sc = inputs.config0_scenario()
+    sim = corrector.GTSSimulation(sc["mesh"], sc["materials"], sc["N"], source=sc["source"],
+                                  receivers=sc["receivers"])
+    Qref, seis_ref = sim.run(sc["Q0"], sc["n_steps"])
+    dt, Q, seis = _gpu_run(L, sc["mesh"], sc["materials"], sc["N"], sc["n_steps"], sc["source"], sc["receivers"])
+    assert dt == pytest.approx(sim.dt, rel=1e-13)
+    assert len(seis[0][0]) == sc["n_steps"]
+    np.testing.assert_allclose(seis[0][0], sim.dt * np.arange(1, sc["n_steps"] + 1), rtol=1e-12)
+    _check_seis(seis, seis_ref)
+    assert np.linalg.norm(Q - Qref) <= 1e-10 * np.linalg.norm(Qref)
+    assert np.abs(seis_ref).max() > 0  # the source reached the receivers
+
+
+def test_heterogeneous_bounded_run(L):
+    """Two materials (an inviscid stiff half and a viscous soft half), free
+    surface on top, absorbing elsewhere, random initial data: exercises the
+    interface Riemann solver, both boundary fluxes and every face
+    permutation of the Kuhn mesh."""
+    N, n_steps = 2, 12
+    mesh = inputs.kuhn_box_mesh((3, 3, 2), lo=(0, 0, -1), hi=(1.5, 1.5, 0), periodic=(False, False, False),
+                                tags={"z+": 1})
+    ne = mesh["tets"].shape[0]
+    cz = mesh["vertices"][mesh["tets"]].mean(axis=1)[:, 2]
+    top = inputs.REFERENCE_MATERIAL.copy()
+    bottom = inputs.REFERENCE_MATERIAL * np.array([1.4, 1.1, 1.5, 1.5, 1, 0.8, 1, 1, 1, 0])
+    mats = np.where((cz > -0.5)[:, None], top[None, :], bottom[None, :])
+    rng = np.random.default_rng(11)
+    Q0 = rng.standard_normal((ne, 13, 10))
+    rec = [np.array([0.7, 0.8, -0.3]), np.array([0.4, 0.5, -0.9])]
+    sim = corrector.GTSSimulation(mesh, mats, N, receivers=rec)
+    Qref, seis_ref = sim.run(Q0, n_steps)
+    dt, Q, seis = _gpu_run(L, mesh, mats, N, n_steps, None, rec, Q0=Q0)
+    _check_seis(seis, seis_ref)
+    assert np.linalg.norm(Q - Qref) <= 1e-10 * np.linalg.norm(Qref)

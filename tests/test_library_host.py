@@ -87,3 +87,27 @@ def test_invalid_inputs_rejected(L):
     with pytest.raises(L.PoroError) as ex:
         L.poro_reference_matrices(7)
     assert ex.value.status == L.PORO_EUNSUPPORTED
+
+
+def test_flux_matrices_match_oracle(L):
+    """The library's flux solvers (matrix sign function) against the
+    oracle's (characteristic decomposition), in the impedance-scaled frame."""
+    from oracle import flux
+
+    rng = np.random.default_rng(0)
+    mats = inputs.perturbed_materials(rng, 3)
+    mats[1, 9] = 0.0  # inviscid neighbour
+    for n in ([1, 0, 0], [0, 0, -1], np.array([1, 2, -2]) / 3.0):
+        n = np.array(n, float)
+        An = flux.normal_jacobian(inputs.material_dict(mats[0]), n)
+        s = np.ones(13)
+        s[[0, 1, 2, 3, 4, 5, 9]] = np.sqrt(np.abs(An[[0, 1, 2, 3, 4, 5, 9]]).max() /
+                                           np.abs(An[[6, 7, 8, 10, 11, 12]]).max())
+        sc = s[None, :] / s[:, None]
+        amax = np.abs(An * sc).max()
+        for kind, name in ((0, "interior"), (1, "free_surface"), (2, "absorbing")):
+            Fm, Fp = L.poro_flux_matrices(mats[0], mats[1] if kind == 0 else None, n, kind)
+            om, op = flux.flux_matrices(inputs.material_dict(mats[0]),
+                                        inputs.material_dict(mats[1]) if kind == 0 else None, n, name)
+            assert np.abs((Fm - om) * sc).max() < 1e-13 * amax
+            assert np.abs((Fp - op) * sc).max() < 1e-13 * amax
