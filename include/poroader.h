@@ -194,13 +194,16 @@ poro_status poro_set_mesh(poro_ctx* ctx, int64_t n_vert, const double* xyz, int6
 poro_status poro_set_materials(poro_ctx* ctx, const poro_material* mat);
 
 /* Time steps (Section "Temporal discretisation with ADER"): every element's
- * CFL step cfl_c/(2N+1) d/v; with max_clusters = 1 (global time stepping) all
- * elements use the smallest.  Builds the element constants, the face data
- * (neighbour face, vertex permutation, outward normal, area) and the Godunov
- * flux solvers of every face, and zeroes the DOFs.  dt_min_out (nullable)
- * receives the step, cluster_out[n_elem] (nullable) the cluster of each
- * element.  Errors: PORO_ESTATE, PORO_EINVAL (non-conforming face),
- * PORO_EUNSUPPORTED (max_clusters > 1: local time stepping not built). */
+ * CFL step dt_e = cfl_c/(2N+1) d/v (cfl_c = 0.5 in the paper).  Clustered
+ * local time stepping with rate 2: element e joins cluster
+ * c_e = min(max_clusters - 1, floor(log2(dt_e / dt_min))) and steps with
+ * 2^c_e dt_min; max_clusters = 1 is global time stepping with dt_min.
+ * Builds the element constants, the face data (neighbour face, vertex
+ * permutation, outward normal, area), the Godunov flux solvers of every face
+ * and the buffers of the cluster interfaces, and zeroes the DOFs.
+ * dt_min_out (nullable) receives dt_min, cluster_out[n_elem] (nullable) the
+ * cluster of each element.  Errors: PORO_ESTATE, PORO_EINVAL
+ * (non-conforming face, max_clusters outside 1..16). */
 poro_status poro_set_clusters(poro_ctx* ctx, double cfl_c, int32_t max_clusters, double* dt_min_out,
                               int32_t* cluster_out);
 
@@ -217,12 +220,17 @@ poro_status poro_add_point_source(poro_ctx* ctx, const double xyz[3], const doub
  * every step.  *id_out receives its index. */
 poro_status poro_add_receiver(poro_ctx* ctx, const double xyz[3], int32_t* id_out);
 
-/* Advance from the current time by whole steps while t + dt <= t_end:
- * predictor of every element (the context's precision, Algorithm 3), the
- * corrector of Eq. semi_discrete over the step (volume, Darcy source term,
- * Godunov flux with the neighbours' time-integrated predictors), point
- * sources and receivers.  Synchronises at the end and collects the new
- * seismogram samples. */
+/* Advance by whole steps of the largest cluster (2^(C-1) dt_min) while
+ * t <= t_end.  Ticks k of dt_min: (A) the clusters whose step starts at k
+ * predict (the context's precision, Algorithm 3) and add their
+ * time-integrated predictor to the buffers of larger neighbours; (B) the
+ * clusters whose step ends at k + 1 correct (Eq. semi_discrete over their
+ * step: volume, Darcy source term, Godunov flux with each neighbour's trace
+ * integrated over the same interval: its own integral, the buffered sum of
+ * its sub-steps, or its predictor integrated over the sub-interval), then
+ * point sources (over the element's own step) and receivers (sampled at
+ * the end of every step of their element).  Synchronises at the end and
+ * collects the new seismogram samples. */
 poro_status poro_advance(poro_ctx* ctx, double t_end);
 
 /* One corrector pass of all elements from the last predictor (low-level). */

@@ -212,3 +212,96 @@ class GTSSimulation:
             for i, (e, phi) in enumerate(self.rec):
                 seis[i, n] = Q[e] @ phi
         return Q, seis
+
+
+class LTSSimulation(GTSSimulation):
+    """Clustered local time stepping (Section "Temporal discretisation with
+    ADER": clustered LTS; the paper gives no algorithm, this is the reading).
+
+    Element e has its CFL step dt_e; dt_min = min dt_e; its cluster is
+    c_e = min(C - 1, floor(log2(dt_e / dt_min))) and it steps with
+    dt_c = 2^c dt_min.  Ticks k of length dt_min run:
+      (A) every cluster with k mod 2^c = 0 predicts from its current DOFs
+          (own interval [t_k, t_k + dt_c]); an element whose neighbour lies in
+          a larger cluster L adds its time-integrated predictor I to a buffer
+          of level L (reset when k mod 2^L = 0);
+      (B) every cluster with (k + 1) mod 2^c = 0 corrects over its interval
+          [t_{k+1} - dt_c, t_{k+1}].  The neighbour's trace is integrated over
+          exactly that interval: same cluster -> its I; smaller cluster -> its
+          buffer (the chronological sum of its sub-step integrals); larger
+          cluster -> dt_L sum_s Qt_s int_a^b chi_s over the sub-interval
+          [a, b] of its reference time interval.
+    Sources act over each element's own interval; receivers sample at the
+    end of every step of their element.  With C = 1 this is global time
+    stepping."""
+
+    def __init__(self, mesh, materials, N, max_clusters, cfl=0.5, source=None, receivers=()):
+        super().__init__(mesh, materials, N, cfl, source, receivers)
+        self.C = max_clusters
+        dte = np.array([geometry.cfl_dt(self.vert[e], self.mats[e], N, cfl) for e in range(self.ne)])
+        self.dt_min = dte.min()
+        self.cl = np.minimum(max_clusters - 1, np.floor(np.log2(dte / self.dt_min) + 1e-12)).astype(int)
+        self.dtc = self.dt_min * 2.0 ** np.arange(max_clusters)
+        # buffer levels each element needs (larger neighbour clusters)
+        self.levels = [sorted({int(self.cl[r]) for r in self.nb[e] if r >= 0 and self.cl[r] > self.cl[e]})
+                       for e in range(self.ne)]
+
+    def run(self, Q0, n_cycles):
+        """n_cycles steps of the largest cluster; returns final Q and, per
+        receiver, (times, samples [n][13])."""
+        N, C = self.N, self.C
+        Q = np.array(Q0, float)
+        Qt = np.zeros((self.ne, NQ, self.B, self.T))
+        I = np.zeros((self.ne, NQ, self.B))
+        buf = {}
+        seis = [([], []) for _ in self.rec]
+        rec_of = {}
+        for i, (e, phi) in enumerate(self.rec):
+            rec_of.setdefault(e, []).append(i)
+        clusters = [np.nonzero(self.cl == c)[0] for c in range(C)]
+        K = n_cycles * 2 ** (C - 1)
+        for k in range(K):
+            for c in range(C):
+                els = clusters[c]
+                if k % 2 ** c or len(els) == 0:
+                    continue
+                dt = self.dtc[c]
+                Qt[els] = predict_alg3_batch(N, self.Aj[els] * dt, self.E[els] * dt, Q[els])
+                I[els] = dt * Qt[els][:, :, :, 0]
+                for e in els:
+                    for L in self.levels[e]:
+                        if k % 2 ** L == 0:
+                            buf[(e, L)] = I[e].copy()
+                        else:
+                            buf[(e, L)] += I[e]
+            for c in range(C):
+                els = clusters[c]
+                if (k + 1) % 2 ** c or len(els) == 0:
+                    continue
+                ks = k + 1 - 2 ** c
+                for e in els:
+                    dQ = sum((self.Aj[e, j] @ I[e]) @ self.K[j] for j in range(3)) / self.M[None, :]
+                    dQ += self.E[e] @ I[e]
+                    for (area, phiL, phiR, Fm, Fp, r) in self.face[e]:
+                        trace = Fm @ (I[e] @ phiL.T)
+                        if r >= 0:
+                            cr = self.cl[r]
+                            if cr == c:
+                                Ir = I[r]
+                            elif cr < c:
+                                Ir = buf[(r, c)]
+                            else:
+                                m = (ks // 2 ** cr) * 2 ** cr
+                                a, b = (ks - m) / 2 ** cr, (k + 1 - m) / 2 ** cr
+                                Ir = self.dtc[cr] * np.einsum("qls,s->ql", Qt[r], timebasis.chi_integrals(N, a, b))
+                            trace += Fp @ (Ir @ phiR.T)
+                        dQ -= (2.0 * area / self.detJ[e]) * (trace * self.qw[None, :]) @ phiL / self.M[None, :]
+                    Q[e] += dQ
+                    if self.src is not None and self.src[0] == e:
+                        _, coef, f0, t0 = self.src
+                        Q[e] += coef * (ricker_antiderivative((k + 1) * self.dt_min, f0, t0)
+                                        - ricker_antiderivative(ks * self.dt_min, f0, t0))
+                    for i in rec_of.get(e, []):
+                        seis[i][0].append((k + 1) * self.dt_min)
+                        seis[i][1].append(Q[e] @ self.rec[i][1])
+        return Q, [(np.array(t), np.array(q)) for t, q in seis]

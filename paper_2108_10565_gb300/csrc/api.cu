@@ -55,7 +55,15 @@ struct poro_ctx {
     std::vector<int64_t> rec_elem;
     std::vector<double> rec_phi;
     std::vector<std::vector<double>> seis_q;   // per receiver [n][13]
-    std::vector<double> seis_t;
+    std::vector<std::vector<double>> seis_t;   // per receiver sample times
+    // clustered local time stepping
+    int C = 1;
+    int64_t tick = 0;                          // ticks of dt (the smallest step) done
+    std::vector<int32_t> h_cl;                 // cluster of each element
+    std::vector<std::vector<int32_t>> cl_elems;
+    std::vector<int32_t*> d_cl_elems;
+    int32_t *d_cl = nullptr, *d_slot = nullptr;
+    double* d_buf = nullptr;
 };
 
 namespace {
@@ -98,6 +106,11 @@ void free_mesh_device(poro_ctx* c) {
     dfree(c->d_minv);
     for (auto& s : c->sources) dfree(s.d_coef);
     c->sources.clear();
+    for (auto& p : c->d_cl_elems) dfree(p);
+    c->d_cl_elems.clear();
+    dfree(c->d_cl);
+    dfree(c->d_slot);
+    dfree(c->d_buf);
     c->ready = false;
 }
 
@@ -409,9 +422,9 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     }
     if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
     if (c->prec == PORO_FP64) {
-        rc = poro::launch_stp_fp64(c->dref, count, q0, ec, qt, iout, st);
+        rc = poro::launch_stp_fp64(c->dref, nullptr, count, q0, ec, qt, iout, st);
     } else {
-        rc = poro::launch_stp_mixed(c->mref, c->refine, count, q0, ec, qt, iout, st);
+        rc = poro::launch_stp_mixed(c->mref, c->refine, nullptr, count, q0, ec, qt, iout, st);
     }
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "predict: kernel launch");
     return PORO_OK;
@@ -585,6 +598,7 @@ poro_status poro_set_mesh(poro_ctx* c, int64_t n_vert, const double* xyz, int64_
     c->seis_q.clear();
     c->seis_t.clear();
     c->t = 0.0;
+    c->tick = 0;
     return PORO_OK;
 }
 
@@ -636,13 +650,13 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_clusters: ctx is NULL");
     if (!c->mesh_mode || !c->have_mat) return fail(c, PORO_ESTATE, "poro_set_clusters: mesh and materials first");
     if (!(cfl_c > 0.0) || max_clusters < 1) return fail(c, PORO_EINVAL, "poro_set_clusters: bad argument");
-    if (max_clusters != 1) return fail(c, PORO_EUNSUPPORTED, "poro_set_clusters: local time stepping not built");
+    if (max_clusters > 16) return fail(c, PORO_EINVAL, "poro_set_clusters: at most 16 clusters");
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     free_population(c);
     const int64_t ne = (int64_t)c->h_tet.size() / 4;
     const int N = c->N, B = c->B;
-    std::vector<double> detJ(ne);
+    std::vector<double> detJ(ne), dte(ne);
     double dtmin = 1e300;
     for (int64_t e = 0; e < ne; ++e) {
         double v[12], jinv[3][3], vol, dins, sp;
@@ -651,14 +665,23 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
         if (!poro::tet_geometry(v, jinv, vol, dins, err) || !poro::max_wave_speed(c->h_mat[e], sp, err))
             return fail(c, PORO_EINVAL, "poro_set_clusters: element " + std::to_string(e) + ": " + err);
         detJ[e] = 6.0 * vol;
-        dtmin = std::min(dtmin, cfl_c / (2 * N + 1) * dins / sp);
+        dte[e] = cfl_c / (2 * N + 1) * dins / sp;
+        dtmin = std::min(dtmin, dte[e]);
+    }
+    // rate-2 clusters: c_e = min(C - 1, floor(log2(dt_e / dt_min))), dt_c = 2^c dt_min
+    const int C = max_clusters;
+    c->h_cl.assign(ne, 0);
+    for (int64_t e = 0; e < ne; ++e) {
+        int ce = (int)std::floor(std::log2(dte[e] / dtmin) + 1e-12);
+        c->h_cl[e] = std::max(0, std::min(C - 1, ce));
     }
     std::vector<double> ec((size_t)ne * c->stride);
     for (int64_t e = 0; e < ne; ++e) {
         double v[12];
         std::string err;
         elem_vertices(c, e, v);
-        if (!poro::element_constants(c->ref, v, c->h_mat[e], dtmin, ec.data() + (size_t)e * c->stride, err))
+        const double dt_e = std::ldexp(dtmin, c->h_cl[e]);
+        if (!poro::element_constants(c->ref, v, c->h_mat[e], dt_e, ec.data() + (size_t)e * c->stride, err))
             return fail(c, PORO_EINVAL, "poro_set_clusters: element " + std::to_string(e) + ": " + err);
     }
     poro_status st = upload_population(c, ne, ec);
@@ -798,15 +821,50 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     d.vcol = c->d_vcol;
     d.vval = c->d_vval;
     d.minv = c->d_minv;
+    // clusters: element lists, buffer slots of (element, larger neighbour level)
+    c->C = C;
+    c->cl_elems.assign(C, std::vector<int32_t>());
+    for (int64_t e = 0; e < ne; ++e) c->cl_elems[c->h_cl[e]].push_back((int32_t)e);
+    std::vector<int32_t> slot((size_t)ne * C, -1);
+    int32_t nslot = 0;
+    for (int64_t e = 0; e < ne; ++e)
+        for (int f = 0; f < 4; ++f) {
+            const int64_t r = c->h_nb[4 * e + f];
+            if (r >= 0 && c->h_cl[r] > c->h_cl[e] && slot[e * C + c->h_cl[r]] < 0) slot[e * C + c->h_cl[r]] = nslot++;
+        }
+    for (int k = 0; k < C; ++k) {
+        int32_t* d = nullptr;
+        if (!c->cl_elems[k].empty() &&
+            (er = upload((void**)&d, c->cl_elems[k].data(), c->cl_elems[k].size() * sizeof(int32_t))) != cudaSuccess) {
+            free_population(c);
+            return cuda_fail(c, er, "poro_set_clusters");
+        }
+        c->d_cl_elems.push_back(d);
+    }
+    if (C > 1) {
+        if ((er = upload((void**)&c->d_cl, c->h_cl.data(), ne * sizeof(int32_t))) != cudaSuccess ||
+            (er = upload((void**)&c->d_slot, slot.data(), slot.size() * sizeof(int32_t))) != cudaSuccess ||
+            (er = cudaMalloc((void**)&c->d_buf, (size_t)std::max(nslot, 1) * NQ * B * sizeof(double))) != cudaSuccess) {
+            free_population(c);
+            return er == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_clusters: out of device memory")
+                                                   : cuda_fail(c, er, "poro_set_clusters");
+        }
+    }
+    d.C = C;
+    d.cl = c->d_cl;
+    d.slot = c->d_slot;
+    d.buf = c->d_buf;
+    d.qt = c->d_qt;
     c->dt = dtmin;
     c->t = 0.0;
+    c->tick = 0;
     c->have_dofs = true;
     c->ready = true;
     c->seis_q.assign(c->rec_elem.size(), std::vector<double>());
-    c->seis_t.clear();
+    c->seis_t.assign(c->rec_elem.size(), std::vector<double>());
     if (dt_min_out) *dt_min_out = dtmin;
     if (cluster_out)
-        for (int64_t e = 0; e < ne; ++e) cluster_out[e] = 0;
+        for (int64_t e = 0; e < ne; ++e) cluster_out[e] = c->h_cl[e];
     er = cudaStreamSynchronize(c->stream);
     if (er != cudaSuccess) return cuda_fail(c, er, "poro_set_clusters");
     return PORO_OK;
@@ -848,6 +906,7 @@ poro_status poro_add_receiver(poro_ctx* c, const double xyz[3], int32_t* id_out)
     c->rec_elem.push_back(e);
     c->rec_phi.insert(c->rec_phi.end(), phi.begin(), phi.end());
     c->seis_q.emplace_back();
+    c->seis_t.emplace_back();
     if (id_out) *id_out = (int32_t)c->rec_elem.size() - 1;
     return PORO_OK;
 }
@@ -861,8 +920,12 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_advance: ctx is NULL");
     if (!c->ready) return fail(c, PORO_ESTATE, "poro_advance: call poro_set_clusters first");
     cudaSetDevice(c->device);
-    const int64_t n_steps = (int64_t)std::floor((t_end - c->t) / c->dt + 1e-9);
-    if (n_steps <= 0) return PORO_OK;
+    const int C = c->C;
+    const int64_t cycle = (int64_t)1 << (C - 1);            // ticks per step of the largest cluster
+    const double dt_max = std::ldexp(c->dt, C - 1);
+    const int64_t n_cycles = (int64_t)std::floor((t_end - c->t) / dt_max + 1e-9);
+    if (n_cycles <= 0) return PORO_OK;
+    const int64_t ticks = n_cycles * cycle;
     const int nrec = (int)c->rec_elem.size();
     int64_t* d_re = nullptr;
     double *d_rp = nullptr, *d_seis = nullptr;
@@ -870,47 +933,71 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
     if (nrec > 0) {
         if ((er = upload((void**)&d_re, c->rec_elem.data(), nrec * sizeof(int64_t))) != cudaSuccess ||
             (er = upload((void**)&d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
-            (er = cudaMalloc((void**)&d_seis, (size_t)nrec * n_steps * NQ * sizeof(double))) != cudaSuccess) {
+            (er = cudaMalloc((void**)&d_seis, (size_t)nrec * ticks * NQ * sizeof(double))) != cudaSuccess) {
             dfree(d_re);
             dfree(d_rp);
             return cuda_fail(c, er, "poro_advance");
         }
     }
+    std::vector<int64_t> nsamp(nrec, 0);
+    std::vector<std::vector<double>> tsamp(nrec);
     int rc = 0;
-    for (int64_t k = 0; k < n_steps && rc == 0; ++k) {
-        poro_status s = dispatch_predict(c, 0, c->n_elem, c->d_q0, nullptr, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
-        if (s != PORO_OK) {
-            rc = -1;
-            break;
+    const bool want_qt = C > 1;
+    for (int64_t k = c->tick; k < c->tick + ticks && rc == 0; ++k) {
+        // (A) predictors of the clusters whose step starts at tick k
+        for (int cl = 0; cl < C && rc == 0; ++cl) {
+            if (k % ((int64_t)1 << cl) || c->cl_elems[cl].empty()) continue;
+            const int32_t* el = C > 1 ? c->d_cl_elems[cl] : nullptr;
+            const int64_t cnt = (int64_t)c->cl_elems[cl].size();
+            if (c->prec == PORO_FP64)
+                rc = poro::launch_stp_fp64(c->dref, el, cnt, c->d_q0, c->d_econst, want_qt ? c->d_qt : nullptr,
+                                           c->d_iout, c->stream);
+            else
+                rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
+                                            want_qt ? c->d_qt : nullptr, c->d_iout, c->stream);
+            if (rc == 0 && C > 1)
+                rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, c->stream);
         }
-        rc = poro::launch_corrector(c->cd, nullptr, c->n_elem, c->stream);
-        const double t0 = c->t + k * c->dt, t1 = t0 + c->dt;
-        for (auto& src : c->sources)
-            if (rc == 0)
-                rc = poro::launch_point_source(c->N, c->d_q0, src.elem, src.d_coef,
-                                               ricker_integral(t1, src.f0, src.t0) - ricker_integral(t0, src.f0, src.t0),
-                                               c->stream);
-        if (rc == 0 && nrec > 0)
-            rc = poro::launch_receivers(c->N, c->d_q0, nrec, d_re, d_rp, d_seis + (size_t)k * NQ, n_steps * NQ,
+        // (B) correctors of the clusters whose step ends at tick k + 1
+        for (int cl = 0; cl < C && rc == 0; ++cl) {
+            const int64_t len = (int64_t)1 << cl;
+            if ((k + 1) % len || c->cl_elems[cl].empty()) continue;
+            c->cd.tick = k;
+            rc = poro::launch_corrector(c->cd, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(),
                                         c->stream);
+            const double t0 = (double)(k + 1 - len) * c->dt, t1 = (double)(k + 1) * c->dt;
+            for (auto& src : c->sources)
+                if (rc == 0 && c->h_cl[src.elem] == cl)
+                    rc = poro::launch_point_source(c->N, c->d_q0, src.elem, src.d_coef,
+                                                   ricker_integral(t1, src.f0, src.t0) - ricker_integral(t0, src.f0, src.t0),
+                                                   c->stream);
+            for (int r = 0; r < nrec && rc == 0; ++r) {
+                if (c->h_cl[c->rec_elem[r]] != cl) continue;
+                rc = poro::launch_receivers(c->N, c->d_q0, 1, d_re + r, d_rp + (size_t)r * c->B,
+                                            d_seis + ((size_t)r * ticks + nsamp[r]) * NQ, 0, c->stream);
+                ++nsamp[r];
+                tsamp[r].push_back(t1);
+            }
+        }
     }
     if (rc == 0) er = cudaStreamSynchronize(c->stream);
     std::vector<double> h;
     if (rc == 0 && er == cudaSuccess && nrec > 0) {
-        h.resize((size_t)nrec * n_steps * NQ);
+        h.resize((size_t)nrec * ticks * NQ);
         er = cudaMemcpy(h.data(), d_seis, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
     }
     dfree(d_re);
     dfree(d_rp);
     dfree(d_seis);
-    if (rc == -1) return PORO_ECUDA;
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch");
     if (er != cudaSuccess) return cuda_fail(c, er, "poro_advance");
-    for (int r = 0; r < nrec; ++r)
-        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * n_steps * NQ,
-                            h.begin() + (size_t)(r + 1) * n_steps * NQ);
-    for (int64_t k = 0; k < n_steps; ++k) c->seis_t.push_back(c->t + (k + 1) * c->dt);
-    c->t += n_steps * c->dt;
+    for (int r = 0; r < nrec; ++r) {
+        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * ticks * NQ,
+                            h.begin() + ((size_t)r * ticks + nsamp[r]) * NQ);
+        c->seis_t[r].insert(c->seis_t[r].end(), tsamp[r].begin(), tsamp[r].end());
+    }
+    c->tick += ticks;
+    c->t = (double)c->tick * c->dt;
     c->have_pred = true;
     return PORO_OK;
 }
@@ -940,12 +1027,12 @@ poro_status poro_get_dofs(poro_ctx* c, double* Q_out) {
 poro_status poro_get_seismogram(poro_ctx* c, int32_t rec, int64_t cap, double* t_out, double* q_out, int64_t* n_out) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_seismogram: ctx is NULL");
     if (rec < 0 || rec >= (int32_t)c->rec_elem.size()) return fail(c, PORO_EINVAL, "poro_get_seismogram: no such receiver");
-    const int64_t n = (int64_t)c->seis_t.size();
+    const int64_t n = (int64_t)c->seis_t[rec].size();
     if (n_out) *n_out = n;
     const int64_t m = std::min(n, cap);
     if (m > 0 && (!t_out || !q_out)) return fail(c, PORO_EINVAL, "poro_get_seismogram: NULL output");
     for (int64_t k = 0; k < m; ++k) {
-        t_out[k] = c->seis_t[k];
+        t_out[k] = c->seis_t[rec][k];
         for (int p = 0; p < NQ; ++p) q_out[k * NQ + p] = c->seis_q[rec][k * NQ + p];
     }
     return PORO_OK;

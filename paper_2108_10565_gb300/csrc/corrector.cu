@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
     double* dQ = Y + QB;       // [13][B]
     double* In = dQ + QB;      // [13][B]
     __shared__ double F[NQ * NQ];
+    __shared__ double wts[MAX_N + 1];
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
         const int64_t e = elems ? elems[it] : it;
         const double* ec = D.econst + e * stride;
@@ -79,7 +80,46 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
             for (int side = 0; side < (nbr >= 0 ? 2 : 1); ++side) {
                 const double* src = I;
                 if (side == 1) {
-                    for (int i = threadIdx.x; i < QB; i += CNT) In[i] = D.iout[nbr * QB + i];
+                    // the neighbour's trace integrated over this element's interval
+                    const int c = D.cl ? D.cl[e] : 0, cr = D.cl ? D.cl[nbr] : 0;
+                    if (cr == c) {
+                        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = D.iout[nbr * QB + i];
+                    } else if (cr < c) {
+                        const double* b = D.buf + (int64_t)D.slot[nbr * D.C + c] * QB;
+                        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = b[i];
+                    } else {
+                        // larger neighbour: dt_r sum_s Qt_s int_a^b chi_s over the sub-interval
+                        const int T = N + 1;
+                        if (threadIdx.x == 0) {
+                            const int64_t ks = D.tick + 1 - ((int64_t)1 << c);
+                            const int64_t m = (ks >> cr) << cr;
+                            const double a = (double)(ks - m) / (double)((int64_t)1 << cr);
+                            const double bb = (double)(D.tick + 1 - m) / (double)((int64_t)1 << cr);
+                            // int_a^b P_s(2 tau - 1) dtau = (1/2) [ (P_{s+1} - P_{s-1}) / (2s+1) ]_{2a-1}^{2b-1}
+                            double P0[MAX_N + 3], P1[MAX_N + 3];
+                            const double x0 = 2 * a - 1, x1 = 2 * bb - 1;
+                            P0[0] = 1;
+                            P0[1] = x0;
+                            P1[0] = 1;
+                            P1[1] = x1;
+                            for (int n = 1; n <= T; ++n) {
+                                P0[n + 1] = ((2 * n + 1) * x0 * P0[n] - n * P0[n - 1]) / (n + 1);
+                                P1[n + 1] = ((2 * n + 1) * x1 * P1[n] - n * P1[n - 1]) / (n + 1);
+                            }
+                            wts[0] = 0.5 * (x1 - x0);
+                            for (int sidx = 1; sidx < T; ++sidx)
+                                wts[sidx] = 0.5 * ((P1[sidx + 1] - P1[sidx - 1]) - (P0[sidx + 1] - P0[sidx - 1])) /
+                                            (2 * sidx + 1);
+                        }
+                        __syncthreads();
+                        const double dtr = D.econst[nbr * stride + ec_scalars(N) + 2];
+                        const double* qr = D.qt + nbr * (int64_t)QB * T;
+                        for (int i = threadIdx.x; i < QB; i += CNT) {
+                            double acc = 0.0;
+                            for (int sidx = 0; sidx < T; ++sidx) acc = fma(qr[i * T + sidx], wts[sidx], acc);
+                            In[i] = dtr * acc;
+                        }
+                    }
                     src = In;
                 }
                 for (int i = threadIdx.x; i < NQ * NQ; i += CNT) F[i] = Fm[side * NQ * NQ + i];
@@ -109,6 +149,23 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
     }
 }
 
+// buffers of the sub-step integrals for larger neighbours: level L restarts
+// at ticks that are multiples of 2^L
+__global__ void lts_buffer_kernel(int QB, int C, const int32_t* elems, int64_t count, const int32_t* slot,
+                                  const double* iout, double* buf, int64_t tick) {
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const int64_t e = elems[it];
+        for (int L = 0; L < C; ++L) {
+            const int sl = slot[e * C + L];
+            if (sl < 0) continue;
+            const bool reset = (tick & (((int64_t)1 << L) - 1)) == 0;
+            double* b = buf + (int64_t)sl * QB;
+            const double* I = iout + e * QB;
+            for (int i = threadIdx.x; i < QB; i += blockDim.x) b[i] = reset ? I[i] : b[i] + I[i];
+        }
+    }
+}
+
 __global__ void point_source_kernel(int QB, double* q, int64_t elem, const double* coef, double amp) {
     for (int i = threadIdx.x; i < QB; i += blockDim.x) q[elem * QB + i] += amp * coef[i];
 }
@@ -134,6 +191,15 @@ int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count
     if (err != cudaSuccess) return (int)err;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
     corrector_kernel<<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count);
+    return (int)cudaGetLastError();
+}
+
+int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const int32_t* slot, const double* iout,
+                       double* buf, int64_t tick, void* stream) {
+    if (count <= 0) return 0;
+    const int64_t grid = count < 65536 ? count : 65536;
+    lts_buffer_kernel<<<(unsigned)grid, 128, 0, (cudaStream_t)stream>>>(NQ * n_modes(N), C, elems, count, slot, iout,
+                                                                       buf, tick);
     return (int)cudaGetLastError();
 }
 

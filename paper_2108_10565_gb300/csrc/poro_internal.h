@@ -130,8 +130,8 @@ struct MixedReference {
 
 // Launch the mixed-precision predictor (binary32 sweeps, `refine` residual
 // corrections in double-binary32) for `count` elements.
-int launch_stp_mixed(const MixedReference& ref, int refine, int64_t count, const double* q0,
-                     const double* econst, double* qt, double* iout, void* stream);
+int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count,
+                     const double* q0, const double* econst, double* qt, double* iout, void* stream);
 
 // Dense-LU comparator: reference data and per-batch scratch (factors,
 // pivots, permutation, equilibration factors, singularity flag).
@@ -185,7 +185,16 @@ struct CorrectorData {
     const int32_t* vcol = nullptr;
     const double* vval = nullptr;     // Kv^j_kl = M_ll Khat^j_lk / M_kk
     const double* minv = nullptr;     // [B] 1 / M_kk
+    // clustered local time stepping (all nullptr / 1 for global time stepping)
+    int C = 1;                        // number of clusters
+    const int32_t* cl = nullptr;      // [ne] cluster of each element
+    const int32_t* slot = nullptr;    // [ne][C] buffer slot of (element, larger level) or -1
+    const double* buf = nullptr;      // [slots][13][B] buffered sub-step integrals
+    const double* qt = nullptr;       // [ne][13][B][T] full predictors (larger neighbours)
+    int64_t tick = 0;                 // tick k of the correction (interval ends at k + 1)
 };
+int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const int32_t* slot, const double* iout,
+                       double* buf, int64_t tick, void* stream);
 int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
 int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
 int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems, const double* phi, double* out,
@@ -193,7 +202,8 @@ int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems,
 
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
-int launch_stp_fp64(const DeviceReference& ref, int64_t count, const double* q0,
+// `elems` (nullable): element index list; outputs are indexed by element.
+int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
                     const double* econst, double* qt, double* iout, void* stream);
 
 }  // namespace poro

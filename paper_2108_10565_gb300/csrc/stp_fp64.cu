@@ -27,6 +27,7 @@ namespace poro {
 namespace {
 
 struct K1Params {
+    const int32_t* elems;  // optional element index list (LTS clusters); nullptr: elements 0..count-1
     const double* q0;
     const double* econst;
     double* qt;
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params
     double* zin = sm + S::OFF_ZIN;
     const int tid = threadIdx.x;
 
-    for (int64_t e = blockIdx.x; e < P.count; e += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
+        const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
         const double* q0 = P.q0 + e * (int64_t)(NQ * B);
         const double* ec = P.econst + e * (int64_t)P.stride;
         // element constants: star[162], zinv_uf[T*T], e, g, dt, pad are contiguous
@@ -88,10 +90,11 @@ __global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params
 }
 
 template <int N>
-int launch_n(const DeviceReference& ref, int64_t count, const double* q0, const double* econst,
-             double* qt, double* iout, void* stream) {
+int launch_n(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+             const double* econst, double* qt, double* iout, void* stream) {
     using S = K1Shape<N>;
     K1Params P;
+    P.elems = elems;
     P.q0 = q0;
     P.econst = econst;
     P.qt = qt;
@@ -116,15 +119,15 @@ int launch_n(const DeviceReference& ref, int64_t count, const double* q0, const 
 
 }  // namespace
 
-int launch_stp_fp64(const DeviceReference& ref, int64_t count, const double* q0, const double* econst,
-                    double* qt, double* iout, void* stream) {
+int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                    const double* econst, double* qt, double* iout, void* stream) {
     switch (ref.N) {
-        case 1: return launch_n<1>(ref, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, count, q0, econst, qt, iout, stream);
+        case 1: return launch_n<1>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_n<2>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 3: return launch_n<3>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 4: return launch_n<4>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 5: return launch_n<5>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 6: return launch_n<6>(ref, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -30,6 +30,7 @@ namespace poro {
 namespace {
 
 struct K2Params {
+    const int32_t* elems;     // optional element index list (LTS clusters)
     const double* q0;
     const double* econst;
     double* qt;
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(K2Shape<N, REF>::NT, REF == 2 ? 1 : 2) stp_mix
     }
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
 
-    for (int64_t e = blockIdx.x; e < P.count; e += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
+        const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
         const double* q0 = P.q0 + e * (int64_t)(NQ * B);
         const double* ec = P.econst + e * (int64_t)P.stride;
         for (int i = tid; i < 3 * STAR_NNZ; i += NT) {
@@ -283,10 +285,11 @@ __global__ void __launch_bounds__(K2Shape<N, REF>::NT, REF == 2 ? 1 : 2) stp_mix
 }
 
 template <int N, int REF>
-int launch_nr(const MixedReference& ref, int64_t count, const double* q0, const double* econst, double* qt,
-              double* iout, void* stream) {
+int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, const double* q0, const double* econst,
+              double* qt, double* iout, void* stream) {
     using S = K2Shape<N, REF>;
     K2Params P;
+    P.elems = elems;
     P.q0 = q0;
     P.econst = econst;
     P.qt = qt;
@@ -313,27 +316,27 @@ int launch_nr(const MixedReference& ref, int64_t count, const double* q0, const 
 }
 
 template <int N>
-int launch_n(const MixedReference& ref, int refine, int64_t count, const double* q0, const double* econst,
-             double* qt, double* iout, void* stream) {
+int launch_n(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
+             const double* econst, double* qt, double* iout, void* stream) {
     switch (refine) {
-        case 0: return launch_nr<N, 0>(ref, count, q0, econst, qt, iout, stream);
-        case 1: return launch_nr<N, 1>(ref, count, q0, econst, qt, iout, stream);
-        case 2: return launch_nr<N, 2>(ref, count, q0, econst, qt, iout, stream);
+        case 0: return launch_nr<N, 0>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_nr<N, 1>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_nr<N, 2>(ref, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-int launch_stp_mixed(const MixedReference& ref, int refine, int64_t count, const double* q0, const double* econst,
-                     double* qt, double* iout, void* stream) {
+int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
+                     const double* econst, double* qt, double* iout, void* stream) {
     switch (ref.base->N) {
-        case 1: return launch_n<1>(ref, refine, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, refine, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, refine, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, refine, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, refine, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, refine, count, q0, econst, qt, iout, stream);
+        case 1: return launch_n<1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_n<2>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 3: return launch_n<3>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 4: return launch_n<4>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 5: return launch_n<5>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 6: return launch_n<6>(ref, refine, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }

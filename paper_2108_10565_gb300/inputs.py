@@ -121,7 +121,7 @@ SEED_CFG0 = 2108105650
 
 
 def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, True, True),
-                  tags=None):
+                  tags=None, coords=None):
     """Structured tetrahedral mesh: an n[0] x n[1] x n[2] grid of boxes, each
     cut into the 6 Kuhn tetrahedra around its main diagonal (a
     translation-invariant split, so the mesh is conforming, also across
@@ -131,7 +131,8 @@ def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, Tru
     [ne][4] (element across face i, the face opposite local vertex i; -1 on
     a boundary), face_tag [ne][4] (0 interior/periodic, 1 free surface,
     2 absorbing)).  `tags` maps a boundary side ('x-', 'x+', ..., 'z+') to a
-    tag for non-periodic directions (default absorbing)."""
+    tag for non-periodic directions (default absorbing).  `coords` (optional)
+    gives the n[a] + 1 grid coordinates of each axis (graded meshes)."""
     n = (n, n, n) if np.isscalar(n) else tuple(n)
     for ax in range(3):
         if periodic[ax] and n[ax] < 3:
@@ -146,7 +147,11 @@ def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, Tru
     def vid(i, j, k):
         return (i * (ny + 1) + j) * (nz + 1) + k
 
-    vert = np.stack(np.broadcast_arrays(lo[0] + gi * h[0], lo[1] + gj * h[1], lo[2] + gk * h[2]), -1).reshape(-1, 3)
+    if coords is None:
+        coords = [lo[a] + np.arange(n[a] + 1) * h[a] for a in range(3)]
+    coords = [np.asarray(c, float) for c in coords]
+    assert all(len(coords[a]) == n[a] + 1 for a in range(3))
+    vert = np.stack(np.broadcast_arrays(coords[0][gi], coords[1][gj], coords[2][gk]), -1).reshape(-1, 3)
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
     tets = []
     for i in range(nx):

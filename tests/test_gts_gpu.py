@@ -94,3 +94,49 @@ def test_heterogeneous_bounded_run(L):
     dt, Q, seis = _gpu_run(L, mesh, mats, N, n_steps, None, rec, Q0=Q0)
     _check_seis(seis, seis_ref)
     assert np.linalg.norm(Q - Qref) <= 1e-10 * np.linalg.norm(Qref)
+
+
+def _graded(periodic_x):
+    coords = [np.array([0, 0.05, 0.1, 0.2, 0.4, 0.8, 1.6]), np.linspace(0, 2.4, 4), np.linspace(0, 2.4, 4)]
+    return inputs.kuhn_box_mesh((6, 3, 3), periodic=(periodic_x, True, True), coords=coords,
+                                tags={"x-": 1, "x+": 2})
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lts_three_clusters_run(L, precision):
+    """Clustered LTS with 3 rate-2 clusters on a graded mesh (free surface at
+    x = 0, absorbing at x = 1.6, periodic in y and z), viscous material, a
+    point source in the fine region and receivers in three clusters, two
+    cycles of the largest step; FP64 and the mixed (refined) predictor."""
+    mesh = _graded(False)
+    ne = mesh["tets"].shape[0]
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    src = dict(x=np.array([0.07, 1.1, 1.3]), w=np.eye(13)[9], f0=2000.0, t0=2e-4, amplitude=1e6)
+    rec = [np.array([0.03, 0.5, 0.5]), np.array([0.3, 1.2, 0.9]), np.array([1.2, 1.0, 2.0])]
+    Q0 = 1e-3 * np.random.default_rng(5).standard_normal((ne, 13, 10))
+    sim = corrector.LTSSimulation(mesh, mats, 2, 3, source=src, receivers=rec)
+    assert len(set(sim.cl.tolist())) == 3
+    Qref, seis_ref = sim.run(Q0, 2)
+    ctx = L.poro_create(0, 2, precision)
+    try:
+        L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+        L.poro_set_materials(ctx, mats)
+        dt, cl = L.poro_set_clusters(ctx, 0.5, 3, n_elem=ne)
+        assert dt == pytest.approx(sim.dt_min, rel=1e-13)
+        assert np.array_equal(cl, sim.cl)
+        L.poro_set_dofs(ctx, Q0)
+        L.poro_add_point_source(ctx, src["x"], src["w"], src["f0"], src["t0"], src["amplitude"])
+        for x in rec:
+            L.poro_add_receiver(ctx, x)
+        L.poro_advance(ctx, 2 * 4 * dt * 1.0000001)
+        t, _ = L.poro_get_time(ctx)
+        assert t == pytest.approx(8 * sim.dt_min, rel=1e-12)
+        Q = L.poro_get_dofs(ctx)
+        seis = [L.poro_get_seismogram(ctx, r) for r in range(len(rec))]
+    finally:
+        L.poro_destroy(ctx)
+    tol = 1e-9
+    for (tg, qg), (tr, qr) in zip(seis, seis_ref):
+        np.testing.assert_allclose(tg, tr, rtol=1e-12)
+    _check_seis(seis, [qr for _, qr in seis_ref], tol=tol)
+    assert np.linalg.norm(Q - Qref) <= 1e-10 * np.linalg.norm(Qref)
