@@ -233,6 +233,10 @@ poro_status poro_add_receiver(poro_ctx* ctx, const double xyz[3], int32_t* id_ou
  * collects the new seismogram samples. */
 poro_status poro_advance(poro_ctx* ctx, double t_end);
 
+/* Replay a CUDA graph of one cycle (default on) or enqueue every cycle's
+ * launches from the host (off); results are identical. */
+poro_status poro_set_graphs(poro_ctx* ctx, int32_t on);
+
 /* One corrector pass of all elements from the last predictor (low-level). */
 poro_status poro_correct(poro_ctx* ctx, int32_t cluster);
 
@@ -301,6 +305,19 @@ poro_status poro_lu_release(poro_ctx* ctx);
 poro_status poro_lu_predict_static(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
                                    double* Qt_dev, double* I_dev, void* stream);
 
+/* Autotuner of the predictor kernels: times the CTA-size variants (0: 256
+ * threads at N >= 5, 128 at N = 4, 64 at N <= 3; 1: the alternative) on the
+ * first `sample` elements of the loaded population (<= 0: all), three timed
+ * runs after two warm-ups each, and keeps the fastest for this context.
+ * *variant_out (nullable) receives the choice, ms_out[2] (nullable) the
+ * mean milliseconds per run of each variant.  The DOFs are not changed; the
+ * context's predictor buffers are overwritten.  The paper has no counterpart
+ * (its kernels are generated per architecture). */
+poro_status poro_autotune(poro_ctx* ctx, int64_t sample, int32_t* variant_out, double* ms_out);
+
+/* Select a predictor CTA-size variant explicitly (0 or 1). */
+poro_status poro_set_variant(poro_ctx* ctx, int32_t variant);
+
 /* Floating-point operations one predictor of this context performs, counted
  * from the structural non-zeros the kernels touch (Khat blocks, the 54-entry
  * star pattern, the (N+1)^2 time solves): used for rooflines.  flops_out[0]
@@ -308,6 +325,71 @@ poro_status poro_lu_predict_static(poro_ctx* ctx, int64_t first, int64_t count, 
  * (refinement modes), flops_out[2] = residual operations (refinement modes,
  * per sweep). */
 poro_status poro_flop_count(const poro_ctx* ctx, int32_t refine_sweeps, double* flops_out);
+
+/* ------------------------------------------------------ serving */
+/* Continuous-batching server for ensembles of independent simulations (the
+ * paper has no counterpart; it runs one simulation per job).  Requests are
+ * admitted in arrival order while a slot is free and the sum of the admitted
+ * requests' device-memory footprints (poro_footprint_bytes) fits the
+ * budget; each admitted request runs on its own context and CUDA stream on a
+ * worker thread, so requests admitted while others run overlap with them on
+ * the device.  A failing request (invalid input, footprint above the whole
+ * budget, an error in its own calls) ends in PORO_REQ_FAILED without
+ * affecting the others.  All calls are thread-safe. */
+typedef struct poro_server poro_server;
+
+enum { PORO_REQ_QUEUED = 0, PORO_REQ_RUNNING = 1, PORO_REQ_DONE = 2, PORO_REQ_FAILED = 3, PORO_REQ_CANCELLED = 4 };
+
+/* One simulation: the arguments of poro_set_mesh, poro_set_materials,
+ * poro_set_clusters, poro_add_point_source (n_sources of them) and
+ * poro_add_receiver (n_receivers), optional initial DOFs Q0 (nullable), run
+ * from t = 0 by whole steps of the largest cluster to t_end.  All arrays are
+ * copied by poro_submit. */
+typedef struct {
+    int32_t degree_N, precision, refine_sweeps, max_clusters;
+    double cfl_c, t_end;
+    int64_t n_vert;
+    const double* xyz;
+    int64_t n_elem;
+    const int64_t* tet;
+    const int64_t* nb;
+    const int32_t* face_tag;
+    const poro_material* mat;
+    const double* Q0;
+    int32_t n_sources, n_receivers;
+    const double* src_xyz;    /* [n_sources][3] */
+    const double* src_w;      /* [n_sources][13] */
+    const double* src_f0;     /* [n_sources] */
+    const double* src_t0;     /* [n_sources] */
+    const double* src_amp;    /* [n_sources] */
+    const double* rec_xyz;    /* [n_receivers][3] */
+} poro_scenario;
+
+/* Server on `device` with a device-memory budget in bytes and at most
+ * max_slots concurrently running requests. */
+poro_status poro_server_create(int device, size_t hbm_budget, int32_t max_slots, poro_server** out);
+/* Cancel queued and running requests, wait for the workers, free. */
+poro_status poro_server_destroy(poro_server* srv);
+const char* poro_server_last_error(poro_server* srv);
+/* Copy the scenario and queue it; *ticket identifies the request. */
+poro_status poro_submit(poro_server* srv, const poro_scenario* sc, uint64_t* ticket);
+/* State (PORO_REQ_*) and simulated time reached. */
+poro_status poro_poll(poro_server* srv, uint64_t ticket, int32_t* state, double* sim_time);
+/* Block until the request finished (DONE, FAILED or CANCELLED) or timeout_ms
+ * passed (< 0: no limit; PORO_ETIMEOUT then). */
+poro_status poro_wait(poro_server* srv, uint64_t ticket, int32_t timeout_ms, int32_t* state);
+/* Seismogram of receiver rec of a DONE request (as poro_get_seismogram). */
+poro_status poro_fetch(poro_server* srv, uint64_t ticket, int32_t rec, int64_t cap, double* t_out, double* q_out,
+                       int64_t* n_out);
+/* Wall-clock seconds from submission to admission, from admission to the
+ * end, and in total (time to seismogram) of a finished request. */
+poro_status poro_request_times(poro_server* srv, uint64_t ticket, double* queued_s, double* run_s, double* total_s);
+/* Error text of a FAILED request. */
+poro_status poro_request_error(poro_server* srv, uint64_t ticket, char* buf, size_t cap);
+/* Cancel: a queued request is dropped, a running one stops at its next chunk. */
+poro_status poro_cancel(poro_server* srv, uint64_t ticket);
+/* Device bytes the server reserves for a request of this size. */
+poro_status poro_footprint_bytes(int degree_N, int64_t n_elem, int32_t max_clusters, int32_t n_receivers, size_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,19 @@ _c = ctypes
 _i32, _i64, _dbl, _vp = _c.c_int32, _c.c_int64, _c.c_double, _c.c_void_p
 _pd = _c.POINTER(_c.c_double)
 
+class poro_scenario(ctypes.Structure):
+    _fields_ = [("degree_N", ctypes.c_int32), ("precision", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32),
+                ("max_clusters", ctypes.c_int32), ("cfl_c", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("n_vert", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_elem", ctypes.c_int64),
+                ("tet", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("face_tag", ctypes.c_void_p),
+                ("mat", ctypes.c_void_p), ("Q0", ctypes.c_void_p), ("n_sources", ctypes.c_int32),
+                ("n_receivers", ctypes.c_int32), ("src_xyz", ctypes.c_void_p), ("src_w", ctypes.c_void_p),
+                ("src_f0", ctypes.c_void_p), ("src_t0", ctypes.c_void_p), ("src_amp", ctypes.c_void_p),
+                ("rec_xyz", ctypes.c_void_p)]
+
+
+PORO_REQ_QUEUED, PORO_REQ_RUNNING, PORO_REQ_DONE, PORO_REQ_FAILED, PORO_REQ_CANCELLED = 0, 1, 2, 3, 4
+
 # (name, restype, argtypes) for every symbol declared in include/poroader.h
 SIGNATURES = [
     ("poro_create", _i32, [_c.c_int, _c.c_int, _c.c_int, _c.POINTER(_vp)]),
@@ -55,6 +68,20 @@ SIGNATURES = [
     ("poro_get_seismogram", _i32, [_vp, _i32, _i64, _vp, _vp, _c.POINTER(_i64)]),
     ("poro_get_time", _i32, [_vp, _pd, _pd]),
     ("poro_flux_matrices", _i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    ("poro_autotune", _i32, [_vp, _i64, _c.POINTER(_i32), _vp]),
+    ("poro_set_variant", _i32, [_vp, _i32]),
+    ("poro_set_graphs", _i32, [_vp, _i32]),
+    ("poro_server_create", _i32, [_c.c_int, _c.c_size_t, _i32, _c.POINTER(_vp)]),
+    ("poro_server_destroy", _i32, [_vp]),
+    ("poro_server_last_error", _c.c_char_p, [_vp]),
+    ("poro_submit", _i32, [_vp, _c.POINTER(poro_scenario), _c.POINTER(_c.c_uint64)]),
+    ("poro_poll", _i32, [_vp, _c.c_uint64, _c.POINTER(_i32), _pd]),
+    ("poro_wait", _i32, [_vp, _c.c_uint64, _i32, _c.POINTER(_i32)]),
+    ("poro_fetch", _i32, [_vp, _c.c_uint64, _i32, _i64, _vp, _vp, _c.POINTER(_i64)]),
+    ("poro_request_times", _i32, [_vp, _c.c_uint64, _pd, _pd, _pd]),
+    ("poro_request_error", _i32, [_vp, _c.c_uint64, _c.c_char_p, _c.c_size_t]),
+    ("poro_cancel", _i32, [_vp, _c.c_uint64]),
+    ("poro_footprint_bytes", _i32, [_c.c_int, _i64, _i32, _i32, _c.POINTER(_c.c_size_t)]),
 ]
 
 
@@ -295,7 +322,122 @@ def poro_flux_matrices(matL, matR, n, kind):
 PORO_FACE_INTERIOR, PORO_FACE_FREE_SURFACE, PORO_FACE_ABSORBING = 0, 1, 2
 
 
+def poro_autotune(ctx, sample=0):
+    v = _i32()
+    ms = (ctypes.c_double * 2)()
+    _check(lib().poro_autotune(ctx, sample, ctypes.byref(v), ms), ctx)
+    return v.value, list(ms)
+
+
+def poro_set_graphs(ctx, on):
+    return _check(lib().poro_set_graphs(ctx, 1 if on else 0), ctx)
+
+
+def poro_set_variant(ctx, variant):
+    return _check(lib().poro_set_variant(ctx, variant), ctx)
+
+
 def poro_flop_count(ctx, refine_sweeps=0):
     f = (ctypes.c_double * 3)()
     _check(lib().poro_flop_count(ctx, refine_sweeps, f), ctx)
     return list(f)
+
+
+# ------------------------------------------------------------ serving
+def _srv_check(status, srv):
+    if status != PORO_OK:
+        raise PoroError(status, lib().poro_server_last_error(srv).decode())
+    return status
+
+
+def poro_server_create(device, hbm_budget, max_slots):
+    h = _vp()
+    _srv_check(lib().poro_server_create(device, hbm_budget, max_slots, ctypes.byref(h)), None)
+    return h.value
+
+
+def poro_server_destroy(srv):
+    return lib().poro_server_destroy(srv)
+
+
+def make_scenario(N, mesh, materials, t_end, precision=PORO_FP64, max_clusters=1, refine_sweeps=1, cfl_c=0.5,
+                  sources=(), receivers=(), Q0=None):
+    """Build a poro_scenario; returns (struct, keepalive) -- keep the second
+    alive until poro_submit returned (it copies the arrays)."""
+    keep = dict(xyz=_f64(mesh["vertices"]), tet=np.ascontiguousarray(mesh["tets"], dtype=np.int64),
+                nb=np.ascontiguousarray(mesh["neighbors"], dtype=np.int64),
+                tag=np.ascontiguousarray(mesh["face_tag"], dtype=np.int32), mat=_f64(materials))
+    sc = poro_scenario()
+    sc.degree_N, sc.precision, sc.refine_sweeps, sc.max_clusters = N, precision, refine_sweeps, max_clusters
+    sc.cfl_c, sc.t_end = cfl_c, t_end
+    sc.n_vert, sc.xyz = keep["xyz"].shape[0], _ptr(keep["xyz"])
+    sc.n_elem, sc.tet, sc.nb = keep["tet"].shape[0], _ptr(keep["tet"]), _ptr(keep["nb"])
+    sc.face_tag, sc.mat = _ptr(keep["tag"]), _ptr(keep["mat"])
+    if Q0 is not None:
+        keep["q0"] = _f64(Q0)
+        sc.Q0 = _ptr(keep["q0"])
+    if sources:
+        keep["sx"] = _f64([s["x"] for s in sources])
+        keep["sw"] = _f64([s["w"] for s in sources])
+        keep["sf"] = _f64([s["f0"] for s in sources])
+        keep["st"] = _f64([s["t0"] for s in sources])
+        keep["sa"] = _f64([s.get("amplitude", 1.0) for s in sources])
+        sc.n_sources = len(sources)
+        sc.src_xyz, sc.src_w, sc.src_f0 = _ptr(keep["sx"]), _ptr(keep["sw"]), _ptr(keep["sf"])
+        sc.src_t0, sc.src_amp = _ptr(keep["st"]), _ptr(keep["sa"])
+    if len(receivers):
+        keep["rx"] = _f64(receivers)
+        sc.n_receivers = len(receivers)
+        sc.rec_xyz = _ptr(keep["rx"])
+    return sc, keep
+
+
+def poro_submit(srv, scenario):
+    t = ctypes.c_uint64()
+    _srv_check(lib().poro_submit(srv, ctypes.byref(scenario), ctypes.byref(t)), srv)
+    return t.value
+
+
+def poro_poll(srv, ticket):
+    st, t = _i32(), _dbl()
+    _srv_check(lib().poro_poll(srv, ticket, ctypes.byref(st), ctypes.byref(t)), srv)
+    return st.value, t.value
+
+
+def poro_wait(srv, ticket, timeout_ms=-1):
+    st = _i32()
+    rc = lib().poro_wait(srv, ticket, timeout_ms, ctypes.byref(st))
+    if rc not in (PORO_OK, PORO_ETIMEOUT):
+        _srv_check(rc, srv)
+    return st.value
+
+
+def poro_fetch(srv, ticket, rec):
+    n = _i64()
+    _srv_check(lib().poro_fetch(srv, ticket, rec, 0, None, None, ctypes.byref(n)), srv)
+    t = np.empty(n.value)
+    q = np.empty((n.value, 13))
+    _srv_check(lib().poro_fetch(srv, ticket, rec, n.value, _ptr(t), _ptr(q), ctypes.byref(n)), srv)
+    return t, q
+
+
+def poro_request_times(srv, ticket):
+    a, b, c = _dbl(), _dbl(), _dbl()
+    _srv_check(lib().poro_request_times(srv, ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), srv)
+    return a.value, b.value, c.value
+
+
+def poro_request_error(srv, ticket):
+    buf = ctypes.create_string_buffer(512)
+    lib().poro_request_error(srv, ticket, buf, 512)
+    return buf.value.decode()
+
+
+def poro_cancel(srv, ticket):
+    return _srv_check(lib().poro_cancel(srv, ticket), srv)
+
+
+def poro_footprint_bytes(N, n_elem, max_clusters=1, n_receivers=0):
+    b = ctypes.c_size_t()
+    _check(lib().poro_footprint_bytes(N, n_elem, max_clusters, n_receivers, ctypes.byref(b)))
+    return b.value

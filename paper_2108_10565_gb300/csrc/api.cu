@@ -27,6 +27,7 @@ struct poro_ctx {
     poro::LUScratch lu;
     int64_t lu_first = 0, lu_count = 0;
     int refine = 1;
+    int variant = 0;   // predictor CTA-size variant (poro_autotune)
     int64_t n_elem = 0;
     int stride = 0;
     double* d_econst = nullptr;
@@ -64,6 +65,14 @@ struct poro_ctx {
     std::vector<int32_t*> d_cl_elems;
     int32_t *d_cl = nullptr, *d_slot = nullptr;
     double* d_buf = nullptr;
+    bool use_graphs = true;
+    int64_t* d_tick = nullptr;                 // device copy of the tick counter (graph replays)
+    // persistent receiver buffers (no allocation in steady-state advances)
+    double *d_rp = nullptr, *d_seis = nullptr;
+    int32_t* d_cnt = nullptr;
+    int64_t seis_cap = 0;                      // samples per receiver d_seis holds
+    size_t rp_n = 0;                           // receivers uploaded to d_rp
+    std::vector<double> h_seis;                // staging for the D2H copy
 };
 
 namespace {
@@ -111,6 +120,12 @@ void free_mesh_device(poro_ctx* c) {
     dfree(c->d_cl);
     dfree(c->d_slot);
     dfree(c->d_buf);
+    dfree(c->d_tick);
+    dfree(c->d_rp);
+    dfree(c->d_seis);
+    dfree(c->d_cnt);
+    c->seis_cap = 0;
+    c->rp_n = 0;
     c->ready = false;
 }
 
@@ -422,9 +437,9 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     }
     if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
     if (c->prec == PORO_FP64) {
-        rc = poro::launch_stp_fp64(c->dref, nullptr, count, q0, ec, qt, iout, st);
+        rc = poro::launch_stp_fp64(c->dref, nullptr, count, q0, ec, qt, iout, st, c->variant);
     } else {
-        rc = poro::launch_stp_mixed(c->mref, c->refine, nullptr, count, q0, ec, qt, iout, st);
+        rc = poro::launch_stp_mixed(c->mref, c->refine, nullptr, count, q0, ec, qt, iout, st, c->variant);
     }
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "predict: kernel launch");
     return PORO_OK;
@@ -911,9 +926,52 @@ poro_status poro_add_receiver(poro_ctx* c, const double xyz[3], int32_t* id_out)
     return PORO_OK;
 }
 
-static double ricker_integral(double t, double f0, double t0) {
-    const double a = 3.14159265358979323846 * f0 * (t - t0);
-    return (t - t0) * std::exp(-a * a);
+// Enqueue one cycle (2^(C-1) ticks) on the context stream: no host
+// synchronisation and no allocation, so it can be captured in a CUDA graph.
+// Ticks inside the kernels are relative to the cycle (only their residues
+// modulo 2^c matter); the absolute tick for the sources is read from
+// d_tick, which the cycle advances at its end.
+static int enqueue_cycle(poro_ctx* c, const int64_t* d_re, const double* d_rp, double* d_seis, int64_t cap,
+                         int32_t* d_cnt) {
+    const int C = c->C;
+    const int64_t cycle = (int64_t)1 << (C - 1);
+    const int nrec = (int)c->rec_elem.size();
+    const bool want_qt = C > 1;
+    int rc = 0;
+    for (int64_t k = 0; k < cycle && rc == 0; ++k) {
+        for (int cl = 0; cl < C && rc == 0; ++cl) {
+            if (k % ((int64_t)1 << cl) || c->cl_elems[cl].empty()) continue;
+            const int32_t* el = C > 1 ? c->d_cl_elems[cl] : nullptr;
+            const int64_t cnt = (int64_t)c->cl_elems[cl].size();
+            if (c->prec == PORO_FP64)
+                rc = poro::launch_stp_fp64(c->dref, el, cnt, c->d_q0, c->d_econst, want_qt ? c->d_qt : nullptr,
+                                           c->d_iout, c->stream, c->variant);
+            else
+                rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
+                                            want_qt ? c->d_qt : nullptr, c->d_iout, c->stream, c->variant);
+            if (rc == 0 && C > 1)
+                rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, c->stream);
+        }
+        for (int cl = 0; cl < C && rc == 0; ++cl) {
+            const int64_t len = (int64_t)1 << cl;
+            if ((k + 1) % len || c->cl_elems[cl].empty()) continue;
+            poro::CorrectorData d = c->cd;
+            d.tick = k;
+            rc = poro::launch_corrector(d, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(),
+                                        c->stream);
+            for (auto& src : c->sources)
+                if (rc == 0 && c->h_cl[src.elem] == cl)
+                    rc = poro::launch_point_source_tick(c->N, c->d_q0, src.elem, src.d_coef, src.f0, src.t0, c->dt, len,
+                                                        k, c->d_tick, c->stream);
+            for (int r = 0; r < nrec && rc == 0; ++r)
+                if (c->h_cl[c->rec_elem[r]] == cl)
+                    rc = poro::launch_receiver_count(c->N, c->d_q0, c->rec_elem[r], d_rp + (size_t)r * c->B,
+                                                     d_seis + (size_t)r * cap * NQ, d_cnt + r, c->stream);
+        }
+    }
+    if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
+    (void)d_re;
+    return rc;
 }
 
 poro_status poro_advance(poro_ctx* c, double t_end) {
@@ -927,78 +985,85 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
     if (n_cycles <= 0) return PORO_OK;
     const int64_t ticks = n_cycles * cycle;
     const int nrec = (int)c->rec_elem.size();
-    int64_t* d_re = nullptr;
-    double *d_rp = nullptr, *d_seis = nullptr;
     cudaError_t er = cudaSuccess;
+    if (!c->d_tick && (er = cudaMalloc((void**)&c->d_tick, sizeof(int64_t))) != cudaSuccess)
+        return cuda_fail(c, er, "poro_advance");
+    if ((er = cudaMemcpyAsync(c->d_tick, &c->tick, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(c, er, "poro_advance");
     if (nrec > 0) {
-        if ((er = upload((void**)&d_re, c->rec_elem.data(), nrec * sizeof(int64_t))) != cudaSuccess ||
-            (er = upload((void**)&d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
-            (er = cudaMalloc((void**)&d_seis, (size_t)nrec * ticks * NQ * sizeof(double))) != cudaSuccess) {
-            dfree(d_re);
-            dfree(d_rp);
+        // buffers are kept across calls; they grow only when a call needs more
+        if (c->rp_n != (size_t)nrec) {
+            dfree(c->d_rp);
+            dfree(c->d_cnt);
+            c->rp_n = 0;
+            if ((er = upload((void**)&c->d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
+                (er = cudaMalloc((void**)&c->d_cnt, nrec * sizeof(int32_t))) != cudaSuccess)
+                return cuda_fail(c, er, "poro_advance");
+            c->rp_n = nrec;
+            dfree(c->d_seis);
+            c->seis_cap = 0;
+        }
+        if (c->seis_cap < ticks) {
+            dfree(c->d_seis);
+            c->seis_cap = 0;
+            if ((er = cudaMalloc((void**)&c->d_seis, (size_t)nrec * ticks * NQ * sizeof(double))) != cudaSuccess)
+                return cuda_fail(c, er, "poro_advance");
+            c->seis_cap = ticks;
+        }
+        if ((er = cudaMemsetAsync(c->d_cnt, 0, nrec * sizeof(int32_t), c->stream)) != cudaSuccess)
             return cuda_fail(c, er, "poro_advance");
-        }
     }
-    std::vector<int64_t> nsamp(nrec, 0);
-    std::vector<std::vector<double>> tsamp(nrec);
-    int rc = 0;
-    const bool want_qt = C > 1;
-    for (int64_t k = c->tick; k < c->tick + ticks && rc == 0; ++k) {
-        // (A) predictors of the clusters whose step starts at tick k
-        for (int cl = 0; cl < C && rc == 0; ++cl) {
-            if (k % ((int64_t)1 << cl) || c->cl_elems[cl].empty()) continue;
-            const int32_t* el = C > 1 ? c->d_cl_elems[cl] : nullptr;
-            const int64_t cnt = (int64_t)c->cl_elems[cl].size();
-            if (c->prec == PORO_FP64)
-                rc = poro::launch_stp_fp64(c->dref, el, cnt, c->d_q0, c->d_econst, want_qt ? c->d_qt : nullptr,
-                                           c->d_iout, c->stream);
-            else
-                rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
-                                            want_qt ? c->d_qt : nullptr, c->d_iout, c->stream);
-            if (rc == 0 && C > 1)
-                rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, c->stream);
-        }
-        // (B) correctors of the clusters whose step ends at tick k + 1
-        for (int cl = 0; cl < C && rc == 0; ++cl) {
-            const int64_t len = (int64_t)1 << cl;
-            if ((k + 1) % len || c->cl_elems[cl].empty()) continue;
-            c->cd.tick = k;
-            rc = poro::launch_corrector(c->cd, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(),
-                                        c->stream);
-            const double t0 = (double)(k + 1 - len) * c->dt, t1 = (double)(k + 1) * c->dt;
-            for (auto& src : c->sources)
-                if (rc == 0 && c->h_cl[src.elem] == cl)
-                    rc = poro::launch_point_source(c->N, c->d_q0, src.elem, src.d_coef,
-                                                   ricker_integral(t1, src.f0, src.t0) - ricker_integral(t0, src.f0, src.t0),
-                                                   c->stream);
-            for (int r = 0; r < nrec && rc == 0; ++r) {
-                if (c->h_cl[c->rec_elem[r]] != cl) continue;
-                rc = poro::launch_receivers(c->N, c->d_q0, 1, d_re + r, d_rp + (size_t)r * c->B,
-                                            d_seis + ((size_t)r * ticks + nsamp[r]) * NQ, 0, c->stream);
-                ++nsamp[r];
-                tsamp[r].push_back(t1);
+    double* d_rp = c->d_rp;
+    double* d_seis = c->d_seis;
+    int32_t* d_cnt = c->d_cnt;
+    const int64_t cap = c->seis_cap;
+    // the first cycle runs directly (it also sets the kernels' attributes);
+    // the others replay a CUDA graph of one cycle
+    int rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
+    if (rc == 0 && n_cycles > 1) {
+        if (c->use_graphs) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            er = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (er == cudaSuccess) {
+                rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+                if (rc == 0 && e2 != cudaSuccess) rc = (int)e2;
+            } else {
+                rc = (int)er;
             }
+            if (rc == 0) rc = (int)cudaGraphInstantiate(&exec, graph, 0);
+            for (int64_t k = 1; k < n_cycles && rc == 0; ++k) rc = (int)cudaGraphLaunch(exec, c->stream);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+        } else {
+            for (int64_t k = 1; k < n_cycles && rc == 0; ++k) rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
         }
     }
-    if (rc == 0) er = cudaStreamSynchronize(c->stream);
-    std::vector<double> h;
-    if (rc == 0 && er == cudaSuccess && nrec > 0) {
-        h.resize((size_t)nrec * ticks * NQ);
-        er = cudaMemcpy(h.data(), d_seis, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    std::vector<double>& h = c->h_seis;
+    if (rc == 0 && nrec > 0) {
+        h.resize((size_t)nrec * cap * NQ);
+        er = cudaMemcpyAsync(h.data(), d_seis, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     }
-    dfree(d_re);
-    dfree(d_rp);
-    dfree(d_seis);
-    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch");
+    if (rc == 0 && er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch / graph");
     if (er != cudaSuccess) return cuda_fail(c, er, "poro_advance");
     for (int r = 0; r < nrec; ++r) {
-        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * ticks * NQ,
-                            h.begin() + ((size_t)r * ticks + nsamp[r]) * NQ);
-        c->seis_t[r].insert(c->seis_t[r].end(), tsamp[r].begin(), tsamp[r].end());
+        const int cl = c->h_cl[c->rec_elem[r]];
+        const int64_t len = (int64_t)1 << cl, ns = ticks / len;
+        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * cap * NQ,
+                            h.begin() + ((size_t)r * cap + ns) * NQ);
+        for (int64_t j = 1; j <= ns; ++j) c->seis_t[r].push_back((double)(c->tick + j * len) * c->dt);
     }
     c->tick += ticks;
     c->t = (double)c->tick * c->dt;
     c->have_pred = true;
+    return PORO_OK;
+}
+
+poro_status poro_set_graphs(poro_ctx* c, int32_t on) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_graphs: ctx is NULL");
+    c->use_graphs = on != 0;
     return PORO_OK;
 }
 
@@ -1051,6 +1116,55 @@ poro_status poro_flux_matrices(const poro_material* mL, const poro_material* mR,
     if (kind == PORO_FACE_INTERIOR && !mR) return fail(nullptr, PORO_EINVAL, "poro_flux_matrices: interior needs mR");
     std::string err;
     if (!poro::flux_solver(*mL, mR, n, kind, Fm, Fp, err)) return fail(nullptr, PORO_EINVAL, err);
+    return PORO_OK;
+}
+
+poro_status poro_autotune(poro_ctx* c, int64_t sample, int32_t* variant_out, double* ms_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_autotune: ctx is NULL");
+    if (!c->d_econst || c->n_elem <= 0) return fail(c, PORO_ESTATE, "poro_autotune: no element population loaded");
+    cudaSetDevice(c->device);
+    const int64_t n = std::max<int64_t>(1, std::min(sample > 0 ? sample : c->n_elem, c->n_elem));
+    double best = 1e300;
+    int bestv = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved = c->variant;
+    for (int v = 0; v < 2; ++v) {
+        c->variant = v;
+        poro_status s = PORO_OK;
+        for (int w = 0; w < 2 && s == PORO_OK; ++w)
+            s = dispatch_predict(c, 0, n, c->d_q0, c->d_qt, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && s == PORO_OK; ++r)
+            s = dispatch_predict(c, 0, n, c->d_q0, c->d_qt, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
+        cudaEventRecord(e1, c->stream);
+        cudaError_t er = cudaEventSynchronize(e1);
+        if (s != PORO_OK || er != cudaSuccess) {
+            c->variant = saved;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return s != PORO_OK ? s : cuda_fail(c, er, "poro_autotune");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) ms_out[v] = ms / 3.0;
+        if (ms < best) {
+            best = ms;
+            bestv = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->variant = bestv;
+    if (variant_out) *variant_out = bestv;
+    return PORO_OK;
+}
+
+poro_status poro_set_variant(poro_ctx* c, int32_t variant) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_variant: ctx is NULL");
+    if (variant < 0 || variant > 1) return fail(c, PORO_EINVAL, "poro_set_variant: variant must be 0 or 1");
+    c->variant = variant;
     return PORO_OK;
 }
 

@@ -166,6 +166,35 @@ __global__ void lts_buffer_kernel(int QB, int C, const int32_t* elems, int64_t c
     }
 }
 
+// point source with the amplitude of the step computed on the device:
+// int_{t0}^{t1} s dt = S(t1) - S(t0), S(t) = (t - tc) exp(-(pi f0 (t - tc))^2),
+// the step [ (k+1-len) dt, (k+1) dt ], k = *tick + k_rel
+__global__ void point_source_tick_kernel(int QB, double* q, int64_t elem, const double* coef, double f0, double tc,
+                                         double dt, int64_t len, int64_t k_rel, const int64_t* tick) {
+    const int64_t k = *tick + k_rel;
+    const double t1 = (double)(k + 1) * dt, t0 = (double)(k + 1 - len) * dt;
+    const double a1 = 3.14159265358979323846 * f0 * (t1 - tc), a0 = 3.14159265358979323846 * f0 * (t0 - tc);
+    const double amp = (t1 - tc) * exp(-a1 * a1) - (t0 - tc) * exp(-a0 * a0);
+    for (int i = threadIdx.x; i < QB; i += blockDim.x) q[elem * QB + i] += amp * coef[i];
+}
+
+// receiver sample at the position given by a device counter
+__global__ void receiver_count_kernel(int B, const double* q, int64_t elem, const double* phi, double* out,
+                                      int32_t* counter) {
+    const int p = threadIdx.x;
+    const int32_t idx = *counter;
+    if (p < NQ) {
+        const double* qe = q + elem * (int64_t)(NQ * B) + p * B;
+        double acc = 0.0;
+        for (int l = 0; l < B; ++l) acc = fma(qe[l], phi[l], acc);
+        out[(int64_t)idx * NQ + p] = acc;
+    }
+    __syncthreads();
+    if (p == 0) *counter = idx + 1;
+}
+
+__global__ void tick_advance_kernel(int64_t* tick, int64_t n) { *tick += n; }
+
 __global__ void point_source_kernel(int QB, double* q, int64_t elem, const double* coef, double amp) {
     for (int i = threadIdx.x; i < QB; i += blockDim.x) q[elem * QB + i] += amp * coef[i];
 }
@@ -200,6 +229,24 @@ int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const 
     const int64_t grid = count < 65536 ? count : 65536;
     lts_buffer_kernel<<<(unsigned)grid, 128, 0, (cudaStream_t)stream>>>(NQ * n_modes(N), C, elems, count, slot, iout,
                                                                        buf, tick);
+    return (int)cudaGetLastError();
+}
+
+int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef, double f0, double tc, double dt,
+                             int64_t len, int64_t k_rel, const int64_t* tick, void* stream) {
+    point_source_tick_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(NQ * n_modes(N), q, elem, coef, f0, tc, dt, len,
+                                                                  k_rel, tick);
+    return (int)cudaGetLastError();
+}
+
+int launch_receiver_count(int N, const double* q, int64_t elem, const double* phi, double* out, int32_t* counter,
+                          void* stream) {
+    receiver_count_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(n_modes(N), q, elem, phi, out, counter);
+    return (int)cudaGetLastError();
+}
+
+int launch_tick_advance(int64_t* tick, int64_t n, void* stream) {
+    tick_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(tick, n);
     return (int)cudaGetLastError();
 }
 

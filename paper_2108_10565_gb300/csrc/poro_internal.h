@@ -131,7 +131,8 @@ struct MixedReference {
 // Launch the mixed-precision predictor (binary32 sweeps, `refine` residual
 // corrections in double-binary32) for `count` elements.
 int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count,
-                     const double* q0, const double* econst, double* qt, double* iout, void* stream);
+                     const double* q0, const double* econst, double* qt, double* iout, void* stream,
+                     int variant = 0);
 
 // Dense-LU comparator: reference data and per-batch scratch (factors,
 // pivots, permutation, equilibration factors, singularity flag).
@@ -197,13 +198,20 @@ int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const 
                        double* buf, int64_t tick, void* stream);
 int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
 int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
+int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef, double f0, double tc, double dt,
+                             int64_t len, int64_t k_rel, const int64_t* tick, void* stream);
+int launch_receiver_count(int N, const double* q, int64_t elem, const double* phi, double* out, int32_t* counter,
+                          void* stream);
+int launch_tick_advance(int64_t* tick, int64_t n, void* stream);
 int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems, const double* phi, double* out,
                      int64_t stride_out, void* stream);
 
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
 // `elems` (nullable): element index list; outputs are indexed by element.
+// `variant` selects the CTA size (0: default, 1: the alternative the
+// autotuner may pick).
 int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-                    const double* econst, double* qt, double* iout, void* stream);
+                    const double* econst, double* qt, double* iout, void* stream, int variant = 0);
 
 }  // namespace poro

@@ -38,10 +38,17 @@ struct K1Params {
     const double* zinv;
 };
 
+// CTA sizes the autotuner chooses from (index 0 is the default)
 template <int N>
+struct K1Sizes {
+    static constexpr int NT0 = N >= 5 ? 256 : (N == 4 ? 128 : 64);
+    static constexpr int NT1 = N >= 5 ? 128 : (N == 4 ? 256 : 128);
+};
+
+template <int N, int NT_>
 struct K1Shape : Alg3Shape<N> {
     using A = Alg3Shape<N>;
-    static constexpr int NT = N >= 5 ? 256 : (N == 4 ? 128 : 64);
+    static constexpr int NT = NT_;
     static constexpr int T_ = N + 1;
     // shared layout (doubles): bq[13*QS] | X[13*XSMAX] | star[162] | zuf[T*T] | sc[4] | zin[T*T]
     static constexpr int OFF_X = A::SQ;
@@ -52,9 +59,9 @@ struct K1Shape : Alg3Shape<N> {
     static constexpr int SMEM_DOUBLES = OFF_ZIN + T_ * T_;
 };
 
-template <int N>
-__global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params P) {
-    using S = K1Shape<N>;
+template <int N, int NT_>
+__global__ void __launch_bounds__(NT_) stp_fp64_kernel(const K1Params P) {
+    using S = K1Shape<N, NT_>;
     constexpr int B = S::B, T = S::T, NT = S::NT, QS = S::QS;
     extern __shared__ double sm[];
     double* bq = sm;
@@ -89,10 +96,10 @@ __global__ void __launch_bounds__(K1Shape<N>::NT) stp_fp64_kernel(const K1Params
     }
 }
 
-template <int N>
-int launch_n(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-             const double* econst, double* qt, double* iout, void* stream) {
-    using S = K1Shape<N>;
+template <int N, int NT_>
+int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+              const double* econst, double* qt, double* iout, void* stream) {
+    using S = K1Shape<N, NT_>;
     K1Params P;
     P.elems = elems;
     P.q0 = q0;
@@ -108,26 +115,34 @@ int launch_n(const DeviceReference& ref, const int32_t* elems, int64_t count, co
         for (int j = 0; j < 3; ++j) P.khat.row_base[g][j] = ref.row_base[g][j];
     P.zinv = ref.zinv;
     const size_t smem = sizeof(double) * S::SMEM_DOUBLES;
-    cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    stp_fp64_kernel<N><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
+    stp_fp64_kernel<N, NT_><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
     return (int)cudaGetLastError();
+}
+
+template <int N>
+int launch_n(const DeviceReference& ref, int variant, const int32_t* elems, int64_t count, const double* q0,
+             const double* econst, double* qt, double* iout, void* stream) {
+    if (variant == 1)
+        return launch_nt<N, K1Sizes<N>::NT1>(ref, elems, count, q0, econst, qt, iout, stream);
+    return launch_nt<N, K1Sizes<N>::NT0>(ref, elems, count, q0, econst, qt, iout, stream);
 }
 
 }  // namespace
 
 int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-                    const double* econst, double* qt, double* iout, void* stream) {
+                    const double* econst, double* qt, double* iout, void* stream, int variant) {
     switch (ref.N) {
-        case 1: return launch_n<1>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_n<1>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_n<2>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 3: return launch_n<3>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 4: return launch_n<4>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 5: return launch_n<5>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 6: return launch_n<6>(ref, variant, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }

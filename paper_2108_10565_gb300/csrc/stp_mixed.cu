@@ -85,10 +85,17 @@ __device__ __forceinline__ float2 dw_split(double x) {
     return make_float2(h, (float)(x - (double)h));
 }
 
-template <int N, int REF>
+// CTA sizes the autotuner chooses from (index 0 is the default)
+template <int N>
+struct K2Sizes {
+    static constexpr int NT0 = N >= 5 ? 256 : (N == 4 ? 128 : 64);
+    static constexpr int NT1 = N >= 5 ? 128 : (N == 4 ? 256 : 128);
+};
+
+template <int N, int REF, int NT_>
 struct K2Shape : Alg3Shape<N> {
     using A = Alg3Shape<N>;
-    static constexpr int NT = N >= 5 ? 256 : (N == 4 ? 128 : 64);
+    static constexpr int NT = NT_;
     static constexpr int NW = NT / 32;
     static constexpr int T_ = N + 1;
     static constexpr int R4(int x) { return (x + 3) & ~3; }
@@ -110,11 +117,11 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int SMEM_FLOATS = OFF_TAB + R4(NQ + 1 + STAR_NNZ);
 };
 
-template <int N, int REF>
+template <int N, int REF, int NT_>
 __device__ void residual(float* W, const float* Q1, const float* D1, const float2* b0, const float* sh,
                          const float* sl, const float* zi, const int* tab, float2 e_dw, float2 g_dw, float2* Yall,
                          const K2Params& P) {
-    using S = K2Shape<N, REF>;
+    using S = K2Shape<N, REF, NT_>;
     constexpr int B = S::B, T = S::T, PT = S::PT, PUL = S::PUL, QS = S::QS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* Y = Yall + warp * 3 * PT;
@@ -202,9 +209,9 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
     }
 }
 
-template <int N, int REF>
-__global__ void __launch_bounds__(K2Shape<N, REF>::NT, REF == 2 ? 1 : 2) stp_mixed_kernel(const K2Params P) {
-    using S = K2Shape<N, REF>;
+template <int N, int REF, int NT_>
+__global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixed_kernel(const K2Params P) {
+    using S = K2Shape<N, REF, NT_>;
     constexpr int B = S::B, T = S::T, NT = S::NT, QBT = S::QBT, QS = S::QS;
     extern __shared__ float smf[];
     float* W = smf + S::OFF_W;
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(K2Shape<N, REF>::NT, REF == 2 ? 1 : 2) stp_mix
         __syncthreads();
 #pragma unroll 1
         for (int sweep = 1; sweep <= REF; ++sweep) {
-            residual<N, REF>(W, Q1, D1, b0, sh, sl, zi, tab, e_dw, g_dw, Yall, P);
+            residual<N, REF, NT_>(W, Q1, D1, b0, sh, sl, zi, tab, e_dw, g_dw, Yall, P);
             __syncthreads();
             alg3_sweep<N, NT, float, 3>(W, X, sh, zuf, zin, g_dw.x, P.khat);
             if (REF == 2 && sweep == 1) {
@@ -284,10 +291,10 @@ __global__ void __launch_bounds__(K2Shape<N, REF>::NT, REF == 2 ? 1 : 2) stp_mix
     }
 }
 
-template <int N, int REF>
+template <int N, int REF, int NT_>
 int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, const double* q0, const double* econst,
               double* qt, double* iout, void* stream) {
-    using S = K2Shape<N, REF>;
+    using S = K2Shape<N, REF, NT_>;
     K2Params P;
     P.elems = elems;
     P.q0 = q0;
@@ -306,37 +313,45 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     P.res_val = reinterpret_cast<const float2*>(ref.res_val);
     P.zinv = ref.zinv_f32;
     const size_t smem = sizeof(float) * S::SMEM_FLOATS;
-    cudaError_t err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    stp_mixed_kernel<N, REF><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
+    stp_mixed_kernel<N, REF, NT_><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
     return (int)cudaGetLastError();
 }
 
-template <int N>
-int launch_n(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
-             const double* econst, double* qt, double* iout, void* stream) {
+template <int N, int NT_>
+int launch_nv(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
+              const double* econst, double* qt, double* iout, void* stream) {
     switch (refine) {
-        case 0: return launch_nr<N, 0>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 1: return launch_nr<N, 1>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_nr<N, 2>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 0: return launch_nr<N, 0, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_nr<N, 1, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_nr<N, 2, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
+}
+
+template <int N>
+int launch_n(const MixedReference& ref, int refine, int variant, const int32_t* elems, int64_t count,
+             const double* q0, const double* econst, double* qt, double* iout, void* stream) {
+    if (variant == 1)
+        return launch_nv<N, K2Sizes<N>::NT1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+    return launch_nv<N, K2Sizes<N>::NT0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
 }
 
 }  // namespace
 
 int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
-                     const double* econst, double* qt, double* iout, void* stream) {
+                     const double* econst, double* qt, double* iout, void* stream, int variant) {
     switch (ref.base->N) {
-        case 1: return launch_n<1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_n<1>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_n<2>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 3: return launch_n<3>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 4: return launch_n<4>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 5: return launch_n<5>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 6: return launch_n<6>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }

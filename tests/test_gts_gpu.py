@@ -140,3 +140,31 @@ def test_lts_three_clusters_run(L, precision):
         np.testing.assert_allclose(tg, tr, rtol=1e-12)
     _check_seis(seis, [qr for _, qr in seis_ref], tol=tol)
     assert np.linalg.norm(Q - Qref) <= 1e-10 * np.linalg.norm(Qref)
+
+
+def test_graphs_autotune_and_variants_agree(L):
+    """The CUDA-graph replay of a cycle, the host-enqueued cycles and both
+    autotuner CTA-size variants give bitwise identical runs (FP64, 3 clusters)."""
+    mesh = _graded(True)
+    ne = mesh["tets"].shape[0]
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    Q0 = np.random.default_rng(6).standard_normal((ne, 13, 10))
+    out = []
+    for graphs, variant in ((True, 0), (False, 0), (True, 1)):
+        ctx = L.poro_create(0, 2, 0)
+        try:
+            L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+            L.poro_set_materials(ctx, mats)
+            dt, _ = L.poro_set_clusters(ctx, 0.5, 3)
+            v, ms = L.poro_autotune(ctx, 0)
+            assert v in (0, 1) and min(ms) > 0
+            L.poro_set_variant(ctx, variant)
+            L.poro_set_graphs(ctx, graphs)
+            L.poro_set_dofs(ctx, Q0)
+            r = L.poro_add_receiver(ctx, np.array([0.3, 1.2, 0.9]))
+            L.poro_advance(ctx, 3 * 4 * dt * 1.0000001)
+            out.append((L.poro_get_dofs(ctx), L.poro_get_seismogram(ctx, r)[1]))
+        finally:
+            L.poro_destroy(ctx)
+    for Q, s in out[1:]:
+        assert np.array_equal(Q, out[0][0]) and np.array_equal(s, out[0][1])
