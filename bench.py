@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-lu", action="store_true")
     ap.add_argument("--lu-n6", type=int, default=4, help="elements factored at N=6 for the LU comparator")
     ap.add_argument("--lu-n3", type=int, default=1024, help="elements factored at N=3 for the LU comparator")
+    ap.add_argument("--no-steps", action="store_true", help="skip the time-stepping / LTS sections")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=12)
     return ap.parse_args()
 
 
@@ -233,6 +236,132 @@ def lu_comparator(L, torch, dev, local, args, hbm_gbs):
     return out
 
 
+def _setup_mesh_ctx(L, N, prec, mesh, mats, C, local=0, graphs=True):
+    ctx = L.poro_create(local, N, prec)
+    L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+    L.poro_set_materials(ctx, mats)
+    dt, cl = L.poro_set_clusters(ctx, 0.5, C, n_elem=mesh["tets"].shape[0])
+    L.poro_set_graphs(ctx, graphs)
+    return ctx, dt, cl
+
+
+def time_stepping_sections(L, local, args):
+    """Full ADER-DG steps (predictor + corrector + sources + receivers) under
+    global and clustered local time stepping; wall-clock time to solution of
+    poro_advance (synchronous)."""
+    from paper_2108_10565_gb300 import inputs
+
+    out = {}
+    # the small periodic scenario: 384 tets, N = 2, 50 steps, graphs on / off
+    sc = inputs.config0_scenario()
+    r = {}
+    for graphs in (True, False):
+        ctx, dt, _ = _setup_mesh_ctx(L, sc["N"], 0, sc["mesh"], sc["materials"], 1, local, graphs)
+        L.poro_add_point_source(ctx, sc["source"]["x"], sc["source"]["w"], sc["source"]["f0"], sc["source"]["t0"])
+        for x in sc["receivers"]:
+            L.poro_add_receiver(ctx, x)
+        L.poro_advance(ctx, 5.5 * dt)  # warm-up (kernel attributes, graph capture path)
+        t0 = time.perf_counter()
+        L.poro_advance(ctx, (5 + sc["n_steps"] + 0.5) * dt)
+        el = time.perf_counter() - t0
+        L.poro_destroy(ctx)
+        r["graphs" if graphs else "no_graphs"] = {"seconds": el, "steps": sc["n_steps"],
+                                                  "element_updates_per_s": 384 * sc["n_steps"] / el}
+    out["periodic_384_N2_50_steps"] = r
+    # larger periodic GTS run: predictor + corrector throughput at N = 5
+    mesh = inputs.kuhn_box_mesh(20)
+    ne = mesh["tets"].shape[0]
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    r = {}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        ctx, dt, _ = _setup_mesh_ctx(L, 5, prec, mesh, mats, 1, local)
+        L.poro_set_dofs(ctx, np.random.default_rng(0).standard_normal((ne, 13, 56)))
+        L.poro_advance(ctx, 1.5 * dt)
+        nsteps = 6
+        t0 = time.perf_counter()
+        L.poro_advance(ctx, (1 + nsteps + 0.5) * dt)
+        el = time.perf_counter() - t0
+        L.poro_destroy(ctx)
+        r[name] = {"seconds": el, "steps": nsteps, "element_updates_per_s": ne * nsteps / el}
+    out[f"periodic_{ne}_N5_gts"] = r
+    # clustered LTS vs GTS on the layered graded mesh, same simulated time
+    mesh, mats = inputs.layered_graded_mesh(12, grading=512.0)
+    ne = mesh["tets"].shape[0]
+    r = {"n_elem": ne, "degree": 5}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        res = {}
+        for C in (6, 1):
+            ctx, dt, cl = _setup_mesh_ctx(L, 5, prec, mesh, mats, C, local)
+            L.poro_add_point_source(ctx, np.array([0.0, 0.0, -1010.0]),
+                                    -np.r_[np.ones(3), np.zeros(6), -1, np.zeros(3)], 5.0, 0.25, 1e12)
+            L.poro_add_receiver(ctx, np.array([0.0, 0.0, -1.0]))
+            t_sim = 32 * dt * 2.0 ** 0  # one step of the largest cluster of the LTS run
+            L.poro_advance(ctx, t_sim * 1.0000001)  # warm-up cycle
+            t0 = time.perf_counter()
+            L.poro_advance(ctx, 2 * t_sim * 1.0000001)
+            el = time.perf_counter() - t0
+            L.poro_destroy(ctx)
+            hist = np.bincount(cl, minlength=C).tolist()
+            upd = sum(n * 32 / 2 ** c for c, n in enumerate(hist))
+            res["lts" if C > 1 else "gts"] = {"seconds": el, "element_updates": upd,
+                                              "element_updates_per_s": upd / el, "clusters": hist}
+        res["lts_speedup_time_to_solution"] = res["gts"]["seconds"] / res["lts"]["seconds"]
+        r[name] = res
+    out["layered_graded_lts_vs_gts"] = r
+    return out
+
+
+def serving_section(L, local, args):
+    """Served ensemble (scaled): a Poisson trace (mean 2 requests/s) of
+    independent simulations with uniform meshes of 3k-30k tets, N in {2,3,4},
+    seeded sources and material perturbations, a fixed number of steps of
+    their largest cluster each; continuous batching in mixed precision vs
+    the same trace one at a time in FP64."""
+    from paper_2108_10565_gb300 import inputs
+
+    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING))
+    n_req = args.serving_requests
+    arrivals = np.cumsum(rng.exponential(0.5, n_req))
+    reqs = []
+    for i in range(n_req):
+        mesh = inputs.uniform_box_mesh_for(int(rng.uniform(3000, 30000)))
+        ne = mesh["tets"].shape[0]
+        N = int(rng.integers(2, 5))
+        mats = inputs.perturbed_materials(rng, ne, base=inputs.HALFSPACE_MATERIAL)
+        src = dict(x=np.array([rng.uniform(5e3, 15e3), rng.uniform(5e3, 15e3), -rng.uniform(1e3, 5e3)]),
+                   w=-np.r_[np.ones(3), np.zeros(6), -1, np.zeros(3)], f0=2.0, t0=0.6, amplitude=1e12)
+        rec = [np.array([x, y, -1.0]) for x, y in rng.uniform(2e3, 18e3, (4, 2))]
+        reqs.append(dict(N=N, mesh=mesh, mats=mats, src=[src], rec=rec, ne=ne))
+    # simulated time: 10 steps of each request's own step
+    for rq in reqs:
+        dt = L.poro_cfl_dt(rq["N"], rq["mesh"]["vertices"][rq["mesh"]["tets"]], rq["mats"]).min()
+        rq["t_end"] = 10.0 * dt * 1.0000001
+    out = {"requests": n_req, "arrival_rate_per_s": 2.0,
+           "mesh_elements": [int(r["ne"]) for r in reqs], "degrees": [int(r["N"]) for r in reqs]}
+    for mode, prec, slots in (("served_mixed", 1, 4), ("one_at_a_time_fp64", 0, 1)):
+        srv = L.poro_server_create(local, 200 << 30, slots)
+        tickets, keep = [], []
+        t0 = time.perf_counter()
+        for rq, ta in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            sc, k = L.make_scenario(rq["N"], rq["mesh"], rq["mats"], rq["t_end"], precision=prec,
+                                    sources=rq["src"], receivers=rq["rec"])
+            keep.append(k)
+            tickets.append(L.poro_submit(srv, sc))
+        states = [L.poro_wait(srv, t, 600_000) for t in tickets]
+        wall = time.perf_counter() - t0
+        lat = np.array([L.poro_request_times(srv, t)[2] for t in tickets])
+        L.poro_server_destroy(srv)
+        upd = sum(r["ne"] * 10 for r in reqs)
+        out[mode] = {"wall_s": wall, "done": int(sum(s == L.PORO_REQ_DONE for s in states)),
+                     "requests_per_s": n_req / wall, "element_updates_per_s": upd / wall,
+                     "p50_time_to_seismogram_s": float(np.percentile(lat, 50)),
+                     "p99_time_to_seismogram_s": float(np.percentile(lat, 99))}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -359,6 +488,17 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hi.numel() * 8), "form": head}
     for r in res.values():
         L.poro_destroy(r["ctx"])
+    steps = serving = None
+    if not args.no_steps and world == 1:
+        try:
+            steps = time_stepping_sections(L, local, args)
+        except Exception as ex:  # reported, the headline line still prints
+            steps = {"error": repr(ex)}
+    if not args.no_serving and world == 1:
+        try:
+            serving = serving_section(L, local, args)
+        except Exception as ex:
+            serving = {"error": repr(ex)}
     lu = None
     if not args.no_lu and world == 1:
         hbm = 6792.1
@@ -392,7 +532,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
         "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": err,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
-        "lu_comparator": lu,
+        "lu_comparator": lu, "time_stepping": steps, "serving": serving,
     }
     print(json.dumps(out))
     if world > 1:

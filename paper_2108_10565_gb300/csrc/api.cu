@@ -705,8 +705,9 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     // faces: neighbour face, vertex permutation, normal, area, flux solvers
     std::vector<int32_t> nb(4 * ne), tab(4 * ne);
     std::vector<double> fc(4 * ne), fF((size_t)ne * 4 * 2 * NQ * NQ);
-    std::map<std::string, std::vector<double>> cache;
-    for (int64_t e = 0; e < ne; ++e) {
+    // per element (independent): run over host threads, each with its own
+    // cache of flux solvers keyed by (materials, normal, kind)
+    auto face_setup = [&](int64_t e, std::map<std::string, std::vector<double>>& cache, std::string& ferr) -> bool {
         double v[12];
         elem_vertices(c, e, v);
         for (int f = 0; f < 4; ++f) {
@@ -766,8 +767,10 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
                     if (ok && perm[0] != perm[1] && perm[1] != perm[2] && perm[0] != perm[2])
                         tab[4 * e + f] = f * 24 + h * 6 + poro::face_permutation_index(perm);
                 }
-                if (tab[4 * e + f] < 0)
-                    return fail(c, PORO_EINVAL, "poro_set_clusters: non-conforming face at element " + std::to_string(e));
+                if (tab[4 * e + f] < 0) {
+                    ferr = "non-conforming face at element " + std::to_string(e);
+                    return false;
+                }
             }
             std::string key(reinterpret_cast<const char*>(&c->h_mat[e]), sizeof(poro_material));
             if (r >= 0) key.append(reinterpret_cast<const char*>(&c->h_mat[r]), sizeof(poro_material));
@@ -779,11 +782,42 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
                 std::vector<double> F(2 * NQ * NQ);
                 std::string err;
                 if (!poro::flux_solver(c->h_mat[e], r >= 0 ? &c->h_mat[r] : nullptr, nr, kind, F.data(),
-                                       F.data() + NQ * NQ, err))
-                    return fail(c, PORO_ENUMERIC, "poro_set_clusters: flux at element " + std::to_string(e) + ": " + err);
+                                       F.data() + NQ * NQ, err)) {
+                    ferr = "flux at element " + std::to_string(e) + ": " + err;
+                    return false;
+                }
                 itc = cache.emplace(key, std::move(F)).first;
             }
             std::memcpy(dst, itc->second.data(), sizeof(double) * 2 * NQ * NQ);
+        }
+        return true;
+    };
+    {
+        const int nthreads = (int)std::max<int64_t>(1, std::min<int64_t>(
+            std::min<unsigned>(32u, std::max(1u, std::thread::hardware_concurrency())), ne / 256 + 1));
+        std::vector<std::string> errs(nthreads);
+        std::vector<int64_t> bad_at(nthreads, -1);
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nthreads; ++t)
+            pool.emplace_back([&, t] {
+                std::map<std::string, std::vector<double>> cache;
+                for (int64_t e = t; e < ne; e += nthreads)
+                    if (!face_setup(e, cache, errs[t])) {
+                        bad_at[t] = e;
+                        return;
+                    }
+            });
+        for (auto& th : pool) th.join();
+        int64_t first_bad = -1;
+        std::string msg;
+        for (int t = 0; t < nthreads; ++t)
+            if (bad_at[t] >= 0 && (first_bad < 0 || bad_at[t] < first_bad)) {
+                first_bad = bad_at[t];
+                msg = errs[t];
+            }
+        if (first_bad >= 0) {
+            free_population(c);
+            return fail(c, msg.rfind("flux", 0) == 0 ? PORO_ENUMERIC : PORO_EINVAL, "poro_set_clusters: " + msg);
         }
     }
     // volume CSR: Kv^j_kl = M_ll Khat^j_lk / M_kk

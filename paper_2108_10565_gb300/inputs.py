@@ -212,3 +212,41 @@ def config0_scenario():
     return dict(mesh=mesh, N=2, n_steps=50, materials=np.tile(REFERENCE_MATERIAL, (ne, 1)),
                 source=dict(x=np.array([0.5, 0.5, 0.5]), w=w, f0=1.0e4, t0=1.0e-4, amplitude=1.0),
                 receivers=rec, Q0=np.zeros((ne, 13, 10)))
+
+
+# layer over half-space (Table material_heterogeneous columns, viscous fluid)
+LAYER_MATERIAL = np.array([7.6e9, 2210.0, 3.96e9, 3.96e9, 1e-12, 0.16, 2.0, 2.5e9, 1040.0, 1e-3])
+HALFSPACE_MATERIAL = np.array([40e9, 2500.0, 12e9, 12e9, 6e-12, 0.2, 2.0, 2.5e9, 1040.0, 1e-3])
+SEED_LOH = 2108105653
+SEED_SERVING = 2108105654
+
+
+def layered_graded_mesh(nz, radius=2000.0, grading=32.0, layer_depth=500.0):
+    """Layer-over-half-space geometry on a graded tetrahedral mesh (the shape
+    of the LOHp setting, scaled): a Kuhn mesh of the parameter box
+    [-1, 1]^2 x [-1, 0] with 2nz x 2nz x nz boxes is mapped radially about
+    the surface origin by rho' = R (exp(k rho) - 1) / (exp(k) - 1),
+    k = ln(grading) / sqrt(3): z = 0 stays planar (free surface), edge
+    lengths grow ~grading-fold from the origin outwards; absorbing faces
+    elsewhere.  Elements with centroid depth < layer_depth get the layer
+    material, the others the half-space material."""
+    n = (2 * nz, 2 * nz, nz)
+    mesh = kuhn_box_mesh(n, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 0.0), periodic=(False, False, False),
+                         tags={"z+": 1})
+    v = mesh["vertices"]
+    rho = np.linalg.norm(v, axis=1)
+    k = np.log(grading) / np.sqrt(3.0)
+    scale = np.where(rho > 0, radius * (np.exp(k * rho) - 1.0) / (np.exp(k) - 1.0) / np.maximum(rho, 1e-300), 0.0)
+    mesh["vertices"] = v * scale[:, None]
+    depth = -mesh["vertices"][mesh["tets"]].mean(axis=1)[:, 2]
+    mats = np.where((depth < layer_depth)[:, None], LAYER_MATERIAL[None, :], HALFSPACE_MATERIAL[None, :])
+    return mesh, np.ascontiguousarray(mats)
+
+
+def uniform_box_mesh_for(n_target, extent=(20e3, 20e3, 10e3)):
+    """Kuhn box mesh with about n_target tetrahedra, n_x = n_y = 2 n_z,
+    free surface on top, absorbing elsewhere (the served-ensemble meshes)."""
+    nz = max(1, int(round((n_target / 24.0) ** (1.0 / 3.0))))
+    n = (2 * nz, 2 * nz, nz)
+    return kuhn_box_mesh(n, lo=(0.0, 0.0, -extent[2]), hi=(extent[0], extent[1], 0.0),
+                         periodic=(False, False, False), tags={"z+": 1})
