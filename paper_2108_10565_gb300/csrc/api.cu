@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "poro_internal.h"
+#include "tc_device.cuh"
 
 using poro::NQ;
 
@@ -159,6 +160,8 @@ void free_reference(poro_ctx* c) {
     dfree(c->mref.res_row);
     dfree(c->mref.res_col);
     dfree(c->mref.res_val);
+    dfree(c->mref.khat_tc);
+    dfree(c->mref.status);
     dfree(c->mref.zinv_f32);
     dfree(c->dref.khat_val);
     dfree(c->dref.khat_col);
@@ -294,12 +297,40 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             }
         }
         (void)T;
+        // tensor-core images (tf32 hi + lo, K-major core matrices) of the blocks
+        auto tf32 = [](float x) {
+            uint32_t b;
+            std::memcpy(&b, &x, 4);
+            b = (b + 0x1000u) & 0xFFFFE000u;  // nearest, ties away from zero
+            std::memcpy(&x, &b, 4);
+            return x;
+        };
+        std::vector<float> tci;
+        for (int g = 1; g <= degree_N; ++g) {
+            const int NP = poro::tc_np(g), KP = poro::tc_kp(g), o = poro::block_offset(g), d = poro::block_size(g);
+            for (int j = 0; j < 3; ++j) {
+                const size_t base = tci.size();
+                c->mref.tc_off[g][j] = (int32_t)base;
+                tci.resize(base + 2 * (size_t)NP * KP, 0.f);
+                for (int l = 0; l < o; ++l)
+                    for (int m = 0; m < d; ++m) {
+                        const double v = c->ref.khat[((size_t)j * B + l) * B + o + m];
+                        const float h = tf32((float)v);
+                        const size_t at = base + (size_t)poro::tc::kmajor_offset(l, m, KP);
+                        tci[at] = h;
+                        tci[at + (size_t)NP * KP] = tf32((float)(v - (double)h));
+                    }
+            }
+        }
         c->mref.base = &c->dref;
         if ((e = upload((void**)&c->mref.khat_val_f32, vf.data(), vf.size() * sizeof(float))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_row, rrow.data(), rrow.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_col, rcol.data(), rcol.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_val, rval.data(), rval.size() * sizeof(float))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.zinv_f32, zf.data(), zf.size() * sizeof(float))) != cudaSuccess) {
+            (e = upload((void**)&c->mref.zinv_f32, zf.data(), zf.size() * sizeof(float))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.khat_tc, tci.data(), tci.size() * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&c->mref.status, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMemset(c->mref.status, 0, sizeof(int32_t))) != cudaSuccess) {
             free_reference(c);
             cudaStreamDestroy(c->stream);
             delete c;
@@ -526,13 +557,29 @@ poro_status poro_lu_release(poro_ctx* c) {
     return PORO_OK;
 }
 
+// A kernel whose bounded wait gave up (tensor-core completion of the mixed
+// predictor) leaves a flag in device memory; the next synchronising call
+// reports it once.  Call only after the context's stream is idle.
+static poro_status device_status(poro_ctx* c, const char* who) {
+    if (!c->mref.status) return PORO_OK;
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->mref.status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    if (st == 0) return PORO_OK;
+    e = cudaMemsetAsync(c->mref.status, 0, sizeof st, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    return fail(c, PORO_ETIMEOUT, std::string(who) + ": a bounded tensor-core wait in the mixed predictor gave up");
+}
+
 poro_status poro_sync(poro_ctx* c, int32_t timeout_ms) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_sync: ctx is NULL");
     cudaSetDevice(c->device);
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(c->stream);
-        if (e == cudaSuccess) return PORO_OK;
+        if (e == cudaSuccess) return device_status(c, "poro_sync");
         if (e != cudaErrorNotReady) return cuda_fail(c, e, "poro_sync");
         if (timeout_ms >= 0) {
             auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -553,7 +600,7 @@ static poro_status copy_out(poro_ctx* c, const double* src, int64_t first, int64
                                     c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, who);
-    return PORO_OK;
+    return device_status(c, who);
 }
 
 poro_status poro_get_predictor(poro_ctx* c, int64_t first, int64_t count, double* out) {
@@ -1082,6 +1129,7 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
     if (rc == 0 && er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch / graph");
     if (er != cudaSuccess) return cuda_fail(c, er, "poro_advance");
+    if (poro_status st = device_status(c, "poro_advance")) return st;
     for (int r = 0; r < nrec; ++r) {
         const int cl = c->h_cl[c->rec_elem[r]];
         const int64_t len = (int64_t)1 << cl, ns = ticks / len;
@@ -1120,7 +1168,7 @@ poro_status poro_get_dofs(poro_ctx* c, double* Q_out) {
                                     cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "poro_get_dofs");
-    return PORO_OK;
+    return device_status(c, "poro_get_dofs");
 }
 
 poro_status poro_get_seismogram(poro_ctx* c, int32_t rec, int64_t cap, double* t_out, double* q_out, int64_t* n_out) {

@@ -18,6 +18,11 @@ enum { SXX, SYY, SZZ, SXY, SYZ, SXZ, QU, QV, QW, QP, QUF, QVF, QWF };
 constexpr int n_modes(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
 constexpr int block_size(int g) { return (g + 1) * (g + 2) / 2; }
 constexpr int block_offset(int g) { return g * (g + 1) * (g + 2) / 6; }
+// tensor-core tile of degree block g's Khat product: N extent (rows l < o_g,
+// a multiple of 16, at least 16) and K extent (columns of the block, a
+// multiple of 8)
+constexpr int tc_np(int g) { return block_offset(g) <= 16 ? 16 : (block_offset(g) + 15) / 16 * 16; }
+constexpr int tc_kp(int g) { return (block_size(g) + 7) / 8 * 8; }
 
 // Union sparsity pattern of A*, B*, C* (54 entries): for every row p the
 // columns q with a structurally non-zero Jacobian entry.  Rows are stored
@@ -126,6 +131,12 @@ struct MixedReference {
     int32_t* res_col = nullptr;     // column m
     float* res_val = nullptr;       // [nnz][2] Khat split into (hi, lo) binary32 words
     float* zinv_f32 = nullptr;      // [T][T]
+    // tensor-core images of Khat^j restricted to block g (rows l < o_g, columns
+    // of the block), K-major core-matrix layout of tc_np(g) x tc_kp(g) tf32
+    // words, hi image then lo image; tc_off[g][j] in floats
+    float* khat_tc = nullptr;
+    int32_t tc_off[MAX_N + 1][3] = {};
+    int32_t* status = nullptr;      // device word: 1 after a bounded wait gave up
 };
 
 // Launch the mixed-precision predictor (binary32 sweeps, `refine` residual

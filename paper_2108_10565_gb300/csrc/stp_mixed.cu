@@ -9,7 +9,18 @@
 //   d  = Alg3_f32(fl32(r));  Q = Q1 + d    (one sweep; a second repeats with
 //                                           Q1 + d in the residual)
 // The binary32 sweeps are Algorithm 3 (degree blocks, time solves with
-// (Z - E*_pp I)^{-1}, G coupling, star and Khat products) in float.  The
+// (Z - E*_pp I)^{-1}, G coupling, star and Khat products).  Their dominant
+// step, b[p, l, u] -= sum_j sum_m Khat^j[l, m] X^j[p, m, u] over the rows
+// l < o_g of degree block g, is a dense contraction whose left operand Khat is
+// the same for every element: it runs on the tensor cores (tcgen05.mma
+// kind::tf32, accumulator in TMEM) with both operands split into tf32 hi + lo
+// words and the three products hi*hi + hi*lo + lo*hi accumulated (binary32
+// accuracy).  One MMA tile per (g, j): M = 128 rows (p, u) of the element,
+// N = rows l (o_g rounded up to 16), K = columns m of the block (d_g rounded up
+// to 8).  X^j (A operand) is written by the star-product threads straight
+// into shared memory in the K-major core-matrix layout; the Khat^j block (B
+// operand, prebuilt on the host in the same layout) arrives by bulk copy while
+// the star products run.  The
 // residual needs ~47 significant bits because Y Q1 cancels b0 to ~1e-7; GB300
 // issues binary64 FMAs at ~1/60 of its binary32 rate, so the residual runs on
 // the binary32 pipe with error-free transformations: FMA-based exact products
@@ -25,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include "alg3_device.cuh"
+#include "tc_device.cuh"
 
 namespace poro {
 namespace {
@@ -42,6 +54,9 @@ struct K2Params {
     const int32_t* res_col;   // column m
     const float2* res_val;    // Khat value split (hi, lo)
     const float* zinv;        // Z^{-1} [T][T] binary32
+    const float* khat_tc;     // tensor-core images of the Khat^j blocks (hi then lo)
+    int32_t tc_off[MAX_N + 1][3];
+    int32_t* status;          // set to 1 if a bounded wait gave up
 };
 
 // star pattern tables for lane-varying lookups (copied to shared memory)
@@ -99,26 +114,165 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int NW = NT / 32;
     static constexpr int T_ = N + 1;
     static constexpr int R4(int x) { return (x + 3) & ~3; }
+    static constexpr int R32(int x) { return (x + 31) & ~31; }
     static constexpr int MAX2(int a, int b) { return a > b ? a : b; }
-    // shared layout in floats; the star products X of the sweeps (3 directions)
-    // and the per-warp Y buffers of the residual share one region
-    static constexpr int OFF_W = 0;
-    static constexpr int OFF_Q1 = R4(A::SQ);
-    static constexpr int OFF_D1 = OFF_Q1 + R4(A::SQ);
-    static constexpr int OFF_XY = OFF_D1 + (REF == 2 ? R4(A::SQ) : 0);
-    static constexpr int XY_SIZE = R4(MAX2(3 * NQ * A::XSMAX, NW * 3 * A::PT * 2));
-    static constexpr int OFF_B0 = OFF_XY + XY_SIZE;
-    static constexpr int OFF_SH = OFF_B0 + R4(2 * NQ * A::B);
+    // tensor-core operand tiles: A (X^j, hi and lo) with ceil(13 T / 8) row
+    // groups of the widest block, then the Khat^j image (hi and lo).  The MMA
+    // reads 16 row groups of each A tile; the rows past 13 T only feed
+    // accumulator rows that are never read, so they may overlap what follows.
+    static constexpr int SBOMAX = tc_kp(N) * 8;
+    static constexpr int AH = (A::PT + 7) / 8 * SBOMAX;
+    static constexpr int BIMG = 2 * tc_np(N) * tc_kp(N);
+    static constexpr int TC_SIZE = MAX2(2 * AH + BIMG, AH + 16 * SBOMAX);
+    // shared layout in floats; the tensor-core tiles of the sweeps and the
+    // per-warp Y buffers of the residual share the first region
+    static constexpr int OFF_XY = 0;
+    static constexpr int XY_SIZE = R32(MAX2(TC_SIZE, NW * 3 * A::PT * 2));
+    static constexpr int OFF_W = OFF_XY + XY_SIZE;
+    static constexpr int OFF_Q1 = OFF_W + R4(A::SQ);
+    static constexpr int OFF_D1 = OFF_Q1 + (REF >= 1 ? R4(A::SQ) : 0);
+    static constexpr int OFF_SH = OFF_D1 + (REF == 2 ? R4(A::SQ) : 0);
     static constexpr int OFF_SL = OFF_SH + R4(3 * STAR_NNZ);
     static constexpr int OFF_ZIN = OFF_SL + R4(3 * STAR_NNZ);
     static constexpr int OFF_ZUF = OFF_ZIN + R4(T_ * T_);
     static constexpr int OFF_ZI = OFF_ZUF + R4(T_ * T_);
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
-    static constexpr int SMEM_FLOATS = OFF_TAB + R4(NQ + 1 + STAR_NNZ);
+    static constexpr int OFF_BAR = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // 2 mbarriers, TMEM slot, abort flag
+    static constexpr int SMEM_FLOATS = OFF_BAR + 8;
+    static constexpr int TMEM_COLS = tc_np(N) <= 32 ? 32 : (tc_np(N) <= 64 ? 64 : 128);
+    static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
+    static_assert(NW == 2 || NW == 4 || NW == 8, "2, 4 or 8 warps");
 };
 
+// Tensor-core state of one CTA (shared addresses, barrier phases)
+struct TcState {
+    float* ah;
+    float* al;
+    uint32_t ah_s, al_s, b_s;
+    uint32_t mma_bar, ld_bar;
+    uint32_t tmem;
+    uint32_t mph, lph;
+    volatile int* abort;
+};
+
+// One binary32 sweep of Algorithm 3 with the Khat products on the tensor
+// cores.  On entry bq holds b, on exit Q.  Returns false (uniformly across the
+// CTA) if a bounded wait gave up.
+template <int N, int NT>
+__device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, const float* zin, const float gcoup,
+                              const K2Params& P, TcState& S) {
+    using A = Alg3Shape<N>;
+    constexpr int T = A::T, QS = A::QS, PT = A::PT, NW = NT / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
+    for (int g = N; g >= 0; --g) {
+        const int o = block_offset(g), d = block_size(g);
+        // time solves of block g: 7 plain rows (6 stresses, p) and 3 coupled
+        // pairs (u_f then u, v_f then v, w_f then w) per mode
+        for (int it = tid; it < 10 * d; it += NT) {
+            const int kind = it / d, m = o + it % d;
+            if (kind < 7) {
+                const int p = kind < 6 ? kind : QP;
+                solve_row<T>(bq + p * QS + m * T, zin);
+            } else {
+                const int i = kind - 7;
+                float* rf = bq + (QUF + i) * QS + m * T;
+                float* rv = bq + (QU + i) * QS + m * T;
+                solve_row<T>(rf, zuf);
+#pragma unroll
+                for (int u = 0; u < T; ++u) rv[u] = fmaf(gcoup, rf[u], rv[u]);
+                solve_row<T>(rv, zin);
+            }
+        }
+        __syncthreads();
+        if (g == 0) break;
+        const int KP = tc_kp(g), NP = tc_np(g);
+        const uint32_t sbo = (uint32_t)KP * 32u;
+        const uint32_t half = (uint32_t)(NP * KP) * 4u;
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j) {
+            if (j > 0) {  // the previous direction's MMAs have read A and B
+                if (!tc::mbar_wait(S.mma_bar, S.mph)) *S.abort = 1;
+                S.mph ^= 1;
+            }
+            if (tid == 0) {
+                tc::fence_async_smem();
+                tc::mbar_expect_tx(S.ld_bar, 2u * half);
+                tc::bulk_g2s(S.b_s, P.khat_tc + P.tc_off[g][j], 2u * half, S.ld_bar);
+            }
+            // X^j[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u], stored as tf32 hi + lo
+            const float* sj = star + j * STAR_NNZ;
+            for (int it = tid; it < d * T; it += NT) {
+                const int ml = it / T, u = it % T;
+                float qv[NQ], acc[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    qv[q] = bq[q * QS + (o + ml) * T + u];
+                    acc[q] = 0.f;
+                }
+#pragma unroll
+                for (int n = 0; n < STAR_NNZ; ++n) acc[star_row(n)] = fmaf(sj[n], qv[star_col(n)], acc[star_row(n)]);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int at = tc::kmajor_offset(q * T + u, ml, KP);
+                    const float h = tc::to_tf32(acc[q]);
+                    S.ah[at] = h;
+                    S.al[at] = acc[q] - h;
+                }
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (*S.abort) return false;
+            if (tid == 0) {
+                if (!tc::mbar_wait(S.ld_bar, S.lph)) *S.abort = 1;
+                S.lph ^= 1;
+                tc::fence_after_sync();
+                const uint32_t id = tc::idesc_tf32(128, NP);
+#pragma unroll 1
+                for (int kk = 0; kk < KP / 8; ++kk) {
+                    const uint32_t ko = (uint32_t)kk * 256u;  // 8 tf32 = two core matrices, 128 B apart
+                    tc::mma_tf32(S.tmem, tc::smem_desc(S.al_s + ko, sbo), tc::smem_desc(S.b_s + ko, sbo), id,
+                                 (j | kk) != 0);
+                    tc::mma_tf32(S.tmem, tc::smem_desc(S.ah_s + ko, sbo), tc::smem_desc(S.b_s + half + ko, sbo), id, 1u);
+                    tc::mma_tf32(S.tmem, tc::smem_desc(S.ah_s + ko, sbo), tc::smem_desc(S.b_s + ko, sbo), id, 1u);
+                }
+                tc::mma_commit(S.mma_bar);
+            }
+        }
+        if (!tc::mbar_wait(S.mma_bar, S.mph)) *S.abort = 1;
+        S.mph ^= 1;
+        tc::fence_after_sync();
+        // b[p, l, u] -= D[(p, u), l]: warp w reads TMEM lanes 32 (w % 4) ...,
+        // with 8 warps the two warps of a lane quarter split the columns
+        {
+            const int sp = warp & 3;
+            const int ncol = NW == 8 ? NP / 2 : NP;
+            const int c_begin = NW == 8 ? (warp >> 2) * ncol : 0;
+            if (sp * 32 < PT) {
+                const int r = sp * 32 + lane;
+                const int p = r / T, u = r - (r / T) * T;
+                float* dst = bq + p * QS + u;
+#pragma unroll 1
+                for (int c0 = c_begin; c0 < c_begin + ncol && c0 < o; c0 += 8) {
+                    float v[8];
+                    tc::tmem_ld8(S.tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
+                    if (r < PT) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (c0 + q < o) dst[(c0 + q) * T] -= v[q];
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (*S.abort) return false;
+    }
+    return true;
+}
+
 template <int N, int REF, int NT_>
-__device__ void residual(float* W, const float* Q1, const float* D1, const float2* b0, const float* sh,
+__device__ void residual(float* W, const float* Q1, const float* D1, const double* q0, const float* sh,
                          const float* sl, const float* zi, const int* tab, float2 e_dw, float2 g_dw, float2* Yall,
                          const K2Params& P) {
     using S = K2Shape<N, REF, NT_>;
@@ -169,7 +323,7 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
                 const int p = pu / T, u = pu % T;
                 const int base = p * QS + l * T;
                 float h = 0.f, lo = 0.f;
-                const float2 bv = b0[p * B + l];
+                const float2 bv = dw_split(__ldg(q0 + p * B + l));
                 const float sw = (float)((2 * u + 1) * ((u & 1) ? -1 : 1));
                 dw_mac(h, lo, sw, 0.f, bv.x, bv.y);
                 // - sum_s Z_us Q[p, l, s]   (Z entries are exact small integers)
@@ -207,33 +361,62 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
         }
         __syncwarp();
     }
+    // the Y buffers share memory with the tensor-core tiles that bulk copies
+    // and MMAs touch next
+    tc::fence_async_smem();
 }
 
 template <int N, int REF, int NT_>
 __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixed_kernel(const K2Params P) {
     using S = K2Shape<N, REF, NT_>;
     constexpr int B = S::B, T = S::T, NT = S::NT, QBT = S::QBT, QS = S::QS;
-    extern __shared__ float smf[];
+    extern __shared__ __align__(1024) float smf[];
     float* W = smf + S::OFF_W;
     float* Q1 = smf + S::OFF_Q1;
     float* D1 = smf + S::OFF_D1;
-    float* X = smf + S::OFF_XY;
     float2* Yall = reinterpret_cast<float2*>(smf + S::OFF_XY);
-    float2* b0 = reinterpret_cast<float2*>(smf + S::OFF_B0);
     float* sh = smf + S::OFF_SH;
     float* sl = smf + S::OFF_SL;
     float* zin = smf + S::OFF_ZIN;
     float* zuf = smf + S::OFF_ZUF;
     float* zi = smf + S::OFF_ZI;
     int* tab = reinterpret_cast<int*>(smf + S::OFF_TAB);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::OFF_BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 4);
+    volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 5);
     const int tid = threadIdx.x;
 
+    TcState tcs;
+    tcs.ah = smf + S::OFF_XY;
+    tcs.al = tcs.ah + S::AH;
+    tcs.ah_s = tc::smem_addr(tcs.ah);
+    tcs.al_s = tc::smem_addr(tcs.al);
+    tcs.b_s = tc::smem_addr(tcs.al + S::AH);
+    tcs.mma_bar = tc::smem_addr(bars);
+    tcs.ld_bar = tc::smem_addr(bars + 1);
+    tcs.mph = tcs.lph = 0;
+    tcs.abort = abort;
+
+    // operand region starts finite (K padding of A meets zeros of B)
+    for (int i = tid; i < S::XY_SIZE; i += NT) smf[S::OFF_XY + i] = 0.f;
     for (int i = tid; i < T * T; i += NT) {
         zin[i] = P.zinv[i];
         const int u = i / T, s = i % T;
         zi[i] = (float)((2 * u + 1) * ((u > s && ((u - s) & 1)) ? -1 : 1));  // Z = S^{-1}(W - K^tau)
     }
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
+    if (tid == 0) {
+        *abort = 0;
+        tc::mbar_init(tcs.mma_bar, 1);
+        tc::mbar_init(tcs.ld_bar, 1);
+        tc::mbar_init_fence();
+    }
+    if (tid < 32) tc::tmem_alloc(tc::smem_addr(tslot), S::TMEM_COLS);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tcs.tmem = *tslot;
 
     for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
@@ -248,39 +431,41 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         const double* scal = ec + 3 * STAR_NNZ + T * T;
         const float2 e_dw = dw_split(scal[0]), g_dw = dw_split(scal[1]);
         const double dt = scal[2];
-        for (int i = tid; i < NQ * B; i += NT) b0[i] = dw_split(q0[i]);
-        __syncthreads();
-        // Q1 = Alg3_f32(b0)
+        // Q1 = Alg3_f32(b0), b0[p, l, u] = (S^{-1} w)_u q0[p, l]
         for (int i = tid; i < NQ * B; i += NT) {
-            const float v = b0[i].x;
+            const float v = (float)q0[i];
             float* row = W + (i / B) * QS + (i % B) * T;
 #pragma unroll
             for (int u = 0; u < T; ++u) row[u] = (float)((2 * u + 1) * ((u & 1) ? -1 : 1)) * v;
         }
         __syncthreads();
-        alg3_sweep<N, NT, float, 3>(W, X, sh, zuf, zin, g_dw.x, P.khat);
-        for (int i = tid; i < S::SQ; i += NT) {
-            Q1[i] = W[i];
-            if (REF == 2) D1[i] = 0.f;
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int sweep = 1; sweep <= REF; ++sweep) {
-            residual<N, REF, NT_>(W, Q1, D1, b0, sh, sl, zi, tab, e_dw, g_dw, Yall, P);
+        if (!alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
+        if (REF >= 1) {
+            for (int i = tid; i < S::SQ; i += NT) {
+                Q1[i] = W[i];
+                if (REF == 2) D1[i] = 0.f;
+            }
             __syncthreads();
-            alg3_sweep<N, NT, float, 3>(W, X, sh, zuf, zin, g_dw.x, P.khat);
-            if (REF == 2 && sweep == 1) {
+        }
+        bool ok = true;
+#pragma unroll 1
+        for (int sweep = 1; sweep <= REF && ok; ++sweep) {
+            residual<N, REF, NT_>(W, Q1, D1, q0, sh, sl, zi, tab, e_dw, g_dw, Yall, P);
+            __syncthreads();
+            ok = alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs);
+            if (ok && REF == 2 && sweep == 1) {
                 for (int i = tid; i < S::SQ; i += NT) D1[i] = W[i];
                 __syncthreads();
             }
         }
+        if (!ok) break;
         // Q = Q1 (+ d1) (+ d2) in binary64; time integration
         if (P.qt || P.iout) {
             double* qo = P.qt ? P.qt + e * (int64_t)QBT : nullptr;
             double* io = P.iout ? P.iout + e * (int64_t)(NQ * B) : nullptr;
             for (int i = tid; i < QBT; i += NT) {
                 const int si = (i / (B * T)) * QS + i % (B * T);
-                double v = (double)Q1[si];
+                double v = (double)(REF >= 1 ? Q1[si] : W[si]);
                 if (REF == 2) v += (double)D1[si];
                 if (REF >= 1) v += (double)W[si];
                 if (qo) qo[i] = v;
@@ -289,6 +474,10 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         }
         __syncthreads();
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abort && P.status) atomicExch(P.status, 1);
+    if (tid < 32) tc::tmem_dealloc(tcs.tmem, S::TMEM_COLS);
 }
 
 template <int N, int REF, int NT_>
@@ -312,9 +501,23 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     P.res_col = ref.res_col;
     P.res_val = reinterpret_cast<const float2*>(ref.res_val);
     P.zinv = ref.zinv_f32;
-    const size_t smem = sizeof(float) * S::SMEM_FLOATS;
-    cudaError_t err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    P.khat_tc = ref.khat_tc;
+    for (int g = 0; g <= MAX_N; ++g)
+        for (int j = 0; j < 3; ++j) P.tc_off[g][j] = ref.tc_off[g][j];
+    P.status = ref.status;
+    // one CTA per element; every resident CTA holds TMEM_COLS columns of the
+    // SM's 512, so the shared-memory request is raised where needed to keep
+    // at most 512 / TMEM_COLS CTAs of this kernel resident on an SM (so none
+    // of them waits for TMEM)
+    int dev = 0, sm_smem = 0, reserved = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (err != cudaSuccess) return (int)err;
+    size_t smem = sizeof(float) * S::SMEM_FLOATS;
+    const size_t floor_smem = (size_t)sm_smem / (512 / S::TMEM_COLS + 1) + 64;
+    if (smem + (size_t)reserved < floor_smem) smem = floor_smem - (size_t)reserved;
+    err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
