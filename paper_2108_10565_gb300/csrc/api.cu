@@ -3,10 +3,12 @@
 // on the host beyond the per-element set-up of constants.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
@@ -156,10 +158,12 @@ void free_reference(poro_ctx* c) {
     dfree(c->lref.krow);
     dfree(c->lref.kcol);
     dfree(c->lref.kval);
-    dfree(c->mref.khat_val_f32);
     dfree(c->mref.res_row);
-    dfree(c->mref.res_col);
-    dfree(c->mref.res_val);
+    dfree(c->mref.res_int);
+    dfree(c->mref.res_inv);
+    dfree(c->mref.res_order8);
+    dfree(c->mref.res_order4);
+    dfree(c->mref.res_order2);
     dfree(c->mref.khat_tc);
     dfree(c->mref.status);
     dfree(c->mref.zinv_f32);
@@ -191,6 +195,34 @@ void ctx_set_error(poro_ctx* c, const std::string& msg) {
 extern "C" {
 
 const char* poro_last_error(const poro_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+// x = num / den with den <= 10^6 (continued-fraction convergents), if x is
+// such a rational to 1e-14 relative
+static bool rational_of(double x, int64_t& num, int64_t& den) {
+    const double ax = std::fabs(x);
+    int64_t h0 = 0, h1 = 1, k0 = 1, k1 = 0;
+    double r = ax;
+    for (int it = 0; it < 64; ++it) {
+        const double a = std::floor(r);
+        if (a > 9.0e15) break;
+        const int64_t ai = (int64_t)a;
+        const int64_t h2 = ai * h1 + h0, k2 = ai * k1 + k0;
+        if (k2 > 1000000) break;
+        h0 = h1;
+        h1 = h2;
+        k0 = k1;
+        k1 = k2;
+        if (std::fabs((double)h1 / (double)k1 - ax) <= 1e-14 * ax) {
+            num = x < 0 ? -h1 : h1;
+            den = k1;
+            return true;
+        }
+        const double f = r - a;
+        if (f <= 0.0) break;
+        r = 1.0 / f;
+    }
+    return false;
+}
 
 poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out) {
     if (!out) return fail(nullptr, PORO_EINVAL, "poro_create: out is NULL");
@@ -276,27 +308,85 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
         }
     }
     if (precision == PORO_FP32_REFINE) {
-        // binary32 copies for the sweeps and the (hi, lo) full-row CSR of the residual
-        const int B = c->B, T = c->T;
-        std::vector<float> vf(val.begin(), val.end()), zf(c->ref.zinv.begin(), c->ref.zinv.end());
-        std::vector<int32_t> rrow, rcol;
-        std::vector<float> rval;
-        for (int j = 0; j < 3; ++j) {
-            rrow.push_back((int32_t)rcol.size());
-            for (int l = 0; l < B; ++l) {
+        // Residual CSR of Khat^j (all rows): every row l of every Khat^j is an
+        // integer row over a common denominator d (the reference matrices are
+        // rational with small denominators), so an entry is packed as
+        // (numerator << 7) | column, exact in binary32, and the row carries
+        // 1/d as a double-binary32 pair.
+        const int B = c->B;
+        std::vector<float> zf(c->ref.zinv.begin(), c->ref.zinv.end());
+        std::vector<int32_t> rrow, rint;
+        std::vector<float> rinv;
+        std::string rerr;
+        for (int j = 0; j < 3 && rerr.empty(); ++j) {
+            rrow.push_back((int32_t)rint.size());
+            for (int l = 0; l < B && rerr.empty(); ++l) {
+                const double* row = c->ref.khat.data() + ((size_t)j * B + l) * B;
+                int64_t d = 1;
                 for (int m = 0; m < B; ++m) {
-                    const double v = c->ref.khat[((size_t)j * B + l) * B + m];
-                    if (v != 0.0) {
-                        const float h = (float)v;
-                        rcol.push_back(m);
-                        rval.push_back(h);
-                        rval.push_back((float)(v - (double)h));
+                    int64_t num = 0, den = 1;
+                    if (row[m] == 0.0) continue;
+                    if (!rational_of(row[m], num, den)) {
+                        rerr = "Khat entry is not a small-denominator rational";
+                        break;
+                    }
+                    d = d / std::gcd(d, den) * den;
+                    if (d > (1 << 30)) {
+                        rerr = "Khat row denominator too large";
+                        break;
                     }
                 }
-                rrow.push_back((int32_t)rcol.size());
+                for (int m = 0; m < B && rerr.empty(); ++m) {
+                    if (row[m] == 0.0) continue;
+                    const double cv = row[m] * (double)d;
+                    const int64_t ci = std::llround(cv);
+                    if (std::fabs(cv - (double)ci) > 1e-6 || std::llabs(ci) >= (1 << 23)) {
+                        rerr = "Khat numerator out of range";
+                        break;
+                    }
+                    rint.push_back((int32_t)(((uint32_t)(int32_t)ci << 7) | (uint32_t)m));
+                }
+                const double inv = 1.0 / (double)d;
+                const float ih = (float)inv;
+                rinv.push_back(ih);
+                rinv.push_back((float)(inv - (double)ih));
+                rrow.push_back((int32_t)rint.size());
             }
         }
-        (void)T;
+        // residual row order per warp count: a row costs its Khat entries (all
+        // directions) plus a fixed share for the star and time terms
+        auto deal = [&](int warps) {
+            std::vector<std::pair<int64_t, int>> w;
+            for (int l = 0; l < B; ++l) {
+                int64_t cost = 40;
+                for (int j = 0; j < 3; ++j) cost += rrow[j * (B + 1) + l + 1] - rrow[j * (B + 1) + l];
+                w.push_back({cost, l});
+            }
+            std::sort(w.begin(), w.end(), [](auto& a, auto& b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
+            std::vector<std::vector<int>> lists(warps);
+            std::vector<int64_t> load(warps, 0);
+            for (auto& [cost, l] : w) {
+                int best = 0;
+                for (int k = 1; k < warps; ++k)
+                    if (load[k] < load[best]) best = k;
+                load[best] += cost;
+                lists[best].push_back(l);
+            }
+            // [warps + 1] list starts, then the lists one after another
+            std::vector<int32_t> out(warps + 1, 0);
+            for (int k = 0; k < warps; ++k) {
+                out[k + 1] = out[k] + (int32_t)lists[k].size();
+            }
+            for (int k = 0; k < warps; ++k) out.insert(out.end(), lists[k].begin(), lists[k].end());
+            return out;
+        };
+        const std::vector<int32_t> ord8 = deal(8), ord4 = deal(4), ord2 = deal(2);
+        if (!rerr.empty()) {
+            free_reference(c);
+            cudaStreamDestroy(c->stream);
+            delete c;
+            return fail(nullptr, PORO_ENUMERIC, "poro_create: " + rerr);
+        }
         // tensor-core images (tf32 hi + lo, K-major core matrices) of the blocks
         auto tf32 = [](float x) {
             uint32_t b;
@@ -323,10 +413,12 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             }
         }
         c->mref.base = &c->dref;
-        if ((e = upload((void**)&c->mref.khat_val_f32, vf.data(), vf.size() * sizeof(float))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.res_row, rrow.data(), rrow.size() * sizeof(int32_t))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.res_col, rcol.data(), rcol.size() * sizeof(int32_t))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.res_val, rval.data(), rval.size() * sizeof(float))) != cudaSuccess ||
+        if ((e = upload((void**)&c->mref.res_row, rrow.data(), rrow.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_int, rint.data(), rint.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_inv, rinv.data(), rinv.size() * sizeof(float))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_order8, ord8.data(), ord8.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_order4, ord4.data(), ord4.size() * sizeof(int32_t))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.res_order2, ord2.data(), ord2.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.zinv_f32, zf.data(), zf.size() * sizeof(float))) != cudaSuccess ||
             (e = upload((void**)&c->mref.khat_tc, tci.data(), tci.size() * sizeof(float))) != cudaSuccess ||
             (e = cudaMalloc((void**)&c->mref.status, sizeof(int32_t))) != cudaSuccess ||

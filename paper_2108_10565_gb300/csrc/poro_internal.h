@@ -126,10 +126,14 @@ struct DeviceReference {
 // Extra device data of the mixed-precision (refinement) path.
 struct MixedReference {
     const DeviceReference* base = nullptr;
-    float* khat_val_f32 = nullptr;  // block CSR values in binary32 (same col/row as base)
     int32_t* res_row = nullptr;     // [3][B+1] full-row CSR of Khat^j, absolute offsets
-    int32_t* res_col = nullptr;     // column m
-    float* res_val = nullptr;       // [nnz][2] Khat split into (hi, lo) binary32 words
+    int32_t* res_int = nullptr;     // (numerator << 7) | column m; Khat^j[l, m] = numerator / d_jl
+    float* res_inv = nullptr;       // [3][B][2] 1 / d_jl as (hi, lo) binary32 words
+    // residual rows dealt to 8, 4 and 2 warps (longest work first, each row to
+    // the least loaded warp): [warps + 1] list starts, then the lists
+    int32_t* res_order8 = nullptr;
+    int32_t* res_order4 = nullptr;
+    int32_t* res_order2 = nullptr;
     float* zinv_f32 = nullptr;      // [T][T]
     // tensor-core images of Khat^j restricted to block g (rows l < o_g, columns
     // of the block), K-major core-matrix layout of tc_np(g) x tc_kp(g) tf32

@@ -49,15 +49,19 @@ struct K2Params {
     double* iout;
     int64_t count;
     int stride;
-    KhatBlocks<float> khat;   // block CSR, binary32 values (for the sweeps)
     const int32_t* res_row;   // [3][B+1] full-row CSR of Khat^j (absolute offsets)
-    const int32_t* res_col;   // column m
-    const float2* res_val;    // Khat value split (hi, lo)
+    const int32_t* res_int;   // (numerator << 7) | column: Khat^j[l, m] = numerator / d_jl
+    const float2* res_inv;    // [3][B] 1 / d_jl as (hi, lo)
+    const int32_t* res_order; // [warps + 1] list starts, then each warp's residual rows
     const float* zinv;        // Z^{-1} [T][T] binary32
     const float* khat_tc;     // tensor-core images of the Khat^j blocks (hi then lo)
     int32_t tc_off[MAX_N + 1][3];
     int32_t* status;          // set to 1 if a bounded wait gave up
 };
+
+// residual star terms per row p: 3 directions x 6 slots (rows have 2, 4 or 6
+// entries; unused slots carry a zero coefficient)
+constexpr int STAR_SLOTS = 18;
 
 // star pattern tables for lane-varying lookups (copied to shared memory)
 __constant__ int c_star_tab[NQ + 1 + STAR_NNZ] = {
@@ -88,6 +92,29 @@ __device__ __forceinline__ void dw_mac1(float& h, float& l, float ah, float al, 
     const float p = __fmul_rn(ah, b);
     float e = __fmaf_rn(ah, b, -p);
     e = __fmaf_rn(al, b, e);
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(er, e));
+}
+
+// acc += a * b with a exact (no low word)
+__device__ __forceinline__ void dw_mac_x(float& h, float& l, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(er, e));
+}
+
+// acc += a * (bh + bl) with a exact
+__device__ __forceinline__ void dw_mac_x2(float& h, float& l, float a, float bh, float bl) {
+    const float p = __fmul_rn(a, bh);
+    float e = __fmaf_rn(a, bh, -p);
+    e = __fmaf_rn(a, bl, e);
     const float s = __fadd_rn(h, p);
     const float bb = __fsub_rn(s, h);
     const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
@@ -129,15 +156,18 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int OFF_XY = 0;
     static constexpr int XY_SIZE = R32(MAX2(TC_SIZE, NW * 3 * A::PT * 2));
     static constexpr int OFF_W = OFF_XY + XY_SIZE;
+    static constexpr int Q1S = A::PT;                       // mode stride of Q1 / D1
+    static constexpr int Q1SIZE = R4(A::B * Q1S + 32);       // + slack read by idle lanes
     static constexpr int OFF_Q1 = OFF_W + R4(A::SQ);
-    static constexpr int OFF_D1 = OFF_Q1 + (REF >= 1 ? R4(A::SQ) : 0);
-    static constexpr int OFF_SH = OFF_D1 + (REF == 2 ? R4(A::SQ) : 0);
+    static constexpr int OFF_D1 = OFF_Q1 + (REF >= 1 ? Q1SIZE : 0);
+    static constexpr int OFF_SH = OFF_D1 + (REF == 2 ? Q1SIZE : 0);
     static constexpr int OFF_SL = OFF_SH + R4(3 * STAR_NNZ);
     static constexpr int OFF_ZIN = OFF_SL + R4(3 * STAR_NNZ);
     static constexpr int OFF_ZUF = OFF_ZIN + R4(T_ * T_);
     static constexpr int OFF_ZI = OFF_ZUF + R4(T_ * T_);
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
-    static constexpr int OFF_BAR = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // 2 mbarriers, TMEM slot, abort flag
+    static constexpr int OFF_STAB = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // float4 [13][STAR_SLOTS]
+    static constexpr int OFF_BAR = OFF_STAB + 4 * NQ * STAR_SLOTS;  // 2 mbarriers, TMEM slot, abort flag
     static constexpr int SMEM_FLOATS = OFF_BAR + 8;
     static constexpr int TMEM_COLS = tc_np(N) <= 32 ? 32 : (tc_np(N) <= 64 ? 64 : 128);
     static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
@@ -271,48 +301,58 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
     return true;
 }
 
+// Q1 / D1 layout of the residual: mode-major, Q[m * Q1S + p * T + u], so the
+// (q, u) lanes of one mode are consecutive words
 template <int N, int REF, int NT_>
-__device__ void residual(float* W, const float* Q1, const float* D1, const double* q0, const float* sh,
-                         const float* sl, const float* zi, const int* tab, float2 e_dw, float2 g_dw, float2* Yall,
-                         const K2Params& P) {
+__device__ void residual(float* W, const float* Q1, const float* D1, const float4* stab, const float* zi,
+                         float2 e_dw, float2 g_dw, float2* Yall, const K2Params& P) {
     using S = K2Shape<N, REF, NT_>;
-    constexpr int B = S::B, T = S::T, PT = S::PT, PUL = S::PUL, QS = S::QS;
+    constexpr int B = S::B, T = S::T, PT = S::PT, PUL = S::PUL, QS = S::QS, Q1S = S::Q1S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* Y = Yall + warp * 3 * PT;
-    const int* srp = tab;
-    const int* scol = tab + NQ + 1;
+    const int i0 = __ldg(P.res_order + warp), i1 = __ldg(P.res_order + warp + 1);
 #pragma unroll 1
-    for (int l = warp; l < B; l += S::NW) {
-        // R1: Y^j[q, u] = sum_m Khat^j[l, m] Q[q, m, u]
+    for (int i = i0; i < i1; ++i) {
+        const int l = __ldg(P.res_order + S::NW + 1 + i);  // this warp's rows (balanced lists)
+        // R1: Y^j[q, u] = (1 / d_jl) sum_m c_jlm Q[q, m, u] with integer
+        // numerators c (exact in binary32, so every product is an exact
+        // FMA-based pair); each entry is loaded one step ahead
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             float yh[PUL], yl[PUL];
-            int off[PUL];
 #pragma unroll
-            for (int k = 0; k < PUL; ++k) {
-                yh[k] = yl[k] = 0.f;
-                const int pu = lane + 32 * k;
-                const int q = pu / T, u = pu % T;
-                off[k] = pu < PT ? q * QS + u : 0;
-            }
+            for (int k = 0; k < PUL; ++k) yh[k] = yl[k] = 0.f;
             const int n0 = __ldg(P.res_row + j * (B + 1) + l), n1 = __ldg(P.res_row + j * (B + 1) + l + 1);
+            int nx = n0 < n1 ? __ldg(P.res_int + n0) : 0;
             for (int n = n0; n < n1; ++n) {
-                const float2 kv = __ldg(P.res_val + n);
-                const int mo = __ldg(P.res_col + n) * T;
+                const int kv = nx;
+                if (n + 1 < n1) nx = __ldg(P.res_int + n + 1);
+                const float cv = (float)(kv >> 7);
+                const int mo = (kv & 127) * Q1S + lane;
 #pragma unroll
                 for (int k = 0; k < PUL; ++k) {
-                    const int a = off[k] + mo;
                     if (REF == 2)
-                        dw_mac(yh[k], yl[k], kv.x, kv.y, Q1[a], D1[a]);
+                        dw_mac_x2(yh[k], yl[k], cv, Q1[mo + 32 * k], D1[mo + 32 * k]);
                     else
-                        dw_mac1(yh[k], yl[k], kv.x, kv.y, Q1[a]);
+                        dw_mac_x(yh[k], yl[k], cv, Q1[mo + 32 * k]);
                 }
             }
+            const float2 inv = __ldg(P.res_inv + j * B + l);
 #pragma unroll
             for (int k = 0; k < PUL; ++k) {
                 const int pu = lane + 32 * k;
-                if (pu < PT) Y[j * PT + pu] = make_float2(yh[k], yl[k]);
+                float h = 0.f, lo = 0.f;
+                dw_mac(h, lo, inv.x, inv.y, yh[k], yl[k]);
+                if (pu < PT) Y[j * PT + pu] = make_float2(h, lo);
             }
+        }
+        // b0[p, l] (hi, lo) sits in W[p, l, 0..1]; read before row l is written
+        float2 bv[PUL];
+#pragma unroll
+        for (int k = 0; k < PUL; ++k) {
+            const int pu = lane + 32 * k;
+            const int p = pu < PT ? pu / T : 0;
+            bv[k] = make_float2(W[p * QS + l * T], W[p * QS + l * T + 1]);
         }
         __syncwarp();
         // R2: assemble r[p, l, u]
@@ -321,42 +361,37 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const doubl
             const int pu = lane + 32 * k;
             if (pu < PT) {
                 const int p = pu / T, u = pu % T;
-                const int base = p * QS + l * T;
+                const int bq = l * Q1S + p * T;
                 float h = 0.f, lo = 0.f;
-                const float2 bv = dw_split(__ldg(q0 + p * B + l));
                 const float sw = (float)((2 * u + 1) * ((u & 1) ? -1 : 1));
-                dw_mac(h, lo, sw, 0.f, bv.x, bv.y);
+                dw_mac_x2(h, lo, sw, bv[k].x, bv[k].y);
                 // - sum_s Z_us Q[p, l, s]   (Z entries are exact small integers)
 #pragma unroll
                 for (int s = 0; s < T; ++s) {
                     if (REF == 2)
-                        dw_mac(h, lo, -zi[u * T + s], 0.f, Q1[base + s], D1[base + s]);
+                        dw_mac_x2(h, lo, -zi[u * T + s], Q1[bq + s], D1[bq + s]);
                     else
-                        dw_mac1(h, lo, -zi[u * T + s], 0.f, Q1[base + s]);
+                        dw_mac_x(h, lo, -zi[u * T + s], Q1[bq + s]);
                 }
                 // + E*_pp Q[p, l, u] (u_f rows) and + G Q[u_f, l, u] (u rows)
                 if (p >= QUF || (p >= QU && p <= QW)) {
-                    const int src = p >= QUF ? base + u : (p + 4) * QS + l * T + u;
+                    const int src = p >= QUF ? bq + u : l * Q1S + (p + 4) * T + u;
                     const float2 c = p >= QUF ? e_dw : g_dw;
                     if (REF == 2)
                         dw_mac(h, lo, c.x, c.y, Q1[src], D1[src]);
                     else
                         dw_mac1(h, lo, c.x, c.y, Q1[src]);
                 }
-                // - sum_j sum_q A^{j*}_pq Y^j[q, u]
-                const int r0 = srp[p], r1 = srp[p + 1];
+                // - sum_j sum_q A^{j*}_pq Y^j[q, u]: row p's 18 padded entries
+                // (-coef hi, -coef lo, offset of Y^j[q, 0])
+                const float4* st = stab + p * STAR_SLOTS;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) {
-                        const int idx = r0 + t;
-                        if (idx < r1) {
-                            const float2 yv = Y[j * PT + scol[idx] * T + u];
-                            dw_mac(h, lo, -sh[j * STAR_NNZ + idx], -sl[j * STAR_NNZ + idx], yv.x, yv.y);
-                        }
-                    }
+                for (int t = 0; t < STAR_SLOTS; ++t) {
+                    const float4 c = st[t];
+                    const float2 yv = Y[__float_as_int(c.z) + u];
+                    dw_mac(h, lo, c.x, c.y, yv.x, yv.y);
                 }
-                W[base + u] = __fadd_rn(h, lo);
+                W[p * QS + l * T + u] = __fadd_rn(h, lo);
             }
         }
         __syncwarp();
@@ -364,6 +399,24 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const doubl
     // the Y buffers share memory with the tensor-core tiles that bulk copies
     // and MMAs touch next
     tc::fence_async_smem();
+}
+
+// Save the sweep result W into dst (mode-major layout) and put the
+// double-binary32 split of b0 = q0 into W[p, l, 0..1] for the residual
+template <int N, int REF, int NT_>
+__device__ void stash_sweep(float* dst, float* W, const double* q0) {
+    using S = K2Shape<N, REF, NT_>;
+    constexpr int B = S::B, T = S::T, QS = S::QS, Q1S = S::Q1S;
+    for (int i = threadIdx.x; i < NQ * B; i += NT_) {
+        const int p = i / B, l = i - (i / B) * B;
+        float* w = W + p * QS + l * T;
+        float* d = dst + l * Q1S + p * T;
+#pragma unroll
+        for (int u = 0; u < T; ++u) d[u] = w[u];
+        const float2 b = dw_split(q0[i]);
+        w[0] = b.x;
+        w[1] = b.y;
+    }
 }
 
 template <int N, int REF, int NT_>
@@ -381,6 +434,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     float* zuf = smf + S::OFF_ZUF;
     float* zi = smf + S::OFF_ZI;
     int* tab = reinterpret_cast<int*>(smf + S::OFF_TAB);
+    float4* stab = reinterpret_cast<float4*>(smf + S::OFF_STAB);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 5);
@@ -428,6 +482,16 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             sl[i] = v.y;
         }
         for (int i = tid; i < T * T; i += NT) zuf[i] = (float)ec[ec_zinv(N) + i];
+        if (REF >= 1)
+            for (int i = tid; i < NQ * STAR_SLOTS; i += NT) {
+                const int p = i / STAR_SLOTS, t = i % STAR_SLOTS, j = t / 6, idx = tab[p] + t % 6;
+                float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < tab[p + 1]) {
+                    const float2 v = dw_split(ec[j * STAR_NNZ + idx]);
+                    c = make_float4(-v.x, -v.y, __int_as_float(j * S::PT + tab[NQ + 1 + idx] * T), 0.f);
+                }
+                stab[i] = c;
+            }
         const double* scal = ec + 3 * STAR_NNZ + T * T;
         const float2 e_dw = dw_split(scal[0]), g_dw = dw_split(scal[1]);
         const double dt = scal[2];
@@ -441,20 +505,19 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         __syncthreads();
         if (!alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
         if (REF >= 1) {
-            for (int i = tid; i < S::SQ; i += NT) {
-                Q1[i] = W[i];
-                if (REF == 2) D1[i] = 0.f;
-            }
+            stash_sweep<N, REF, NT_>(Q1, W, q0);
+            if (REF == 2)
+                for (int i = tid; i < S::Q1SIZE; i += NT) D1[i] = 0.f;
             __syncthreads();
         }
         bool ok = true;
 #pragma unroll 1
         for (int sweep = 1; sweep <= REF && ok; ++sweep) {
-            residual<N, REF, NT_>(W, Q1, D1, q0, sh, sl, zi, tab, e_dw, g_dw, Yall, P);
+            residual<N, REF, NT_>(W, Q1, D1, stab, zi, e_dw, g_dw, Yall, P);
             __syncthreads();
             ok = alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs);
             if (ok && REF == 2 && sweep == 1) {
-                for (int i = tid; i < S::SQ; i += NT) D1[i] = W[i];
+                stash_sweep<N, REF, NT_>(D1, W, q0);
                 __syncthreads();
             }
         }
@@ -464,9 +527,11 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             double* qo = P.qt ? P.qt + e * (int64_t)QBT : nullptr;
             double* io = P.iout ? P.iout + e * (int64_t)(NQ * B) : nullptr;
             for (int i = tid; i < QBT; i += NT) {
-                const int si = (i / (B * T)) * QS + i % (B * T);
-                double v = (double)(REF >= 1 ? Q1[si] : W[si]);
-                if (REF == 2) v += (double)D1[si];
+                const int p = i / (B * T), lu = i - p * (B * T);
+                const int si = p * QS + lu;
+                const int qi = (lu / T) * S::Q1S + p * T + (lu - (lu / T) * T);
+                double v = (double)(REF >= 1 ? Q1[qi] : W[si]);
+                if (REF == 2) v += (double)D1[qi];
                 if (REF >= 1) v += (double)W[si];
                 if (qo) qo[i] = v;
                 if (io && (i % T) == 0) io[i / T] = dt * v;
@@ -492,14 +557,10 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     P.iout = iout;
     P.count = count;
     P.stride = elem_const_stride(N);
-    P.khat.val = ref.khat_val_f32;
-    P.khat.col = ref.base->khat_col;
-    P.khat.row = ref.base->khat_row;
-    for (int g = 0; g <= MAX_N; ++g)
-        for (int j = 0; j < 3; ++j) P.khat.row_base[g][j] = ref.base->row_base[g][j];
     P.res_row = ref.res_row;
-    P.res_col = ref.res_col;
-    P.res_val = reinterpret_cast<const float2*>(ref.res_val);
+    P.res_int = ref.res_int;
+    P.res_inv = reinterpret_cast<const float2*>(ref.res_inv);
+    P.res_order = NT_ == 256 ? ref.res_order8 : (NT_ == 128 ? ref.res_order4 : ref.res_order2);
     P.zinv = ref.zinv_f32;
     P.khat_tc = ref.khat_tc;
     for (int g = 0; g <= MAX_N; ++g)
