@@ -111,3 +111,15 @@ def test_flux_matrices_match_oracle(L):
                                         inputs.material_dict(mats[1]) if kind == 0 else None, n, name)
             assert np.abs((Fm - om) * sc).max() < 1e-13 * amax
             assert np.abs((Fp - op) * sc).max() < 1e-13 * amax
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_library_khat_rows_match_oracle_fractions(L, N):
+    """The library's own quadrature gives the same rational rows (numerators
+    over a common denominator) that its mixed residual packs."""
+    from tests.test_oracle_pins import khat_row_fractions
+
+    _, k = L.poro_reference_matrices(N)
+    ko = basis.khat_matrices(N)
+    for a in range(3):
+        assert khat_row_fractions(k[a]) == khat_row_fractions(ko[a])

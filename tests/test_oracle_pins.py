@@ -210,6 +210,47 @@ def test_khat_is_the_derivative(N):
             assert got == pytest.approx(fd, rel=1e-8, abs=1e-8 * np.abs(c).sum())
 
 
+def khat_row_fractions(K, max_den=10**6):
+    """Rows of one Khat^alpha as (numerators, common denominator), or None
+    where an entry is not a rational with a denominator <= max_den."""
+    from math import lcm
+
+    out = []
+    for row in K:
+        nz = np.nonzero(row)[0]
+        fr = [Fraction(float(x)).limit_denominator(max_den) for x in row[nz]]
+        if any(abs(float(f) - x) > 1e-14 * abs(x) for f, x in zip(fr, row[nz])):
+            return None
+        d = 1
+        for f in fr:
+            d = lcm(d, f.denominator)
+        out.append(([int(f * d) for f in fr], d))
+    return out
+
+
+# largest common denominator of a Khat row, N = 1..6
+KHAT_MAX_DENOMINATOR = {1: 1, 2: 6, 3: 90, 4: 360, 5: 3150, 6: 103950}
+
+
+@pytest.mark.parametrize("N", range(1, 7))
+def test_khat_rows_are_small_rationals(N):
+    """Khat^alpha = M^{-1} K^alpha with the closed-form rational mass matrix
+    and polynomial integrals of a basis with rational recurrence
+    coefficients, so each row is an integer row over a small common
+    denominator (a wrong normalisation factor, e.g. a stray sqrt(2), breaks
+    this).  The mixed-precision residual stores Khat in exactly this form:
+    numerators below 2^23 (exact in binary32, packable with a 7-bit column)."""
+    worst_den, worst_num = 1, 0
+    for K in basis.khat_matrices(N):
+        rows = khat_row_fractions(K)
+        assert rows is not None
+        for nums, d in rows:
+            worst_den = max(worst_den, d)
+            worst_num = max([worst_num] + [abs(c) for c in nums])
+    assert worst_den == KHAT_MAX_DENOMINATOR[N]
+    assert worst_num < 2**23
+
+
 # ---------------------------------------------------------------- time matrices
 @pytest.mark.parametrize("N", range(0, 7))
 def test_time_matrices_closed_form(N):
