@@ -122,6 +122,46 @@ __device__ __forceinline__ void dw_mac_x2(float& h, float& l, float a, float bh,
     l = __fadd_rn(l, __fadd_rn(er, e));
 }
 
+// ------------------------------------- binary64 results on the integer pipe
+// GB300 runs binary64 (conversions included) at ~1/60 of the binary32 rate,
+// so the result is assembled from its binary32 words by bit manipulation.
+
+// exact binary64 bit pattern of a binary32 value (binary32 subnormals,
+// |x| < 1.2e-38, become signed zero)
+__device__ __forceinline__ unsigned long long f2d_bits(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 0xFFu;
+    const uint32_t hi = ex ? ((b & 0x80000000u) | ((ex + 896u) << 20) | ((b >> 3) & 0xFFFFFu)) : (b & 0x80000000u);
+    const uint32_t lo = ex ? (b << 29) : 0u;
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// s + e as binary64 for a pair with |e| <= ulp(s) / 2 (TwoSum output): e is
+// added to s's binary64 pattern in units of s's binary64 last place.  Exact
+// when e's bits lie within 29 places below s's last bit (the sum then has at
+// most 53 significant bits); otherwise e is truncated below that place.
+__device__ __forceinline__ double pair_to_double(float s, float e) {
+    unsigned long long d = f2d_bits(s);
+    const uint32_t bs = __float_as_uint(s), be = __float_as_uint(e);
+    const int exs = (int)((bs >> 23) & 0xFFu), exe = (int)((be >> 23) & 0xFFu);
+    if (exs != 0 && exe != 0) {
+        const unsigned long long me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
+        const bool opposite = ((bs ^ be) >> 31) != 0;
+        // e in units of 2^(exp(s) - 52); one binade lower (half the unit) when s
+        // is a power of two and e points towards zero
+        int k = exe - exs + 29 + ((opposite && (bs & 0x7FFFFFu) == 0) ? 1 : 0);
+        const unsigned long long delta = k >= 0 ? (me << k) : (k > -32 ? (me >> (-k)) : 0ull);
+        d = opposite ? d - delta : d + delta;
+    }
+    return __longlong_as_double((long long)d);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __device__ __forceinline__ float2 dw_split(double x) {
     const float h = (float)x;
     return make_float2(h, (float)(x - (double)h));
@@ -162,9 +202,9 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int OFF_D1 = OFF_Q1 + (REF >= 1 ? Q1SIZE : 0);
     static constexpr int OFF_SH = OFF_D1 + (REF == 2 ? Q1SIZE : 0);
     static constexpr int OFF_SL = OFF_SH + R4(3 * STAR_NNZ);
-    static constexpr int OFF_ZIN = OFF_SL + R4(3 * STAR_NNZ);
-    static constexpr int OFF_ZUF = OFF_ZIN + R4(T_ * T_);
-    static constexpr int OFF_ZI = OFF_ZUF + R4(T_ * T_);
+    static constexpr int OFF_ZIN = OFF_SL + R4(3 * STAR_NNZ);  // [T][8]
+    static constexpr int OFF_ZUF = OFF_ZIN + 8 * T_;            // [T][8]
+    static constexpr int OFF_ZI = OFF_ZUF + 8 * T_;
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
     static constexpr int OFF_STAB = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // float4 [13][STAR_SLOTS]
     static constexpr int OFF_BAR = OFF_STAB + 4 * NQ * STAR_SLOTS;  // 2 mbarriers, TMEM slot, abort flag
@@ -173,6 +213,30 @@ struct K2Shape : Alg3Shape<N> {
     static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
     static_assert(NW == 2 || NW == 4 || NW == 8, "2, 4 or 8 warps");
 };
+
+// row[0..T) <- Zi row[0..T), Zi stored with row stride 8 (two 16-byte loads a row)
+template <int T>
+__device__ __forceinline__ void solve_row8(float* row, const float* Zi) {
+    float x[T];
+#pragma unroll
+    for (int s = 0; s < T; ++s) x[s] = row[s];
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const float4 a = *reinterpret_cast<const float4*>(Zi + 8 * u);
+        float z[8] = {a.x, a.y, a.z, a.w, 0.f, 0.f, 0.f, 0.f};
+        if constexpr (T > 4) {
+            const float4 b = *reinterpret_cast<const float4*>(Zi + 8 * u + 4);
+            z[4] = b.x;
+            z[5] = b.y;
+            z[6] = b.z;
+            z[7] = b.w;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int s = 0; s < T; ++s) acc = fmaf(z[s], x[s], acc);
+        row[u] = acc;
+    }
+}
 
 // Tensor-core state of one CTA (shared addresses, barrier phases)
 struct TcState {
@@ -203,15 +267,15 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             const int kind = it / d, m = o + it % d;
             if (kind < 7) {
                 const int p = kind < 6 ? kind : QP;
-                solve_row<T>(bq + p * QS + m * T, zin);
+                solve_row8<T>(bq + p * QS + m * T, zin);
             } else {
                 const int i = kind - 7;
                 float* rf = bq + (QUF + i) * QS + m * T;
                 float* rv = bq + (QU + i) * QS + m * T;
-                solve_row<T>(rf, zuf);
+                solve_row8<T>(rf, zuf);
 #pragma unroll
                 for (int u = 0; u < T; ++u) rv[u] = fmaf(gcoup, rf[u], rv[u]);
-                solve_row<T>(rv, zin);
+                solve_row8<T>(rv, zin);
             }
         }
         __syncthreads();
@@ -282,14 +346,15 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                 const int r = sp * 32 + lane;
                 const int p = r / T, u = r - (r / T) * T;
                 float* dst = bq + p * QS + u;
+                const int c_end = min(c_begin + ncol, o);
 #pragma unroll 1
-                for (int c0 = c_begin; c0 < c_begin + ncol && c0 < o; c0 += 8) {
-                    float v[8];
-                    tc::tmem_ld8(S.tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
+                for (int c0 = c_begin; c0 < c_end; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(S.tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)c0, v);
                     if (r < PT) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            if (c0 + q < o) dst[(c0 + q) * T] -= v[q];
+                        for (int q = 0; q < 16; ++q)
+                            if (c0 + q < c_end) dst[(c0 + q) * T] -= v[q];
                     }
                 }
             }
@@ -454,8 +519,8 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     // operand region starts finite (K padding of A meets zeros of B)
     for (int i = tid; i < S::XY_SIZE; i += NT) smf[S::OFF_XY + i] = 0.f;
     for (int i = tid; i < T * T; i += NT) {
-        zin[i] = P.zinv[i];
         const int u = i / T, s = i % T;
+        zin[8 * u + s] = P.zinv[i];
         zi[i] = (float)((2 * u + 1) * ((u > s && ((u - s) & 1)) ? -1 : 1));  // Z = S^{-1}(W - K^tau)
     }
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
@@ -481,7 +546,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             sh[i] = v.x;
             sl[i] = v.y;
         }
-        for (int i = tid; i < T * T; i += NT) zuf[i] = (float)ec[ec_zinv(N) + i];
+        for (int i = tid; i < T * T; i += NT) zuf[8 * (i / T) + i % T] = (float)ec[ec_zinv(N) + i];
         if (REF >= 1)
             for (int i = tid; i < NQ * STAR_SLOTS; i += NT) {
                 const int p = i / STAR_SLOTS, t = i % STAR_SLOTS, j = t / 6, idx = tab[p] + t % 6;
@@ -526,15 +591,32 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         if (P.qt || P.iout) {
             double* qo = P.qt ? P.qt + e * (int64_t)QBT : nullptr;
             double* io = P.iout ? P.iout + e * (int64_t)(NQ * B) : nullptr;
-            for (int i = tid; i < QBT; i += NT) {
-                const int p = i / (B * T), lu = i - p * (B * T);
-                const int si = p * QS + lu;
-                const int qi = (lu / T) * S::Q1S + p * T + (lu - (lu / T) * T);
-                double v = (double)(REF >= 1 ? Q1[qi] : W[si]);
-                if (REF == 2) v += (double)D1[qi];
-                if (REF >= 1) v += (double)W[si];
-                if (qo) qo[i] = v;
-                if (io && (i % T) == 0) io[i / T] = dt * v;
+            // one (p, l) row of T time modes per thread
+            for (int i = tid; i < NQ * B; i += NT) {
+                const int p = i / B, l = i - (i / B) * B;
+                const float* w = W + p * QS + l * T;
+                const float* q1 = Q1 + l * S::Q1S + p * T;
+                const float* d1 = D1 + l * S::Q1S + p * T;
+#pragma unroll
+                for (int u = 0; u < T; ++u) {
+                    double v;
+                    if (REF == 0) {
+                        v = __longlong_as_double((long long)f2d_bits(w[u]));
+                    } else {
+                        float sv, ev;
+                        two_sum(q1[u], w[u], sv, ev);
+                        if (REF == 2) {
+                            float s2, e2;
+                            two_sum(sv, d1[u], s2, e2);
+                            ev = __fadd_rn(ev, e2);
+                            sv = __fadd_rn(s2, ev);  // renormalise: |ev| <= ulp(sv) / 2
+                            ev = __fsub_rn(ev, __fsub_rn(sv, s2));
+                        }
+                        v = pair_to_double(sv, ev);
+                    }
+                    if (qo) qo[(int64_t)i * T + u] = v;
+                    if (io && u == 0) io[i] = dt * v;
+                }
             }
         }
         __syncthreads();
