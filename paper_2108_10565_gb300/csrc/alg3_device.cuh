@@ -38,6 +38,10 @@ struct KhatBlocks {
     const int32_t* col;
     const int32_t* row;
     int32_t row_base[MAX_N + 1][3];
+    // optional (one direction per pass): block (g, j)'s rows dealt to the
+    // warps, [warps + 1] starts then the lists, at lists + list_base[g][j]
+    const int32_t* lists = nullptr;
+    int32_t list_base[MAX_N + 1][3];
 };
 
 template <int T, class Real>
@@ -136,7 +140,7 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
             int xo[PUL];
 #pragma unroll
             for (int k = 0; k < PUL; ++k) xo[k] = lp[k] * XS + lu[k];
-            for (int l = warp; l < o; l += NW) {
+            auto row = [&](int l) {
                 Real acc[PUL];
 #pragma unroll
                 for (int k = 0; k < PUL; ++k) acc[k] = Real(0);
@@ -165,6 +169,14 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
 #pragma unroll
                 for (int k = 0; k < PUL; ++k)
                     if (lane + 32 * k < PT) bq[lp[k] * QS + l * T + lu[k]] -= acc[k];
+            };
+            if (JX == 1 && K.lists) {
+                // this warp's rows of the block, dealt so that the warps' work is balanced
+                const int32_t* L = K.lists + K.list_base[g][jb];
+                const int i0 = __ldg(L + warp), i1 = __ldg(L + warp + 1);
+                for (int i = i0; i < i1; ++i) row(__ldg(L + NW + 1 + i));
+            } else {
+                for (int l = warp; l < o; l += NW) row(l);
             }
             __syncthreads();
         }

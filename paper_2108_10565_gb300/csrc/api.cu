@@ -170,6 +170,7 @@ void free_reference(poro_ctx* c) {
     dfree(c->dref.khat_val);
     dfree(c->dref.khat_col);
     dfree(c->dref.khat_row);
+    for (int w = 0; w < 3; ++w) dfree(c->dref.lists[w]);
     dfree(c->dref.zinv);
 }
 
@@ -195,6 +196,29 @@ void ctx_set_error(poro_ctx* c, const std::string& msg) {
 extern "C" {
 
 const char* poro_last_error(const poro_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+// Rows dealt to `warps` lists, longest first, each to the least loaded list
+// (ties to the lower index); rows of zero cost are left out when `drop_free`.
+// Layout: [warps + 1] list starts, then the lists one after another.
+static std::vector<int32_t> deal_rows(const std::vector<int64_t>& cost, int warps, bool drop_free) {
+    std::vector<int> order;
+    for (int l = 0; l < (int)cost.size(); ++l)
+        if (!drop_free || cost[l] > 0) order.push_back(l);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int32_t>> lists(warps);
+    std::vector<int64_t> load(warps, 0);
+    for (int l : order) {
+        int best = 0;
+        for (int k = 1; k < warps; ++k)
+            if (load[k] < load[best]) best = k;
+        load[best] += cost[l];
+        lists[best].push_back(l);
+    }
+    std::vector<int32_t> out(warps + 1, 0);
+    for (int k = 0; k < warps; ++k) out[k + 1] = out[k] + (int32_t)lists[k].size();
+    for (int k = 0; k < warps; ++k) out.insert(out.end(), lists[k].begin(), lists[k].end());
+    return out;
+}
 
 // x = num / den with den <= 10^6 (continued-fraction convergents), if x is
 // such a rational to 1e-14 relative
@@ -267,7 +291,23 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             val.insert(val.end(), C.val.begin(), C.val.end());
             col.insert(col.end(), C.col.begin(), C.col.end());
         }
-    if ((e = upload((void**)&c->dref.khat_val, val.data(), val.size() * sizeof(double))) != cudaSuccess ||
+    // per block (g, j): its rows l < o_g dealt to 2, 4 and 8 warps by Khat
+    // entries (rows without entries in the block are left out)
+    std::vector<int32_t> blists[3];
+    for (int w = 0; w < 3; ++w)
+        for (int g = 1; g <= degree_N; ++g)
+            for (int j = 0; j < 3; ++j) {
+                const poro::KhatBlockCSR& C = c->ref.blocks[g * 3 + j];
+                std::vector<int64_t> cost(C.row_ptr.size() - 1);
+                for (size_t l = 0; l + 1 < C.row_ptr.size(); ++l) cost[l] = C.row_ptr[l + 1] - C.row_ptr[l];
+                c->dref.list_base[w][g][j] = (int32_t)blists[w].size();
+                const std::vector<int32_t> d = deal_rows(cost, 2 << w, true);
+                blists[w].insert(blists[w].end(), d.begin(), d.end());
+            }
+    if ((e = upload((void**)&c->dref.lists[0], blists[0].data(), blists[0].size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = upload((void**)&c->dref.lists[1], blists[1].data(), blists[1].size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = upload((void**)&c->dref.lists[2], blists[2].data(), blists[2].size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = upload((void**)&c->dref.khat_val, val.data(), val.size() * sizeof(double))) != cudaSuccess ||
         (e = upload((void**)&c->dref.khat_col, col.data(), col.size() * sizeof(int32_t))) != cudaSuccess ||
         (e = upload((void**)&c->dref.khat_row, row.data(), row.size() * sizeof(int32_t))) != cudaSuccess ||
         (e = upload((void**)&c->dref.zinv, c->ref.zinv.data(), c->ref.zinv.size() * sizeof(double))) !=
@@ -356,29 +396,12 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
         // residual row order per warp count: a row costs its Khat entries (all
         // directions) plus a fixed share for the star and time terms
         auto deal = [&](int warps) {
-            std::vector<std::pair<int64_t, int>> w;
+            std::vector<int64_t> cost(B);
             for (int l = 0; l < B; ++l) {
-                int64_t cost = 40;
-                for (int j = 0; j < 3; ++j) cost += rrow[j * (B + 1) + l + 1] - rrow[j * (B + 1) + l];
-                w.push_back({cost, l});
+                cost[l] = 40;
+                for (int j = 0; j < 3; ++j) cost[l] += rrow[j * (B + 1) + l + 1] - rrow[j * (B + 1) + l];
             }
-            std::sort(w.begin(), w.end(), [](auto& a, auto& b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
-            std::vector<std::vector<int>> lists(warps);
-            std::vector<int64_t> load(warps, 0);
-            for (auto& [cost, l] : w) {
-                int best = 0;
-                for (int k = 1; k < warps; ++k)
-                    if (load[k] < load[best]) best = k;
-                load[best] += cost;
-                lists[best].push_back(l);
-            }
-            // [warps + 1] list starts, then the lists one after another
-            std::vector<int32_t> out(warps + 1, 0);
-            for (int k = 0; k < warps; ++k) {
-                out[k + 1] = out[k] + (int32_t)lists[k].size();
-            }
-            for (int k = 0; k < warps; ++k) out.insert(out.end(), lists[k].begin(), lists[k].end());
-            return out;
+            return deal_rows(cost, warps, false);
         };
         const std::vector<int32_t> ord8 = deal(8), ord4 = deal(4), ord2 = deal(2);
         if (!rerr.empty()) {

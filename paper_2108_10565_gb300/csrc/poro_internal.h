@@ -121,6 +121,11 @@ struct DeviceReference {
     int32_t* khat_row = nullptr;  // concatenated row pointers, absolute into val/col
     int32_t row_base[MAX_N + 1][3] = {};  // start of block (g, j)'s row pointers in khat_row
     double* zinv = nullptr;       // [T][T]
+    // rows l < o_g of block (g, j) with Khat entries, dealt to 2, 4, 8 warps
+    // (index 0, 1, 2): at lists[w] + list_base[w][g][j], [warps + 1] list
+    // starts, then the lists
+    int32_t* lists[3] = {nullptr, nullptr, nullptr};
+    int32_t list_base[3][MAX_N + 1][3] = {};
 };
 
 // Extra device data of the mixed-precision (refinement) path.

@@ -113,6 +113,11 @@ int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, c
     P.khat.row = ref.khat_row;
     for (int g = 0; g <= MAX_N; ++g)
         for (int j = 0; j < 3; ++j) P.khat.row_base[g][j] = ref.row_base[g][j];
+    constexpr int W = NT_ == 256 ? 2 : (NT_ == 128 ? 1 : 0);  // lists for NT_ / 32 warps
+    static_assert(NT_ == 64 || NT_ == 128 || NT_ == 256, "2, 4 or 8 warps");
+    P.khat.lists = ref.lists[W];
+    for (int g = 0; g <= MAX_N; ++g)
+        for (int j = 0; j < 3; ++j) P.khat.list_base[g][j] = ref.list_base[W][g][j];
     P.zinv = ref.zinv;
     const size_t smem = sizeof(double) * S::SMEM_DOUBLES;
     cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
