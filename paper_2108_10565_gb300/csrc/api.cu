@@ -50,6 +50,7 @@ struct poro_ctx {
     int32_t *d_nb = nullptr, *d_tab = nullptr, *d_vrow = nullptr, *d_vcol = nullptr;
     double *d_fc = nullptr, *d_fF = nullptr, *d_Floc = nullptr, *d_Fnb = nullptr, *d_vval = nullptr,
            *d_minv = nullptr;
+    float *d_fF2 = nullptr, *d_Floc2 = nullptr, *d_Fnb2 = nullptr, *d_vval2 = nullptr;  // (hi, lo) pairs
     struct Source {
         int64_t elem;
         double* d_coef;
@@ -116,6 +117,10 @@ void free_mesh_device(poro_ctx* c) {
     dfree(c->d_Fnb);
     dfree(c->d_vval);
     dfree(c->d_minv);
+    dfree(c->d_fF2);
+    dfree(c->d_Floc2);
+    dfree(c->d_Fnb2);
+    dfree(c->d_vval2);
     for (auto& s : c->sources) dfree(s.d_coef);
     c->sources.clear();
     for (auto& p : c->d_cl_elems) dfree(p);
@@ -1002,11 +1007,33 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     for (int k = 0; k < B; ++k) minv[k] = 1.0 / c->ref.mass_diag[k];
     std::vector<double> Floc, Fnb;
     poro::face_matrices(N, Floc, Fnb);
-    cudaError_t er;
+    // the mixed-precision form corrects in double-binary32: (hi, lo) copies
+    const bool dw = c->prec == PORO_FP32_REFINE;
+    auto split = [](const std::vector<double>& x) {
+        std::vector<float> o(2 * x.size());
+        for (size_t i = 0; i < x.size(); ++i) {
+            const float h = (float)x[i];
+            o[2 * i] = h;
+            o[2 * i + 1] = (float)(x[i] - (double)h);
+        }
+        return o;
+    };
+    cudaError_t er = cudaSuccess;
+    if (dw) {
+        const std::vector<float> f2 = split(fF), l2 = split(Floc), n2 = split(Fnb), v2 = split(vval);
+        if ((er = upload((void**)&c->d_fF2, f2.data(), f2.size() * sizeof(float))) != cudaSuccess ||
+            (er = upload((void**)&c->d_Floc2, l2.data(), l2.size() * sizeof(float))) != cudaSuccess ||
+            (er = upload((void**)&c->d_Fnb2, n2.data(), n2.size() * sizeof(float))) != cudaSuccess ||
+            (er = upload((void**)&c->d_vval2, v2.data(), v2.size() * sizeof(float))) != cudaSuccess) {
+            free_population(c);
+            return er == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_clusters: out of device memory")
+                                                   : cuda_fail(c, er, "poro_set_clusters");
+        }
+    }
     if ((er = upload((void**)&c->d_nb, nb.data(), nb.size() * sizeof(int32_t))) != cudaSuccess ||
         (er = upload((void**)&c->d_tab, tab.data(), tab.size() * sizeof(int32_t))) != cudaSuccess ||
         (er = upload((void**)&c->d_fc, fc.data(), fc.size() * sizeof(double))) != cudaSuccess ||
-        (er = upload((void**)&c->d_fF, fF.data(), fF.size() * sizeof(double))) != cudaSuccess ||
+        (!dw && (er = upload((void**)&c->d_fF, fF.data(), fF.size() * sizeof(double))) != cudaSuccess) ||
         (er = upload((void**)&c->d_vrow, vrow.data(), vrow.size() * sizeof(int32_t))) != cudaSuccess ||
         (er = upload((void**)&c->d_vcol, vcol.data(), vcol.size() * sizeof(int32_t))) != cudaSuccess ||
         (er = upload((void**)&c->d_vval, vval.data(), vval.size() * sizeof(double))) != cudaSuccess ||
@@ -1032,6 +1059,11 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     d.vcol = c->d_vcol;
     d.vval = c->d_vval;
     d.minv = c->d_minv;
+    d.dw = dw;
+    d.fF2 = c->d_fF2;
+    d.Floc2 = c->d_Floc2;
+    d.Fnb2 = c->d_Fnb2;
+    d.vval2 = c->d_vval2;
     // clusters: element lists, buffer slots of (element, larger neighbour level)
     c->C = C;
     c->cl_elems.assign(C, std::vector<int32_t>());

@@ -214,6 +214,7 @@ __global__ void receiver_kernel(int B, const double* q, int32_t nrec, const int6
 
 int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
     if (count <= 0) return 0;
+    if (d.dw) return launch_corrector_dw(d, elems, count, stream);
     const int B = n_modes(d.N);
     const size_t smem = sizeof(double) * 4 * NQ * B;
     cudaError_t err = cudaFuncSetAttribute(corrector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

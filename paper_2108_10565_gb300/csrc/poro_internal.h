@@ -206,6 +206,13 @@ struct CorrectorData {
     const int32_t* vcol = nullptr;
     const double* vval = nullptr;     // Kv^j_kl = M_ll Khat^j_lk / M_kk
     const double* minv = nullptr;     // [B] 1 / M_kk
+    // double-binary32 (hi, lo) copies for the mixed-precision form (dw = true:
+    // the corrector runs in double-binary32 and fF is not needed)
+    bool dw = false;
+    const float* fF2 = nullptr;       // [ne][4][2][169] pairs
+    const float* Floc2 = nullptr;     // [4][B][B] pairs
+    const float* Fnb2 = nullptr;      // [96][B][B] pairs
+    const float* vval2 = nullptr;     // Kv^j values, pairs
     // clustered local time stepping (all nullptr / 1 for global time stepping)
     int C = 1;                        // number of clusters
     const int32_t* cl = nullptr;      // [ne] cluster of each element
@@ -217,6 +224,7 @@ struct CorrectorData {
 int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const int32_t* slot, const double* iout,
                        double* buf, int64_t tick, void* stream);
 int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
+int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
 int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
 int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef, double f0, double tc, double dt,
                              int64_t len, int64_t k_rel, const int64_t* tick, void* stream);

@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include "alg3_device.cuh"
+#include "dw_device.cuh"
 #include "tc_device.cuh"
 
 namespace poro {
@@ -71,101 +72,6 @@ __constant__ int c_star_tab[NQ + 1 + STAR_NNZ] = {
     SXX, SXY, SXZ, QP, SYY, SXY, SYZ, QP, SZZ, SXZ, SYZ, QP,
     QU, QV, QW, QUF, QVF, QWF,
     SXX, SXY, SXZ, QP, SYY, SXY, SYZ, QP, SZZ, SXZ, SYZ, QP};
-
-// ------------------------------------------------ error-free double-word ops
-// Explicit round-to-nearest intrinsics keep the compiler from contracting or
-// reassociating the transformations.
-__device__ __forceinline__ void dw_mac(float& h, float& l, float ah, float al, float bh, float bl) {
-    const float p = __fmul_rn(ah, bh);
-    float e = __fmaf_rn(ah, bh, -p);
-    e = __fmaf_rn(ah, bl, e);
-    e = __fmaf_rn(al, bh, e);
-    const float s = __fadd_rn(h, p);
-    const float bb = __fsub_rn(s, h);
-    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(er, e));
-}
-
-// acc += a * b with b a single binary32 word
-__device__ __forceinline__ void dw_mac1(float& h, float& l, float ah, float al, float b) {
-    const float p = __fmul_rn(ah, b);
-    float e = __fmaf_rn(ah, b, -p);
-    e = __fmaf_rn(al, b, e);
-    const float s = __fadd_rn(h, p);
-    const float bb = __fsub_rn(s, h);
-    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(er, e));
-}
-
-// acc += a * b with a exact (no low word)
-__device__ __forceinline__ void dw_mac_x(float& h, float& l, float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float e = __fmaf_rn(a, b, -p);
-    const float s = __fadd_rn(h, p);
-    const float bb = __fsub_rn(s, h);
-    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(er, e));
-}
-
-// acc += a * (bh + bl) with a exact
-__device__ __forceinline__ void dw_mac_x2(float& h, float& l, float a, float bh, float bl) {
-    const float p = __fmul_rn(a, bh);
-    float e = __fmaf_rn(a, bh, -p);
-    e = __fmaf_rn(a, bl, e);
-    const float s = __fadd_rn(h, p);
-    const float bb = __fsub_rn(s, h);
-    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(er, e));
-}
-
-// ------------------------------------- binary64 results on the integer pipe
-// GB300 runs binary64 (conversions included) at ~1/60 of the binary32 rate,
-// so the result is assembled from its binary32 words by bit manipulation.
-
-// exact binary64 bit pattern of a binary32 value (binary32 subnormals,
-// |x| < 1.2e-38, become signed zero)
-__device__ __forceinline__ unsigned long long f2d_bits(float x) {
-    const uint32_t b = __float_as_uint(x);
-    const uint32_t ex = (b >> 23) & 0xFFu;
-    const uint32_t hi = ex ? ((b & 0x80000000u) | ((ex + 896u) << 20) | ((b >> 3) & 0xFFFFFu)) : (b & 0x80000000u);
-    const uint32_t lo = ex ? (b << 29) : 0u;
-    return ((unsigned long long)hi << 32) | lo;
-}
-
-// s + e as binary64 for a pair with |e| <= ulp(s) / 2 (TwoSum output): e is
-// added to s's binary64 pattern in units of s's binary64 last place.  Exact
-// when e's bits lie within 29 places below s's last bit (the sum then has at
-// most 53 significant bits); otherwise e is truncated below that place.
-__device__ __forceinline__ double pair_to_double(float s, float e) {
-    unsigned long long d = f2d_bits(s);
-    const uint32_t bs = __float_as_uint(s), be = __float_as_uint(e);
-    const int exs = (int)((bs >> 23) & 0xFFu), exe = (int)((be >> 23) & 0xFFu);
-    if (exs != 0 && exe != 0) {
-        const unsigned long long me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
-        const bool opposite = ((bs ^ be) >> 31) != 0;
-        // e in units of 2^(exp(s) - 52); one binade lower (half the unit) when s
-        // is a power of two and e points towards zero
-        int k = exe - exs + 29 + ((opposite && (bs & 0x7FFFFFu) == 0) ? 1 : 0);
-        const unsigned long long delta = k >= 0 ? (me << k) : (k > -32 ? (me >> (-k)) : 0ull);
-        d = opposite ? d - delta : d + delta;
-    }
-    return __longlong_as_double((long long)d);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ float2 dw_split(double x) {
-    const float h = (float)x;
-    return make_float2(h, (float)(x - (double)h));
-}
 
 // CTA sizes the autotuner chooses from (index 0 is the default)
 template <int N>
