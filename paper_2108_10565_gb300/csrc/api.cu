@@ -48,9 +48,9 @@ struct poro_ctx {
     double dt = 0.0, t = 0.0;
     poro::CorrectorData cd;
     int32_t *d_nb = nullptr, *d_tab = nullptr, *d_vrow = nullptr, *d_vcol = nullptr;
-    double *d_fc = nullptr, *d_fF = nullptr, *d_Floc = nullptr, *d_Fnb = nullptr, *d_vval = nullptr,
+    double *d_fc = nullptr, *d_fF = nullptr, *d_Pf = nullptr, *d_Pnb = nullptr, *d_vval = nullptr,
            *d_minv = nullptr;
-    float *d_fF2 = nullptr, *d_Floc2 = nullptr, *d_Fnb2 = nullptr, *d_vval2 = nullptr;  // (hi, lo) pairs
+    float *d_fF2 = nullptr, *d_Pf2 = nullptr, *d_Pnb2 = nullptr, *d_vval2 = nullptr;  // (hi, lo) pairs
     struct Source {
         int64_t elem;
         double* d_coef;
@@ -113,13 +113,13 @@ void free_mesh_device(poro_ctx* c) {
     dfree(c->d_vcol);
     dfree(c->d_fc);
     dfree(c->d_fF);
-    dfree(c->d_Floc);
-    dfree(c->d_Fnb);
+    dfree(c->d_Pf);
+    dfree(c->d_Pnb);
     dfree(c->d_vval);
     dfree(c->d_minv);
     dfree(c->d_fF2);
-    dfree(c->d_Floc2);
-    dfree(c->d_Fnb2);
+    dfree(c->d_Pf2);
+    dfree(c->d_Pnb2);
     dfree(c->d_vval2);
     for (auto& s : c->sources) dfree(s.d_coef);
     c->sources.clear();
@@ -1005,8 +1005,9 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     }
     // absolute row offsets per direction: rows of direction j start at j*(B+1)
     for (int k = 0; k < B; ++k) minv[k] = 1.0 / c->ref.mass_diag[k];
-    std::vector<double> Floc, Fnb;
-    poro::face_matrices(N, Floc, Fnb);
+    // face traces: Floc^f = Pf^T Pf, Fnb^{f,h,s} = Pf^T Pnb
+    std::vector<double> Pf, Pnb;
+    poro::face_traces(N, Pf, Pnb);
     // the mixed-precision form corrects in double-binary32: (hi, lo) copies
     const bool dw = c->prec == PORO_FP32_REFINE;
     auto split = [](const std::vector<double>& x) {
@@ -1020,10 +1021,10 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     };
     cudaError_t er = cudaSuccess;
     if (dw) {
-        const std::vector<float> f2 = split(fF), l2 = split(Floc), n2 = split(Fnb), v2 = split(vval);
+        const std::vector<float> f2 = split(fF), l2 = split(Pf), n2 = split(Pnb), v2 = split(vval);
         if ((er = upload((void**)&c->d_fF2, f2.data(), f2.size() * sizeof(float))) != cudaSuccess ||
-            (er = upload((void**)&c->d_Floc2, l2.data(), l2.size() * sizeof(float))) != cudaSuccess ||
-            (er = upload((void**)&c->d_Fnb2, n2.data(), n2.size() * sizeof(float))) != cudaSuccess ||
+            (er = upload((void**)&c->d_Pf2, l2.data(), l2.size() * sizeof(float))) != cudaSuccess ||
+            (er = upload((void**)&c->d_Pnb2, n2.data(), n2.size() * sizeof(float))) != cudaSuccess ||
             (er = upload((void**)&c->d_vval2, v2.data(), v2.size() * sizeof(float))) != cudaSuccess) {
             free_population(c);
             return er == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_clusters: out of device memory")
@@ -1038,8 +1039,8 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
         (er = upload((void**)&c->d_vcol, vcol.data(), vcol.size() * sizeof(int32_t))) != cudaSuccess ||
         (er = upload((void**)&c->d_vval, vval.data(), vval.size() * sizeof(double))) != cudaSuccess ||
         (er = upload((void**)&c->d_minv, minv.data(), minv.size() * sizeof(double))) != cudaSuccess ||
-        (er = upload((void**)&c->d_Floc, Floc.data(), Floc.size() * sizeof(double))) != cudaSuccess ||
-        (er = upload((void**)&c->d_Fnb, Fnb.data(), Fnb.size() * sizeof(double))) != cudaSuccess) {
+        (er = upload((void**)&c->d_Pf, Pf.data(), Pf.size() * sizeof(double))) != cudaSuccess ||
+        (er = upload((void**)&c->d_Pnb, Pnb.data(), Pnb.size() * sizeof(double))) != cudaSuccess) {
         free_population(c);
         return er == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_set_clusters: out of device memory")
                                                : cuda_fail(c, er, "poro_set_clusters");
@@ -1053,16 +1054,16 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     d.tab = c->d_tab;
     d.fc = c->d_fc;
     d.fF = c->d_fF;
-    d.Floc = c->d_Floc;
-    d.Fnb = c->d_Fnb;
+    d.Pf = c->d_Pf;
+    d.Pnb = c->d_Pnb;
     d.vrow = c->d_vrow;
     d.vcol = c->d_vcol;
     d.vval = c->d_vval;
     d.minv = c->d_minv;
     d.dw = dw;
     d.fF2 = c->d_fF2;
-    d.Floc2 = c->d_Floc2;
-    d.Fnb2 = c->d_Fnb2;
+    d.Pf2 = c->d_Pf2;
+    d.Pnb2 = c->d_Pnb2;
     d.vval2 = c->d_vval2;
     // clusters: element lists, buffer slots of (element, larger neighbour level)
     c->C = C;

@@ -20,22 +20,79 @@ namespace {
 
 constexpr int CNT = 128;
 
+// the neighbour's trace source, integrated over this element's interval:
+// its own I (same cluster), the buffered sum of its sub-steps (smaller
+// neighbour) or its predictor integrated over the sub-interval (larger
+// neighbour); written to In[13][B]
+template <int N>
+__device__ void neighbour_integral(const CorrectorData& D, int64_t e, int64_t nbr, double* In, double* wts) {
+    constexpr int B = n_modes(N), QB = NQ * B, T = N + 1;
+    const int c = D.cl ? D.cl[e] : 0, cr = D.cl ? D.cl[nbr] : 0;
+    if (cr == c) {
+        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = D.iout[nbr * QB + i];
+    } else if (cr < c) {
+        const double* b = D.buf + (int64_t)D.slot[nbr * D.C + c] * QB;
+        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = b[i];
+    } else {
+        // larger neighbour: dt_r sum_s Qt_s int_a^b chi_s over the sub-interval
+        if (threadIdx.x == 0) {
+            const int64_t ks = D.tick + 1 - ((int64_t)1 << c);
+            const int64_t m = (ks >> cr) << cr;
+            const double a = (double)(ks - m) / (double)((int64_t)1 << cr);
+            const double bb = (double)(D.tick + 1 - m) / (double)((int64_t)1 << cr);
+            // int_a^b P_s(2 tau - 1) dtau = (1/2) [ (P_{s+1} - P_{s-1}) / (2s+1) ]_{2a-1}^{2b-1}
+            double P0[MAX_N + 3], P1[MAX_N + 3];
+            const double x0 = 2 * a - 1, x1 = 2 * bb - 1;
+            P0[0] = 1;
+            P0[1] = x0;
+            P1[0] = 1;
+            P1[1] = x1;
+            for (int n = 1; n <= T; ++n) {
+                P0[n + 1] = ((2 * n + 1) * x0 * P0[n] - n * P0[n - 1]) / (n + 1);
+                P1[n + 1] = ((2 * n + 1) * x1 * P1[n] - n * P1[n - 1]) / (n + 1);
+            }
+            wts[0] = 0.5 * (x1 - x0);
+            for (int sidx = 1; sidx < T; ++sidx)
+                wts[sidx] = 0.5 * ((P1[sidx + 1] - P1[sidx - 1]) - (P0[sidx + 1] - P0[sidx - 1])) / (2 * sidx + 1);
+        }
+        __syncthreads();
+        const int stride = elem_const_stride(N);
+        const double dtr = D.econst[nbr * stride + ec_scalars(N) + 2];
+        const double* qr = D.qt + nbr * (int64_t)QB * T;
+        for (int i = threadIdx.x; i < QB; i += CNT) {
+            double acc = 0.0;
+            for (int sidx = 0; sidx < T; ++sidx) acc = fma(qr[i * T + sidx], wts[sidx], acc);
+            In[i] = dtr * acc;
+        }
+    }
+}
+
+// Face terms through face traces.  Floc^f = Pf^T Pf and Fnb^{f,h,s} = Pf^T Pnb
+// with Pf, Pnb of df = (N+1)(N+2)/2 rows (traces in a basis orthonormal on
+// the reference triangle), so per face
+//   u_f = c_f (F^- (I Pf^T) + F^+ (I^nb Pnb^T))          [13 x df]
+//   dQ -= M^{-1} sum_f Pf^T u_f                          (one pass over all faces)
+template <int N>
 __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, const int32_t* elems, int64_t count) {
-    const int N = D.N, B = n_modes(N), QB = NQ * B;
-    const int stride = elem_const_stride(N);
+    constexpr int B = n_modes(N), QB = NQ * B, DF = (N + 1) * (N + 2) / 2, FQ = NQ * DF;
+    constexpr int stride = elem_const_stride(N);
     extern __shared__ double sm[];
-    double* I = sm;            // [13][B]
-    double* Y = I + QB;        // [13][B]
-    double* dQ = Y + QB;       // [13][B]
-    double* In = dQ + QB;      // [13][B]
-    __shared__ double F[NQ * NQ];
+    double* I = sm;             // [13][B]
+    double* Y = I + QB;         // [13][B]
+    double* dQ = Y + QB;        // [13][B]
+    double* In = dQ + QB;       // [13][B]
+    double* tL = In + QB;       // [4][13][DF] traces of I
+    double* tR = tL + 4 * FQ;   // [13][DF] neighbour trace
+    double* U = tR + FQ;        // [4][13][DF] flux values
+    __shared__ double F[2 * NQ * NQ];
     __shared__ double wts[MAX_N + 1];
+    const int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
         const int64_t e = elems ? elems[it] : it;
         const double* ec = D.econst + e * stride;
         const double dt = ec[ec_scalars(N) + 2];
         const double ev = ec[ec_scalars(N)] / dt, gv = ec[ec_scalars(N) + 1] / dt;
-        for (int i = threadIdx.x; i < QB; i += CNT) {
+        for (int i = tid; i < QB; i += CNT) {
             I[i] = D.iout[e * QB + i];
             dQ[i] = 0.0;
         }
@@ -43,7 +100,7 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
         // volume: X^j = A^j I (54-entry star pattern), dQ += Kv^j X^j
         for (int j = 0; j < 3; ++j) {
             const double* sj = ec + j * STAR_NNZ;
-            for (int l = threadIdx.x; l < B; l += CNT) {
+            for (int l = tid; l < B; l += CNT) {
                 double qv[NQ], acc[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
@@ -57,8 +114,8 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
             }
             __syncthreads();
             const int32_t* vr = D.vrow + j * (B + 1);
-            for (int i = threadIdx.x; i < QB; i += CNT) {
-                const int p = i / B, k = i % B;
+            for (int i = tid; i < QB; i += CNT) {
+                const int p = i / B, k = i - (i / B) * B;
                 double acc = 0.0;
                 for (int n = vr[k]; n < vr[k + 1]; ++n) acc = fma(D.vval[n], Y[p * B + D.vcol[n]], acc);
                 dQ[i] += acc;
@@ -66,85 +123,68 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
             __syncthreads();
         }
         // Darcy source term E I: u rows from u_f, u_f rows from u_f
-        for (int i = threadIdx.x; i < 6 * B; i += CNT) {
-            const int r = i / B, k = i % B;
+        for (int i = tid; i < 6 * B; i += CNT) {
+            const int r = i / B, k = i - (i / B) * B;
             if (r < 3) dQ[(QU + r) * B + k] += gv * I[(QUF + r) * B + k];
             else dQ[(QUF + r - 3) * B + k] += ev * I[(QUF + r - 3) * B + k];
         }
+        // traces of I on the four faces: tL[f][p][a] = sum_k Pf[f][a][k] I[p][k]
+        for (int t = tid; t < 4 * FQ; t += CNT) {
+            const int f = t / FQ, r = t - f * FQ, p = r / DF, a = r - p * DF;
+            const double* row = D.Pf + ((size_t)f * DF + a) * B;
+            double acc = 0.0;
+#pragma unroll 4
+            for (int k = 0; k < B; ++k) acc = fma(__ldg(row + k), I[p * B + k], acc);
+            tL[t] = acc;
+        }
         __syncthreads();
-        // faces
         for (int f = 0; f < 4; ++f) {
             const int64_t nbr = D.nb[e * 4 + f];
             const double cf = D.fc[e * 4 + f];
             const double* Fm = D.fF + ((e * 4 + f) * 2) * NQ * NQ;
-            for (int side = 0; side < (nbr >= 0 ? 2 : 1); ++side) {
-                const double* src = I;
-                if (side == 1) {
-                    // the neighbour's trace integrated over this element's interval
-                    const int c = D.cl ? D.cl[e] : 0, cr = D.cl ? D.cl[nbr] : 0;
-                    if (cr == c) {
-                        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = D.iout[nbr * QB + i];
-                    } else if (cr < c) {
-                        const double* b = D.buf + (int64_t)D.slot[nbr * D.C + c] * QB;
-                        for (int i = threadIdx.x; i < QB; i += CNT) In[i] = b[i];
-                    } else {
-                        // larger neighbour: dt_r sum_s Qt_s int_a^b chi_s over the sub-interval
-                        const int T = N + 1;
-                        if (threadIdx.x == 0) {
-                            const int64_t ks = D.tick + 1 - ((int64_t)1 << c);
-                            const int64_t m = (ks >> cr) << cr;
-                            const double a = (double)(ks - m) / (double)((int64_t)1 << cr);
-                            const double bb = (double)(D.tick + 1 - m) / (double)((int64_t)1 << cr);
-                            // int_a^b P_s(2 tau - 1) dtau = (1/2) [ (P_{s+1} - P_{s-1}) / (2s+1) ]_{2a-1}^{2b-1}
-                            double P0[MAX_N + 3], P1[MAX_N + 3];
-                            const double x0 = 2 * a - 1, x1 = 2 * bb - 1;
-                            P0[0] = 1;
-                            P0[1] = x0;
-                            P1[0] = 1;
-                            P1[1] = x1;
-                            for (int n = 1; n <= T; ++n) {
-                                P0[n + 1] = ((2 * n + 1) * x0 * P0[n] - n * P0[n - 1]) / (n + 1);
-                                P1[n + 1] = ((2 * n + 1) * x1 * P1[n] - n * P1[n - 1]) / (n + 1);
-                            }
-                            wts[0] = 0.5 * (x1 - x0);
-                            for (int sidx = 1; sidx < T; ++sidx)
-                                wts[sidx] = 0.5 * ((P1[sidx + 1] - P1[sidx - 1]) - (P0[sidx + 1] - P0[sidx - 1])) /
-                                            (2 * sidx + 1);
-                        }
-                        __syncthreads();
-                        const double dtr = D.econst[nbr * stride + ec_scalars(N) + 2];
-                        const double* qr = D.qt + nbr * (int64_t)QB * T;
-                        for (int i = threadIdx.x; i < QB; i += CNT) {
-                            double acc = 0.0;
-                            for (int sidx = 0; sidx < T; ++sidx) acc = fma(qr[i * T + sidx], wts[sidx], acc);
-                            In[i] = dtr * acc;
-                        }
-                    }
-                    src = In;
-                }
-                for (int i = threadIdx.x; i < NQ * NQ; i += CNT) F[i] = Fm[side * NQ * NQ + i];
+            const bool inner = nbr >= 0;
+            for (int i = tid; i < (inner ? 2 : 1) * NQ * NQ; i += CNT) F[i] = Fm[i];
+            if (inner) {
+                neighbour_integral<N>(D, e, nbr, In, wts);
                 __syncthreads();
-                for (int i = threadIdx.x; i < QB; i += CNT) {
-                    const int p = i / B, l = i % B;
+                const double* Pn = D.Pnb + (size_t)D.tab[e * 4 + f] * DF * B;
+                for (int t = tid; t < FQ; t += CNT) {
+                    const int p = t / DF, a = t - p * DF;
+                    const double* row = Pn + (size_t)a * B;
                     double acc = 0.0;
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) acc = fma(F[p * NQ + q], src[q * B + l], acc);
-                    Y[i] = acc;
+#pragma unroll 4
+                    for (int k = 0; k < B; ++k) acc = fma(__ldg(row + k), In[p * B + k], acc);
+                    tR[t] = acc;
                 }
-                __syncthreads();
-                const double* Fmat = side == 0 ? D.Floc + (size_t)f * B * B
-                                               : D.Fnb + (size_t)D.tab[e * 4 + f] * B * B;
-                for (int i = threadIdx.x; i < QB; i += CNT) {
-                    const int p = i / B, k = i % B;
-                    const double* row = Fmat + (size_t)k * B;
-                    double acc = 0.0;
-                    for (int l = 0; l < B; ++l) acc = fma(__ldg(row + l), Y[p * B + l], acc);
-                    dQ[i] -= cf * D.minv[k] * acc;
-                }
-                __syncthreads();
             }
+            __syncthreads();
+            // u = c_f (F^- tL + F^+ tR)
+            for (int t = tid; t < FQ; t += CNT) {
+                const int p = t / DF, a = t - p * DF;
+                double acc = 0.0;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc = fma(F[p * NQ + q], tL[f * FQ + q * DF + a], acc);
+                if (inner) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) acc = fma(F[NQ * NQ + p * NQ + q], tR[q * DF + a], acc);
+                }
+                U[f * FQ + t] = cf * acc;
+            }
+            __syncthreads();
         }
-        for (int i = threadIdx.x; i < QB; i += CNT) D.q[e * QB + i] += dQ[i];
+        // dQ[p][k] -= M_kk^{-1} sum_f sum_a Pf[f][a][k] U[f][p][a], then Q += dQ
+        for (int i = tid; i < QB; i += CNT) {
+            const int p = i / B, k = i - (i / B) * B;
+            double acc = 0.0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const double* col = D.Pf + (size_t)f * DF * B + k;
+                const double* u = U + f * FQ + p * DF;
+#pragma unroll 4
+                for (int a = 0; a < DF; ++a) acc = fma(__ldg(col + (size_t)a * B), u[a], acc);
+            }
+            D.q[e * QB + i] += dQ[i] - D.minv[k] * acc;
+        }
         __syncthreads();
     }
 }
@@ -210,18 +250,31 @@ __global__ void receiver_kernel(int B, const double* q, int32_t nrec, const int6
     out[r * stride_out + p] = acc;
 }
 
+template <int N>
+int launch_corr_n(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+    constexpr int B = n_modes(N), DF = (N + 1) * (N + 2) / 2;
+    const size_t smem = sizeof(double) * (4 * NQ * B + 9 * NQ * DF);
+    cudaError_t err = cudaFuncSetAttribute(corrector_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
+    corrector_kernel<N><<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace
 
 int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
     if (count <= 0) return 0;
     if (d.dw) return launch_corrector_dw(d, elems, count, stream);
-    const int B = n_modes(d.N);
-    const size_t smem = sizeof(double) * 4 * NQ * B;
-    cudaError_t err = cudaFuncSetAttribute(corrector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return (int)err;
-    const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    corrector_kernel<<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count);
-    return (int)cudaGetLastError();
+    switch (d.N) {
+        case 1: return launch_corr_n<1>(d, elems, count, stream);
+        case 2: return launch_corr_n<2>(d, elems, count, stream);
+        case 3: return launch_corr_n<3>(d, elems, count, stream);
+        case 4: return launch_corr_n<4>(d, elems, count, stream);
+        case 5: return launch_corr_n<5>(d, elems, count, stream);
+        case 6: return launch_corr_n<6>(d, elems, count, stream);
+        default: return (int)cudaErrorInvalidValue;
+    }
 }
 
 int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const int32_t* slot, const double* iout,

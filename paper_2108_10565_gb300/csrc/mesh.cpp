@@ -353,6 +353,82 @@ void triangle_rule(int N, std::vector<double>& a, std::vector<double>& b, std::v
 }
 }  // namespace
 
+// Face trace operators.  With {psi_a} orthonormal on the reference triangle
+// under the quadrature weights (d_f = (N+1)(N+2)/2 functions, from the
+// Cholesky factor of the monomial Gram matrix), the trace of every basis
+// function on a face is a polynomial of degree <= N in the face parameters, so
+//   phi_k(chi_f(t)) = sum_a Pf[f][a][k] psi_a(t)   exactly, and
+//   Floc[f] = Pf[f]^T Pf[f],  Fnb[f,h,s] = Pf[f]^T Pnb[f,h,s]
+// with Pnb the neighbour's trace seen in this face's parameters.
+void face_traces(int N, std::vector<double>& Pf, std::vector<double>& Pnb) {
+    const int B = n_modes(N), df = (N + 1) * (N + 2) / 2;
+    std::vector<double> qa, qb, qw;
+    triangle_rule(N, qa, qb, qw);
+    const int nq = (int)qw.size();
+    // psi at the quadrature points: [nq][df]; the starting functions are the
+    // collapsed-coordinate (Dubiner) polynomials of the triangle, already
+    // orthogonal, so the Cholesky step only normalises them
+    std::vector<long double> m((size_t)nq * df), G((size_t)df * df, 0.0L), Lc((size_t)df * df, 0.0L);
+    for (int q = 0; q < nq; ++q) {
+        int i = 0;
+        const long double a = qa[q], b = qb[q];
+        for (int g = 0; g <= N; ++g)
+            for (int e = 0; e <= g; ++e) {
+                const int ii = g - e, jj = e;
+                m[(size_t)q * df + i++] = hjacobi(ii, 0, 0, 2 * a - (1 - b), 1 - b) * hjacobi(jj, 2 * ii + 1, 0, 2 * b - 1, 1);
+            }
+    }
+    for (int q = 0; q < nq; ++q)
+        for (int i = 0; i < df; ++i)
+            for (int j = 0; j < df; ++j) G[i * df + j] += qw[q] * m[(size_t)q * df + i] * m[(size_t)q * df + j];
+    for (int j = 0; j < df; ++j) {
+        long double d = G[j * df + j];
+        for (int k = 0; k < j; ++k) d -= Lc[j * df + k] * Lc[j * df + k];
+        Lc[j * df + j] = std::sqrt(d);
+        for (int i = j + 1; i < df; ++i) {
+            long double v = G[i * df + j];
+            for (int k = 0; k < j; ++k) v -= Lc[i * df + k] * Lc[j * df + k];
+            Lc[i * df + j] = v / Lc[j * df + j];
+        }
+    }
+    std::vector<long double> psi((size_t)nq * df);
+    for (int q = 0; q < nq; ++q)
+        for (int i = 0; i < df; ++i) {
+            long double v = m[(size_t)q * df + i];
+            for (int k = 0; k < i; ++k) v -= Lc[i * df + k] * psi[(size_t)q * df + k];
+            psi[(size_t)q * df + i] = v / Lc[i * df + i];
+        }
+    std::vector<long double> acc((size_t)4 * df * B, 0.0L), accn((size_t)96 * df * B, 0.0L);
+    std::vector<double> ph(B);
+    for (int q = 0; q < nq; ++q) {
+        const double lam[3] = {1 - qa[q] - qb[q], qa[q], qb[q]};
+        for (int f = 0; f < 4; ++f) {
+            double xi[3];
+            face_point(f, lam, xi);
+            basis_at(N, xi, ph.data());
+            for (int a = 0; a < df; ++a) {
+                const long double c = qw[q] * psi[(size_t)q * df + a];
+                for (int k = 0; k < B; ++k) acc[((size_t)f * df + a) * B + k] += c * ph[k];
+            }
+            for (int h = 0; h < 4; ++h)
+                for (int s = 0; s < 6; ++s) {
+                    double mu[3];
+                    for (int i = 0; i < 3; ++i) mu[PERM[s][i]] = lam[i];
+                    double xr[3];
+                    face_point(h, mu, xr);
+                    basis_at(N, xr, ph.data());
+                    const size_t t = ((size_t)f * 4 + h) * 6 + s;
+                    for (int a = 0; a < df; ++a) {
+                        const long double c = qw[q] * psi[(size_t)q * df + a];
+                        for (int l = 0; l < B; ++l) accn[(t * df + a) * B + l] += c * ph[l];
+                    }
+                }
+        }
+    }
+    Pf.assign(acc.begin(), acc.end());
+    Pnb.assign(accn.begin(), accn.end());
+}
+
 void face_matrices(int N, std::vector<double>& Floc, std::vector<double>& Fnb) {
     const int B = n_modes(N);
     std::vector<double> qa, qb, qw;

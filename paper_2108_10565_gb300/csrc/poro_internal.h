@@ -111,6 +111,9 @@ void basis_at(int N, const double xi[3], double* phi);
 // Floc[4][B][B] = int_face phi_k phi_l, Fnb[4][4][6][B][B] = int_face phi_k(L) phi_l(R)
 // for local face f, neighbour face h, vertex permutation s
 void face_matrices(int N, std::vector<double>& Floc, std::vector<double>& Fnb);
+// Pf[4][df][B], Pnb[96][df][B] with Floc[f] = Pf^T Pf, Fnb[f,h,s] = Pf^T Pnb,
+// df = (N+1)(N+2)/2 (traces in a basis orthonormal on the reference triangle)
+void face_traces(int N, std::vector<double>& Pf, std::vector<double>& Pnb);
 int face_permutation_index(const int p[3]);
 
 // ----- device side (kernels) -----
@@ -200,18 +203,19 @@ struct CorrectorData {
     const int32_t* tab = nullptr;     // [ne][4] neighbour table index f*24 + h*6 + s, or -1
     const double* fc = nullptr;       // [ne][4] 2 |S_f| / |J|
     const double* fF = nullptr;       // [ne][4][2][169] flux solver matrices
-    const double* Floc = nullptr;     // [4][B][B]
-    const double* Fnb = nullptr;      // [96][B][B]
     const int32_t* vrow = nullptr;    // volume CSR rows [3][B+1] (absolute)
     const int32_t* vcol = nullptr;
     const double* vval = nullptr;     // Kv^j_kl = M_ll Khat^j_lk / M_kk
     const double* minv = nullptr;     // [B] 1 / M_kk
+    // face traces (df = (N+1)(N+2)/2): Floc^f = Pf^T Pf, Fnb^{f,h,s} = Pf^T Pnb
+    const double* Pf = nullptr;       // [4][df][B]
+    const double* Pnb = nullptr;      // [96][df][B]
     // double-binary32 (hi, lo) copies for the mixed-precision form (dw = true:
     // the corrector runs in double-binary32 and fF is not needed)
     bool dw = false;
     const float* fF2 = nullptr;       // [ne][4][2][169] pairs
-    const float* Floc2 = nullptr;     // [4][B][B] pairs
-    const float* Fnb2 = nullptr;      // [96][B][B] pairs
+    const float* Pf2 = nullptr;       // [4][df][B] pairs
+    const float* Pnb2 = nullptr;      // [96][df][B] pairs
     const float* vval2 = nullptr;     // Kv^j values, pairs
     // clustered local time stepping (all nullptr / 1 for global time stepping)
     int C = 1;                        // number of clusters
