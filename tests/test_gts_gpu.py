@@ -168,3 +168,32 @@ def test_graphs_autotune_and_variants_agree(L):
             L.poro_destroy(ctx)
     for Q, s in out[1:]:
         assert np.array_equal(Q, out[0][0]) and np.array_equal(s, out[0][1])
+
+
+@pytest.mark.parametrize("N", [5])
+def test_mixed_time_stepping_matches_fp64_at_scale(L, N):
+    """48,000 elements (periodic 20^3 Kuhn mesh), random DOFs, two global
+    steps: the mixed-precision form (tensor-core predictor with refinement,
+    double-binary32 corrector) matches the binary64 form to 1e-10 relative per
+    element.  (Each form is pinned to the oracle on small meshes above; this
+    checks the full-size launch configuration.)"""
+    mesh = inputs.kuhn_box_mesh(20)
+    ne = len(mesh["tets"])
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    Q0 = np.random.default_rng(5).standard_normal((ne, 13, B))
+    out = []
+    for precision in (0, 1):
+        ctx = L.poro_create(0, N, precision)
+        try:
+            L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+            L.poro_set_materials(ctx, mats)
+            dt, _ = L.poro_set_clusters(ctx, 0.5, 1)
+            L.poro_set_dofs(ctx, Q0)
+            L.poro_advance(ctx, 2.5 * dt)
+            out.append(L.poro_get_dofs(ctx))
+        finally:
+            L.poro_destroy(ctx)
+    a, b = out[1].reshape(ne, -1), out[0].reshape(ne, -1)
+    err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    assert err.max() <= 1e-10, err.max()
