@@ -178,6 +178,21 @@ poro_status poro_sync(poro_ctx* ctx, int32_t timeout_ms);
 poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const double* Q0_dev,
                              double* Qt_dev, double* I_dev, poro_solver solver, void* stream);
 
+/* End-to-end predictor from host buffers: Q0 of every element in, I out, with
+ * the host<->device copies overlapped with the kernels.  The population is
+ * cut into chunks of `chunk_elems` elements (0: automatic, about 8 chunks);
+ * chunk i's Q0 copy, predictor (solver as in poro_predict) and I copy run on
+ * three streams, so one chunk's copies run under another chunk's kernel.
+ * q0_host[n_elem][13][B] is read and becomes the context's DOFs;
+ * I_out[n_elem][13][B] is written; the full predictor stays on the device
+ * (poro_get_predictor).  Pinned host memory gives the overlap; pageable
+ * memory works without it.  Synchronous: returns when I_out is complete.
+ * (The paper has no counterpart: it is the host boundary of a batched GPU
+ * predictor.)  Errors: PORO_EINVAL, PORO_ESTATE (no population),
+ * PORO_EUNSUPPORTED, PORO_ECUDA, PORO_ETIMEOUT (a bounded device wait gave up). */
+poro_status poro_predict_host(poro_ctx* ctx, const double* q0_host, double* I_out, int64_t chunk_elems,
+                              poro_solver solver);
+
 /* ------------------------------------------------------ meshes, corrector, time stepping */
 /* A conforming tetrahedral mesh (Section "Spatial discretisation"):
  * xyz[n_vert][3] vertex coordinates, tet[n_elem][4] vertex ids, nb[n_elem][4]

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("poro_get_integrated", _i32, [_vp, _i64, _i64, _vp]),
     ("poro_sync", _i32, [_vp, _i32]),
     ("poro_predict_dev", _i32, [_vp, _i64, _i64, _vp, _vp, _vp, _c.c_int, _vp]),
+    ("poro_predict_host", _i32, [_vp, _vp, _vp, _i64, _c.c_int]),
     ("poro_flop_count", _i32, [_vp, _i32, _pd]),
     ("poro_set_refinement", _i32, [_vp, _i32]),
     ("poro_lu_bytes", _i32, [_c.c_int, _i64, _c.POINTER(_c.c_size_t)]),
@@ -216,6 +217,18 @@ def poro_get_integrated(ctx, first, count, out=None):
 
 def poro_sync(ctx, timeout_ms=-1):
     return _check(lib().poro_sync(ctx, timeout_ms), ctx)
+
+
+def poro_predict_host(ctx, Q0, out=None, chunk_elems=0, solver=PORO_SOLVE_BLOCK):
+    """End to end from host arrays: Q0[n][13][B] in, I[n][13][B] out, copies
+    overlapped with the kernels (pass pinned arrays for the overlap)."""
+    N, _, n = poro_get_info(ctx)
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    q = _f64(Q0)
+    if out is None:
+        out = np.empty((n, 13, B))
+    _check(lib().poro_predict_host(ctx, _ptr(q), _ptr(out), chunk_elems, solver), ctx)
+    return out
 
 
 def poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver=PORO_SOLVE_BLOCK, stream=None):

@@ -23,6 +23,9 @@ struct poro_ctx {
     int N = 0, B = 0, T = 0;
     poro_precision prec = PORO_FP64;
     cudaStream_t stream = nullptr;
+    // copy streams and chunk events of poro_predict_host (created on first use)
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_k;
     poro::ReferenceData ref;
     poro::DeviceReference dref;
     poro::MixedReference mref;
@@ -475,6 +478,10 @@ poro_status poro_destroy(poro_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_population(c);
     free_reference(c);
+    for (cudaEvent_t ev : c->ev_in) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_k) cudaEventDestroy(ev);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return PORO_OK;
@@ -618,6 +625,65 @@ poro_status poro_predict_dev(poro_ctx* c, int64_t first, int64_t count, const do
     cudaSetDevice(c->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     return dispatch_predict(c, first, count, q0, qt, iout, solver, st);
+}
+
+static poro_status device_status(poro_ctx* c, const char* who);
+
+poro_status poro_predict_host(poro_ctx* c, const double* q0_host, double* I_out, int64_t chunk_elems,
+                              poro_solver solver) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_predict_host: ctx is NULL");
+    if (!c->d_econst) return fail(c, PORO_ESTATE, "poro_predict_host: no element population loaded");
+    if (c->n_elem > 0 && (!q0_host || !I_out)) return fail(c, PORO_EINVAL, "poro_predict_host: NULL buffer");
+    if (chunk_elems < 0) return fail(c, PORO_EINVAL, "poro_predict_host: negative chunk size");
+    const int64_t n = c->n_elem;
+    if (n == 0) return PORO_OK;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaSuccess;
+    if (!c->s_in && (e = cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(c, e, "poro_predict_host");
+    if (!c->s_out && (e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(c, e, "poro_predict_host");
+    int64_t chunk = chunk_elems > 0 ? chunk_elems : ((n + 7) / 8 + 255) / 256 * 256;
+    if (chunk > n) chunk = n;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    if (nchunks > 4096) return fail(c, PORO_EINVAL, "poro_predict_host: more than 4096 chunks");
+    while ((int64_t)c->ev_in.size() < nchunks) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "poro_predict_host");
+        c->ev_in.push_back(a);
+        c->ev_k.push_back(b);
+    }
+    // nothing queued earlier on the context stream may still use the buffers
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "poro_predict_host");
+    const size_t per = (size_t)NQ * c->B;
+    for (int64_t i = 0; i < nchunks; ++i) {
+        const int64_t first = i * chunk, cnt = std::min(chunk, n - first);
+        if ((e = cudaMemcpyAsync(c->d_q0 + first * per, q0_host + first * per, cnt * per * sizeof(double),
+                                 cudaMemcpyHostToDevice, c->s_in)) != cudaSuccess ||
+            (e = cudaEventRecord(c->ev_in[i], c->s_in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c->stream, c->ev_in[i], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "poro_predict_host: copy in");
+        poro_status st = dispatch_predict(c, first, cnt, c->d_q0 + first * per, c->d_qt + first * per * c->T,
+                                          c->d_iout + first * per, solver, c->stream);
+        if (st != PORO_OK) {
+            cudaStreamSynchronize(c->s_in);
+            cudaStreamSynchronize(c->stream);
+            return st;
+        }
+        if ((e = cudaEventRecord(c->ev_k[i], c->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c->s_out, c->ev_k[i], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(I_out + first * per, c->d_iout + first * per, cnt * per * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->s_out)) != cudaSuccess)
+            return cuda_fail(c, e, "poro_predict_host: copy out");
+    }
+    if ((e = cudaStreamSynchronize(c->s_out)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess || (e = cudaStreamSynchronize(c->s_in)) != cudaSuccess)
+        return cuda_fail(c, e, "poro_predict_host");
+    c->have_dofs = true;
+    c->have_pred = true;
+    return device_status(c, "poro_predict_host");
 }
 
 poro_status poro_lu_bytes(int degree_N, int64_t count, size_t* bytes) {

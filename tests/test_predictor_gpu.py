@@ -172,3 +172,38 @@ def test_sync_timeout_is_recoverable(L):
         assert rel_l2(qt[0], oracle_predictor(d, 0)) <= TOL
     finally:
         L.poro_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("chunk", [0, 7, 1000])
+def test_host_pipeline_matches_step_by_step(L, prec, chunk):
+    """poro_predict_host (chunked copies overlapped with the kernels) gives
+    bitwise the same I as set_dofs + predict + get_integrated, for automatic,
+    ragged (7 elements, last chunk partial) and single-chunk sizes; the full
+    predictor it leaves on the device matches too."""
+    d = population(33, 4, seed=11)
+    qt_ref, i_ref = _run_host(L, d, prec)
+    ctx = L.poro_create(0, d["N"], prec)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        i_got = L.poro_predict_host(ctx, d["Q0"], chunk_elems=chunk)
+        qt_got = L.poro_get_predictor(ctx, 0, 33)
+    finally:
+        L.poro_destroy(ctx)
+    np.testing.assert_array_equal(i_got, i_ref)
+    np.testing.assert_array_equal(qt_got, qt_ref)
+
+
+def test_host_pipeline_errors(L):
+    d = population(5, 2, seed=12)
+    ctx = L.poro_create(0, d["N"], 0)
+    try:
+        with pytest.raises(L.PoroError) as ex:
+            L.poro_predict_host(ctx, d["Q0"])
+        assert ex.value.status == L.PORO_ESTATE
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        with pytest.raises(L.PoroError) as ex:
+            L.poro_predict_host(ctx, d["Q0"], chunk_elems=-1)
+        assert ex.value.status == L.PORO_EINVAL
+    finally:
+        L.poro_destroy(ctx)
