@@ -166,8 +166,7 @@ void free_reference(poro_ctx* c) {
     dfree(c->lref.krow);
     dfree(c->lref.kcol);
     dfree(c->lref.kval);
-    dfree(c->mref.res_row);
-    dfree(c->mref.res_int);
+
     dfree(c->mref.res_inv);
     dfree(c->mref.res_order8);
     dfree(c->mref.res_order4);
@@ -444,8 +443,9 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             }
         }
         c->mref.base = &c->dref;
-        if ((e = upload((void**)&c->mref.res_row, rrow.data(), rrow.size() * sizeof(int32_t))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.res_int, rint.data(), rint.size() * sizeof(int32_t))) != cudaSuccess ||
+        if ((e = (cudaError_t)poro::upload_residual_table(degree_N, rrow.data(), rint.data(), (int)rint.size())) !=
+                cudaSuccess ||
+
             (e = upload((void**)&c->mref.res_inv, rinv.data(), rinv.size() * sizeof(float))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_order8, ord8.data(), ord8.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_order4, ord4.data(), ord4.size() * sizeof(int32_t))) != cudaSuccess ||

@@ -134,8 +134,6 @@ struct DeviceReference {
 // Extra device data of the mixed-precision (refinement) path.
 struct MixedReference {
     const DeviceReference* base = nullptr;
-    int32_t* res_row = nullptr;     // [3][B+1] full-row CSR of Khat^j, absolute offsets
-    int32_t* res_int = nullptr;     // (numerator << 7) | column m; Khat^j[l, m] = numerator / d_jl
     float* res_inv = nullptr;       // [3][B][2] 1 / d_jl as (hi, lo) binary32 words
     // residual rows dealt to 8, 4 and 2 warps (longest work first, each row to
     // the least loaded warp): [warps + 1] list starts, then the lists
@@ -150,6 +148,16 @@ struct MixedReference {
     int32_t tc_off[MAX_N + 1][3] = {};
     int32_t* status = nullptr;      // device word: 1 after a bounded wait gave up
 };
+
+// Fill the constant-memory residual table of degree N on the current device
+// (row pointers relative to the entries); idempotent, same data for every
+// context of that degree.
+int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, int n_entries);
+
+// Fill the constant-memory residual table of degree N on the current device
+// (row pointers relative to the entries); idempotent, same data for every
+// context of that degree.
+int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, int n_entries);
 
 // Launch the mixed-precision predictor (binary32 sweeps, `refine` residual
 // corrections in double-binary32) for `count` elements.

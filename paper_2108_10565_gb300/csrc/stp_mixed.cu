@@ -35,6 +35,10 @@
 //       + E*_pp Q[p,l,u] + G Q[uf,l,u] - sum_j sum_q A^{j*}_pq Y^j[q,u]
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "alg3_device.cuh"
 #include "dw_device.cuh"
 #include "tc_device.cuh"
@@ -50,8 +54,6 @@ struct K2Params {
     double* iout;
     int64_t count;
     int stride;
-    const int32_t* res_row;   // [3][B+1] full-row CSR of Khat^j (absolute offsets)
-    const int32_t* res_int;   // (numerator << 7) | column: Khat^j[l, m] = numerator / d_jl
     const float2* res_inv;    // [3][B] 1 / d_jl as (hi, lo)
     const int32_t* res_order; // [warps + 1] list starts, then each warp's residual rows
     const float* zinv;        // Z^{-1} [T][T] binary32
@@ -59,6 +61,16 @@ struct K2Params {
     int32_t tc_off[MAX_N + 1][3];
     int32_t* status;          // set to 1 if a bounded wait gave up
 };
+
+// Residual CSR of every degree in constant memory: the table depends only on
+// N (the reference matrices), so all contexts of one device share it.  Per N:
+// [3][B+1] row pointers (relative to the entries), then the packed entries.
+constexpr int res_words(int N) {
+    return N == 1 ? 21 : N == 2 ? 79 : N == 3 ? 265 : N == 4 ? 755 : N == 5 ? 1879 : 4175;
+}
+constexpr int res_base(int N) { return N <= 1 ? 0 : res_base(N - 1) + res_words(N - 1); }
+constexpr int RES_CONST_WORDS = res_base(MAX_N) + res_words(MAX_N);
+__constant__ int32_t c_res[RES_CONST_WORDS];
 
 // residual star terms per row p: 3 directions x 6 slots (rows have 2, 4 or 6
 // entries; unused slots carry a zero coefficient)
@@ -293,11 +305,13 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
             float yh[PUL], yl[PUL];
 #pragma unroll
             for (int k = 0; k < PUL; ++k) yh[k] = yl[k] = 0.f;
-            const int n0 = __ldg(P.res_row + j * (B + 1) + l), n1 = __ldg(P.res_row + j * (B + 1) + l + 1);
-            int nx = n0 < n1 ? __ldg(P.res_int + n0) : 0;
+            const int32_t* cr = c_res + res_base(N);
+            const int32_t* ce = cr + 3 * (B + 1);
+            const int n0 = cr[j * (B + 1) + l], n1 = cr[j * (B + 1) + l + 1];
+            int nx = n0 < n1 ? ce[n0] : 0;
             for (int n = n0; n < n1; ++n) {
                 const int kv = nx;
-                if (n + 1 < n1) nx = __ldg(P.res_int + n + 1);
+                if (n + 1 < n1) nx = ce[n + 1];
                 const float cv = (float)(kv >> 7);
                 const int mo = (kv & 127) * Q1S + lane;
 #pragma unroll
@@ -545,8 +559,6 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     P.iout = iout;
     P.count = count;
     P.stride = elem_const_stride(N);
-    P.res_row = ref.res_row;
-    P.res_int = ref.res_int;
     P.res_inv = reinterpret_cast<const float2*>(ref.res_inv);
     P.res_order = NT_ == 256 ? ref.res_order8 : (NT_ == 128 ? ref.res_order4 : ref.res_order2);
     P.zinv = ref.zinv_f32;
@@ -594,6 +606,25 @@ int launch_n(const MixedReference& ref, int refine, int variant, const int32_t* 
 }
 
 }  // namespace
+
+int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, int n_entries) {
+    const int B = n_modes(N);
+    if (N < 1 || N > MAX_N || 3 * (B + 1) + n_entries != res_words(N)) return (int)cudaErrorInvalidValue;
+    // once per (device, N): later contexts find the same data in place
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, N})) return 0;
+    const int base = res_base(N);
+    e = cudaMemcpyToSymbol(c_res, rows, sizeof(int32_t) * 3 * (B + 1), sizeof(int32_t) * base);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(c_res, entries, sizeof(int32_t) * n_entries, sizeof(int32_t) * (base + 3 * (B + 1)));
+    if (e == cudaSuccess) done.insert({dev, N});
+    return (int)e;
+}
 
 int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
                      const double* econst, double* qt, double* iout, void* stream, int variant) {
