@@ -284,6 +284,17 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
     return true;
 }
 
+// Residual lanes by star width: the 13 T pairs (p, u) ordered as rows
+// {sxx, syy, szz, p} (6 entries per direction), {u, v, w, uf, vf, wf} (4),
+// {sxy, syz, sxz} (2); slot s -> p * T + u, or -1 past the last pair
+__host__ __device__ constexpr int r2_class(int T, int s) { return s < 4 * T ? 0 : (s < 10 * T ? 1 : 2); }
+__host__ __device__ constexpr int r2_slot(int T, int s) {
+    return s >= NQ * T ? -1
+           : s < 4 * T ? ((s / T) < 3 ? s / T : QP) * T + s % T
+           : s < 10 * T ? (((s - 4 * T) / T) < 3 ? QU + (s - 4 * T) / T : QUF + (s - 4 * T) / T - 3) * T + (s - 4 * T) % T
+                        : (SXY + (s - 10 * T) / T) * T + (s - 10 * T) % T;
+}
+
 // Q1 / D1 layout of the residual: mode-major, Q[m * Q1S + p * T + u], so the
 // (q, u) lanes of one mode are consecutive words
 template <int N, int REF, int NT_>
@@ -331,20 +342,25 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
                 if (pu < PT) Y[j * PT + pu] = make_float2(h, lo);
             }
         }
+        // R2 lanes are dealt by the width of row p's star pattern (6, 4 or 2
+        // entries per direction), so a warp's padded star loop is as short as
+        // its widest row: slot s -> (p, u) via r2_slot
         // b0[p, l] (hi, lo) sits in W[p, l, 0..1]; read before row l is written
         float2 bv[PUL];
 #pragma unroll
         for (int k = 0; k < PUL; ++k) {
-            const int pu = lane + 32 * k;
-            const int p = pu < PT ? pu / T : 0;
+            const int pu = r2_slot(T, lane + 32 * k);
+            const int p = pu >= 0 ? pu / T : 0;
             bv[k] = make_float2(W[p * QS + l * T], W[p * QS + l * T + 1]);
         }
         __syncwarp();
         // R2: assemble r[p, l, u]
 #pragma unroll
         for (int k = 0; k < PUL; ++k) {
-            const int pu = lane + 32 * k;
-            if (pu < PT) {
+            const int pu = r2_slot(T, lane + 32 * k);
+            constexpr int WID[3] = {6, 4, 2};
+            const int wk = WID[r2_class(T, 32 * k)];  // widest row of this slot
+            if (pu >= 0) {
                 const int p = pu / T, u = pu % T;
                 const int bq = l * Q1S + p * T;
                 float h = 0.f, lo = 0.f;
@@ -367,15 +383,20 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
                     else
                         dw_mac1(h, lo, c.x, c.y, Q1[src]);
                 }
-                // - sum_j sum_q A^{j*}_pq Y^j[q, u]: row p's 18 padded entries
+                // - sum_j sum_q A^{j*}_pq Y^j[q, u]: row p's entries of each
+                // direction, padded to the slot width
                 // (-coef hi, -coef lo, offset of Y^j[q, 0])
                 const float4* st = stab + p * STAR_SLOTS;
 #pragma unroll
-                for (int t = 0; t < STAR_SLOTS; ++t) {
-                    const float4 c = st[t];
-                    const float2 yv = Y[__float_as_int(c.z) + u];
-                    dw_mac(h, lo, c.x, c.y, yv.x, yv.y);
-                }
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        if (t < wk) {
+                            const float4 c = st[j * 6 + t];
+                            const float2 yv = Y[__float_as_int(c.z) + u];
+                            dw_mac(h, lo, c.x, c.y, yv.x, yv.y);
+                        }
+                    }
                 W[p * QS + l * T + u] = __fadd_rn(h, lo);
             }
         }
