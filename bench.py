@@ -174,6 +174,11 @@ def run_reference(args):
 # residual: 9 for an exact coefficient (Khat numerators, Z), 12 for a
 # double-word coefficient (star terms); weighted over the residual's mix.
 DW_OPS_PER_MAC = 9.6
+# DRAM bytes (read + write) per element of the headline kernels at N = 6, from
+# one ncu capture each of the 20,000-element case (dram__bytes_read.sum +
+# dram__bytes_write.sum divided by the elements; the traffic grows in
+# proportion to the elements, so a launch of n elements moves n times this)
+TRAFFIC_BYTES_PER_ELEMENT = {("mixed", 6, 1): 77510.0, ("fp64", 6, None): 77506.0}
 # nominal tf32 : bf16 dense tensor ratio (1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -462,8 +467,10 @@ def run_ours(args):
         if r["prec"] == L.PORO_FP64:
             ach = r["flops"][0] * n / t / 1e12
             peak = fp64_alu_peak_tflops(mhz)
+            tb = TRAFFIC_BYTES_PER_ELEMENT.get(("fp64", N, None))
             return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "kernel": f"stp_fp64_kernel<{N}>", "flops_per_element": r["flops"][0],
+                    "traffic": tb * n if tb else None, "kernel": f"stp_fp64_kernel<{N}>",
+                    "flops_per_element": r["flops"][0],
                     "peak_source": "binary64 FMA pipe: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled clock"}
         # Algorithm 3 flops split by engine: the Khat products (S4b) run on the
         # tensor cores (tf32 hi/lo, 3 products), the rest of the sweeps and
@@ -485,8 +492,9 @@ def run_ours(args):
         t_tc = tc_tile_flops(N) * sw * n / (tf32_peak * 1e12)
         t_min = max(t_alu, t_tc)
         peak = (f_alu + f_tc + f_res) * n / t_min / 1e12
+        tb = TRAFFIC_BYTES_PER_ELEMENT.get(("mixed", N, r["sweeps"]))
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}>",
+                "traffic": tb * n if tb else None, "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}>",
                 "flops_per_element": {"binary32_pipe": f_alu, "tensor_khat_tf32x3": f_tc,
                                       "residual_double_word": f_res},
                 "tensor": {"issued_tflops": tc_tile_flops(N) * sw * n / t / 1e12, "tf32_peak": tf32_peak,
