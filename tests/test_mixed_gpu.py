@@ -104,3 +104,25 @@ def test_mixed_full_size_against_fp64(L):
         sub = {"N": N, "vertices": d["vertices"][i:i + 1], "materials": d["materials"][i:i + 1],
                "Q0": d["Q0"][i:i + 1], "dt": dt[i:i + 1]}
         assert rel_l2(a[i].cpu().numpy(), oracle_predictor(sub, 0)) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+@pytest.mark.parametrize("sweeps", [0, 1, 2])
+def test_cta_size_variants_agree(L, N, sweeps):
+    """Both CTA sizes of the mixed kernel (the autotuner's choices: different
+    warp counts for the tensor-core epilogue, the time solves and the
+    residual's balanced row lists) give bitwise identical predictors."""
+    d = population(19, N, seed=2108 + N)
+    out = []
+    for variant in (0, 1):
+        ctx = L.poro_create(0, N, L.PORO_FP32_REFINE)
+        try:
+            L.poro_set_refinement(ctx, sweeps)
+            L.poro_set_variant(ctx, variant)
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+            L.poro_set_dofs(ctx, d["Q0"])
+            L.poro_predict(ctx)
+            out.append(L.poro_get_predictor(ctx, 0, 19))
+        finally:
+            L.poro_destroy(ctx)
+    np.testing.assert_array_equal(out[0], out[1])
