@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=6)
     ap.add_argument("--n-elem", type=int, default=200_000)
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed", "bf16x3"])
     ap.add_argument("--refine", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -183,15 +183,16 @@ TRAFFIC_BYTES_PER_ELEMENT = {("mixed", 6, 1): 77510.0, ("fp64", 6, None): 77506.
 TF32_PER_BF16 = 1.1 / 2.25
 
 
-def tc_tile_flops(N):
-    """Tensor-core flops of one binary32 sweep's Khat products as issued:
-    per degree block g and direction, 3 tf32 products of M = 128 rows,
-    N = rows l (o_g rounded up to 16), K = block columns (d_g rounded to 8)."""
+def tc_tile_flops(N, bf16=False):
+    """Tensor-core flops of one sweep's Khat products as issued: per degree
+    block g and direction, 3 split products of M = 128 rows, N = rows l (o_g
+    rounded up to 16), K = block columns (d_g rounded to 8 for tf32, 16 for
+    bf16)."""
     tot = 0
     for g in range(1, N + 1):
         o, d = g * (g + 1) * (g + 2) // 6, (g + 1) * (g + 2) // 2
         npad = 16 if o <= 16 else (o + 15) // 16 * 16
-        kpad = (d + 7) // 8 * 8
+        kpad = (d + 15) // 16 * 16 if bf16 else (d + 7) // 8 * 8
         tot += 3 * 3 * 2 * 128 * npad * kpad
     return tot
 
@@ -410,13 +411,15 @@ def run_ours(args):
     q0 = torch.from_numpy(d["Q0"]).to(dev)
     stream = torch.cuda.Stream(device=local)
     sh = stream.cuda_stream
-    forms = {"fp64": (L.PORO_FP64, 0), "mixed": (L.PORO_FP32_REFINE, args.refine)}
-    order = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    forms = {"fp64": (L.PORO_FP64, 0), "mixed": (L.PORO_FP32_REFINE, args.refine),
+             "mixed_bf16x3": (L.PORO_BF16X3_REFINE, args.refine)}
+    order = ["fp64", "mixed", "mixed_bf16x3"] if args.precision == "both" else [
+        "mixed_bf16x3" if args.precision == "bf16x3" else args.precision]
     res, qts = {}, {}
     for name in order:
         prec, sweeps = forms[name]
         ctx = L.poro_create(local, N, prec)
-        if prec == L.PORO_FP32_REFINE:
+        if prec != L.PORO_FP64:
             L.poro_set_refinement(ctx, sweeps)
         L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
         qt = torch.empty((n, 13, B, T), dtype=torch.float64, device=dev)
@@ -450,14 +453,16 @@ def run_ours(args):
         f = L.poro_flop_count(ctx, sweeps)
         res[name] = dict(ctx=ctx, ms=ms, per=per, clocks=clocks, flops=f, sweeps=sweeps, prec=prec)
         qts[name] = qt
-    # accuracy of the mixed form against the FP64 form on every element
-    err = None
-    if "fp64" in qts and "mixed" in qts:
-        a, b = qts["mixed"], qts["fp64"]
-        e = (torch.linalg.vector_norm((a - b).reshape(n, -1), dim=1)
-             / torch.linalg.vector_norm(b.reshape(n, -1), dim=1)).double().cpu().numpy()
-        err = {"vs": "fp64 kernel (pinned to the oracle at 1e-12)", "median": float(np.median(e)),
-               "p99": float(np.quantile(e, 0.99)), "max": float(e.max())}
+    # accuracy of the mixed forms against the FP64 form on every element
+    errs = {}
+    for name in ("mixed", "mixed_bf16x3"):
+        if "fp64" in qts and name in qts:
+            a, b = qts[name], qts["fp64"]
+            e = (torch.linalg.vector_norm((a - b).reshape(n, -1), dim=1)
+                 / torch.linalg.vector_norm(b.reshape(n, -1), dim=1)).double().cpu().numpy()
+            errs[name] = {"vs": "fp64 kernel (pinned to the oracle at 1e-12)", "median": float(np.median(e)),
+                          "p99": float(np.quantile(e, 0.99)), "max": float(e.max())}
+    err = errs.get("mixed")
     del qts
 
     def roofline(name):
@@ -488,22 +493,27 @@ def run_ours(args):
         # overlapped with the tensor tiles at the tf32 peak (measured bf16
         # burst x nominal tf32 ratio); the slower of the two bounds the kernel
         t_alu = (f_alu / 2 + DW_OPS_PER_MAC * f_res / 2) * n / (152 * 128 * mhz * 1e6)
-        tf32_peak = tensor_bf16_burst * TF32_PER_BF16
-        t_tc = tc_tile_flops(N) * sw * n / (tf32_peak * 1e12)
+        bf = r["prec"] == L.PORO_BF16X3_REFINE
+        tf32_peak = tensor_bf16_burst * (1.0 if bf else TF32_PER_BF16)
+        t_tc = tc_tile_flops(N, bf) * sw * n / (tf32_peak * 1e12)
         t_min = max(t_alu, t_tc)
         peak = (f_alu + f_tc + f_res) * n / t_min / 1e12
-        tb = TRAFFIC_BYTES_PER_ELEMENT.get(("mixed", N, r["sweeps"]))
+        tb = None if bf else TRAFFIC_BYTES_PER_ELEMENT.get(("mixed", N, r["sweeps"]))
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": tb * n if tb else None, "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}>",
-                "flops_per_element": {"binary32_pipe": f_alu, "tensor_khat_tf32x3": f_tc,
+                "traffic": tb * n if tb else None,
+                "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}" + (",bf16>" if bf else ">"),
+                "flops_per_element": {"binary32_pipe": f_alu,
+                                      ("tensor_khat_bf16x3" if bf else "tensor_khat_tf32x3"): f_tc,
                                       "residual_double_word": f_res},
-                "tensor": {"issued_tflops": tc_tile_flops(N) * sw * n / t / 1e12, "tf32_peak": tf32_peak,
-                           "frac": (tc_tile_flops(N) * sw * n / t / 1e12) / tf32_peak},
+                "tensor": {"issued_tflops": tc_tile_flops(N, bf) * sw * n / t / 1e12, "peak": tf32_peak,
+                           "dtype": "bf16" if bf else "tf32",
+                           "frac": (tc_tile_flops(N, bf) * sw * n / t / 1e12) / tf32_peak},
                 "bound_times_ms": {"binary32_pipe": 1e3 * t_alu, "tensor": 1e3 * t_tc},
                 "peak_source": f"binary32 pipe issue rate (152 SM x 128 lanes x {mhz:.0f} MHz): 1 instr per FMA, "
                                f"{DW_OPS_PER_MAC} instr per double-word MAC, overlapped with the Khat tiles on the "
-                               f"tensor cores at {tf32_peak:.0f} TFLOP/s tf32 (measured bf16 burst x {TF32_PER_BF16:.3f}); "
-                               f"binary32 FMA peak {fp32_alu_peak_tflops(mhz):.1f} TFLOP/s"}
+                               + (f"tensor cores at {tf32_peak:.0f} TFLOP/s bf16 (measured burst); " if bf else
+                                  f"tensor cores at {tf32_peak:.0f} TFLOP/s tf32 (measured bf16 burst x {TF32_PER_BF16:.3f}); ")
+                               + f"binary32 FMA peak {fp32_alu_peak_tflops(mhz):.1f} TFLOP/s"}
 
     head = "mixed" if ("mixed" in res and (err is None or err["max"] <= 1e-10)) else "fp64"
     hr = res[head]
@@ -563,8 +573,10 @@ def run_ours(args):
     forms_out = {}
     for name, r in res.items():
         forms_out[name] = {"value": n * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
-                           "refine_sweeps": r["sweeps"] if name == "mixed" else None,
+                           "refine_sweeps": r["sweeps"] if name != "fp64" else None,
                            "roofline": roofline(name), "clocks": r["clocks"]}
+        if name in errs:
+            forms_out[name]["error_vs_fp64"] = errs[name]
     cfg = _workload(args)
     cfg["form"] = head
     out = {

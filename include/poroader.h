@@ -63,7 +63,9 @@ typedef enum {
     PORO_FP64 = 0,          /* every step in IEEE binary64 */
     PORO_FP32_REFINE = 1,   /* binary32 back-substitution + refinement against an
                                FP64-accurate residual of the predictor system */
-    PORO_BF16X3_REFINE = 2  /* reserved: tensor-core split products (not built) */
+    PORO_BF16X3_REFINE = 2  /* as PORO_FP32_REFINE with the tensor-core split products
+                               in bf16 (hi + lo, ~16 significant bits per product);
+                               one refinement sweep by default, as for FP32_REFINE */
 } poro_precision;
 
 typedef enum {
@@ -96,10 +98,11 @@ poro_status poro_destroy(poro_ctx* ctx);
  * context (e.g. a failed poro_create), thread-local. */
 const char* poro_last_error(const poro_ctx* ctx);
 
-/* Number of refinement sweeps of a PORO_FP32_REFINE context (0, 1 or 2;
- * default 1): each sweep forms the residual of the predictor system in
- * double-binary32 arithmetic (error-free products and sums, ~2^-48 relative)
- * and solves for the correction with the binary32 back-substitution.
+/* Number of refinement sweeps of a mixed-precision context (0, 1 or 2;
+ * default 1): each sweep forms
+ * the residual of the predictor system in double-binary32 arithmetic
+ * (error-free products and sums, ~2^-48 relative) and solves for the
+ * correction with the low-precision back-substitution.
  * Errors: PORO_EUNSUPPORTED for a PORO_FP64 context, PORO_EINVAL. */
 poro_status poro_set_refinement(poro_ctx* ctx, int32_t sweeps);
 

@@ -260,8 +260,8 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
     *out = nullptr;
     if (degree_N < 1 || degree_N > poro::MAX_N)
         return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: degree N must be in 1..6");
-    if (precision != PORO_FP64 && precision != PORO_FP32_REFINE)
-        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: precision not built");
+    if (precision != PORO_FP64 && precision != PORO_FP32_REFINE && precision != PORO_BF16X3_REFINE)
+        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: unknown precision");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "poro_create: cudaGetDeviceCount");
@@ -272,6 +272,7 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
     c->device = device;
     c->N = degree_N;
     c->prec = precision;
+    c->refine = 1;  // one sweep reaches the 1e-10 goal in both mixed forms (measured)
     std::string err;
     if (!poro::reference_data(degree_N, c->ref, err)) {
         delete c;
@@ -354,7 +355,7 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             return cuda_fail(nullptr, e, "poro_create: upload (LU)");
         }
     }
-    if (precision == PORO_FP32_REFINE) {
+    if (precision != PORO_FP64) {
         // Residual CSR of Khat^j (all rows): every row l of every Khat^j is an
         // integer row over a common denominator d (the reference matrices are
         // rational with small denominators), so an entry is packed as
@@ -417,7 +418,10 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             delete c;
             return fail(nullptr, PORO_ENUMERIC, "poro_create: " + rerr);
         }
-        // tensor-core images (tf32 hi + lo, K-major core matrices) of the blocks
+        // tensor-core images of the blocks, hi image then lo image in the
+        // K-major core-matrix layout: tf32 words, or bf16 for the bf16 form
+        const bool bf16 = precision == PORO_BF16X3_REFINE;
+        c->mref.bf16 = bf16;
         auto tf32 = [](float x) {
             uint32_t b;
             std::memcpy(&b, &x, 4);
@@ -425,20 +429,30 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             std::memcpy(&x, &b, 4);
             return x;
         };
-        std::vector<float> tci;
+        std::vector<uint8_t> tci;  // bytes
         for (int g = 1; g <= degree_N; ++g) {
-            const int NP = poro::tc_np(g), KP = poro::tc_kp(g), o = poro::block_offset(g), d = poro::block_size(g);
+            const int NP = poro::tc_np(g), KP = poro::tc_kp(g, bf16), o = poro::block_offset(g),
+                      d = poro::block_size(g);
+            const size_t es = bf16 ? 2 : 4, img = (size_t)NP * KP * es;
             for (int j = 0; j < 3; ++j) {
                 const size_t base = tci.size();
                 c->mref.tc_off[g][j] = (int32_t)base;
-                tci.resize(base + 2 * (size_t)NP * KP, 0.f);
+                tci.resize(base + 2 * img, 0);
                 for (int l = 0; l < o; ++l)
                     for (int m = 0; m < d; ++m) {
                         const double v = c->ref.khat[((size_t)j * B + l) * B + o + m];
-                        const float h = tf32((float)v);
-                        const size_t at = base + (size_t)poro::tc::kmajor_offset(l, m, KP);
-                        tci[at] = h;
-                        tci[at + (size_t)NP * KP] = tf32((float)(v - (double)h));
+                        if (bf16) {
+                            const uint16_t h = poro::tc::bf16_bits((float)v);
+                            const uint16_t lo = poro::tc::bf16_bits((float)(v - (double)poro::tc::bf16_value(h)));
+                            const size_t at = base + 2 * (size_t)poro::tc::kmajor_offset16(l, m, KP);
+                            std::memcpy(&tci[at], &h, 2);
+                            std::memcpy(&tci[at + img], &lo, 2);
+                        } else {
+                            const float h = tf32((float)v), lo = tf32((float)(v - (double)h));
+                            const size_t at = base + 4 * (size_t)poro::tc::kmajor_offset(l, m, KP);
+                            std::memcpy(&tci[at], &h, 4);
+                            std::memcpy(&tci[at + img], &lo, 4);
+                        }
                     }
             }
         }
@@ -451,7 +465,7 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
             (e = upload((void**)&c->mref.res_order4, ord4.data(), ord4.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.res_order2, ord2.data(), ord2.size() * sizeof(int32_t))) != cudaSuccess ||
             (e = upload((void**)&c->mref.zinv_f32, zf.data(), zf.size() * sizeof(float))) != cudaSuccess ||
-            (e = upload((void**)&c->mref.khat_tc, tci.data(), tci.size() * sizeof(float))) != cudaSuccess ||
+            (e = upload((void**)&c->mref.khat_tc, tci.data(), tci.size())) != cudaSuccess ||
             (e = cudaMalloc((void**)&c->mref.status, sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMemset(c->mref.status, 0, sizeof(int32_t))) != cudaSuccess) {
             free_reference(c);
@@ -466,7 +480,7 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
 
 poro_status poro_set_refinement(poro_ctx* c, int32_t sweeps) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_refinement: ctx is NULL");
-    if (c->prec != PORO_FP32_REFINE) return fail(c, PORO_EUNSUPPORTED, "poro_set_refinement: context is not mixed precision");
+    if (c->prec == PORO_FP64) return fail(c, PORO_EUNSUPPORTED, "poro_set_refinement: context is not mixed precision");
     if (sweeps < 0 || sweeps > 2) return fail(c, PORO_EINVAL, "poro_set_refinement: sweeps must be 0, 1 or 2");
     c->refine = sweeps;
     return PORO_OK;
@@ -1075,7 +1089,7 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     std::vector<double> Pf, Pnb;
     poro::face_traces(N, Pf, Pnb);
     // the mixed-precision form corrects in double-binary32: (hi, lo) copies
-    const bool dw = c->prec == PORO_FP32_REFINE;
+    const bool dw = c->prec != PORO_FP64;
     auto split = [](const std::vector<double>& x) {
         std::vector<float> o(2 * x.size());
         for (size_t i = 0; i < x.size(); ++i) {

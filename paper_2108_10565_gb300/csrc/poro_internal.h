@@ -20,9 +20,11 @@ constexpr int block_size(int g) { return (g + 1) * (g + 2) / 2; }
 constexpr int block_offset(int g) { return g * (g + 1) * (g + 2) / 6; }
 // tensor-core tile of degree block g's Khat product: N extent (rows l < o_g,
 // a multiple of 16, at least 16) and K extent (columns of the block, a
-// multiple of 8)
+// multiple of the MMA's K step: 8 for tf32 words, 16 for bf16)
 constexpr int tc_np(int g) { return block_offset(g) <= 16 ? 16 : (block_offset(g) + 15) / 16 * 16; }
-constexpr int tc_kp(int g) { return (block_size(g) + 7) / 8 * 8; }
+constexpr int tc_kp(int g, bool bf16 = false) {
+    return bf16 ? (block_size(g) + 15) / 16 * 16 : (block_size(g) + 7) / 8 * 8;
+}
 
 // Union sparsity pattern of A*, B*, C* (54 entries): for every row p the
 // columns q with a structurally non-zero Jacobian entry.  Rows are stored
@@ -134,6 +136,7 @@ struct DeviceReference {
 // Extra device data of the mixed-precision (refinement) path.
 struct MixedReference {
     const DeviceReference* base = nullptr;
+    bool bf16 = false;              // sweeps' split products in bf16 (else tf32)
     float* res_inv = nullptr;       // [3][B][2] 1 / d_jl as (hi, lo) binary32 words
     // residual rows dealt to 8, 4 and 2 warps (longest work first, each row to
     // the least loaded warp): [warps + 1] list starts, then the lists
@@ -142,8 +145,9 @@ struct MixedReference {
     int32_t* res_order2 = nullptr;
     float* zinv_f32 = nullptr;      // [T][T]
     // tensor-core images of Khat^j restricted to block g (rows l < o_g, columns
-    // of the block), K-major core-matrix layout of tc_np(g) x tc_kp(g) tf32
-    // words, hi image then lo image; tc_off[g][j] in floats
+    // of the block), K-major core-matrix layout of tc_np(g) x tc_kp(g) words
+    // (tf32 in 32-bit words, or bf16), hi image then lo image; tc_off[g][j] in
+    // bytes
     float* khat_tc = nullptr;
     int32_t tc_off[MAX_N + 1][3] = {};
     int32_t* status = nullptr;      // device word: 1 after a bounded wait gave up

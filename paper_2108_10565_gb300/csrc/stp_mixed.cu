@@ -92,7 +92,7 @@ struct K2Sizes {
     static constexpr int NT1 = N >= 5 ? 128 : (N == 4 ? 256 : 128);
 };
 
-template <int N, int REF, int NT_>
+template <int N, int REF, int NT_, int BF = 0>
 struct K2Shape : Alg3Shape<N> {
     using A = Alg3Shape<N>;
     static constexpr int NT = NT_;
@@ -105,9 +105,12 @@ struct K2Shape : Alg3Shape<N> {
     // groups of the widest block, then the Khat^j image (hi and lo).  The MMA
     // reads 16 row groups of each A tile; the rows past 13 T only feed
     // accumulator rows that are never read, so they may overlap what follows.
-    static constexpr int SBOMAX = tc_kp(N) * 8;
+    // (sizes in floats; operand words are 4 bytes for tf32, 2 for bf16)
+    static constexpr int ES = BF ? 2 : 4;
+    static constexpr int KPM = tc_kp(N, BF != 0);
+    static constexpr int SBOMAX = KPM * 8 * ES / 4;
     static constexpr int AH = (A::PT + 7) / 8 * SBOMAX;
-    static constexpr int BIMG = 2 * tc_np(N) * tc_kp(N);
+    static constexpr int BIMG = 2 * tc_np(N) * KPM * ES / 4;
     static constexpr int TC_SIZE = MAX2(2 * AH + BIMG, AH + 16 * SBOMAX);
     // shared layout in floats; the tensor-core tiles of the sweeps and the
     // per-warp Y buffers of the residual share the first region
@@ -158,7 +161,7 @@ __device__ __forceinline__ void solve_row8(float* row, const float* Zi) {
 
 // Tensor-core state of one CTA (shared addresses, barrier phases)
 struct TcState {
-    float* ah;
+    float* ah;  // A tiles (tf32 words, or bf16 values in the same bytes)
     float* al;
     uint32_t ah_s, al_s, b_s;
     uint32_t mma_bar, ld_bar;
@@ -170,7 +173,7 @@ struct TcState {
 // One binary32 sweep of Algorithm 3 with the Khat products on the tensor
 // cores.  On entry bq holds b, on exit Q.  Returns false (uniformly across the
 // CTA) if a bounded wait gave up.
-template <int N, int NT>
+template <int N, int NT, int BF>
 __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, const float* zin, const float gcoup,
                               const K2Params& P, TcState& S) {
     using A = Alg3Shape<N>;
@@ -198,9 +201,10 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         }
         __syncthreads();
         if (g == 0) break;
-        const int KP = tc_kp(g), NP = tc_np(g);
-        const uint32_t sbo = (uint32_t)KP * 32u;
-        const uint32_t half = (uint32_t)(NP * KP) * 4u;
+        constexpr int ES = BF ? 2 : 4, KSTEP = BF ? 16 : 8;
+        const int KP = tc_kp(g, BF != 0), NP = tc_np(g);
+        const uint32_t sbo = (uint32_t)KP * 8u * ES;
+        const uint32_t half = (uint32_t)(NP * KP) * ES;
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             if (j > 0) {  // the previous direction's MMAs have read A and B
@@ -210,9 +214,10 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             if (tid == 0) {
                 tc::fence_async_smem();
                 tc::mbar_expect_tx(S.ld_bar, 2u * half);
-                tc::bulk_g2s(S.b_s, P.khat_tc + P.tc_off[g][j], 2u * half, S.ld_bar);
+                tc::bulk_g2s(S.b_s, reinterpret_cast<const char*>(P.khat_tc) + P.tc_off[g][j], 2u * half, S.ld_bar);
             }
-            // X^j[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u], stored as tf32 hi + lo
+            // X^j[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u], stored as hi + lo
+            // (tf32 words, or bf16)
             const float* sj = star + j * STAR_NNZ;
             for (int it = tid; it < d * T; it += NT) {
                 const int ml = it / T, u = it % T;
@@ -226,10 +231,17 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                 for (int n = 0; n < STAR_NNZ; ++n) acc[star_row(n)] = fmaf(sj[n], qv[star_col(n)], acc[star_row(n)]);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
-                    const int at = tc::kmajor_offset(q * T + u, ml, KP);
-                    const float h = tc::to_tf32(acc[q]);
-                    S.ah[at] = h;
-                    S.al[at] = acc[q] - h;
+                    if (BF) {
+                        const int at = tc::kmajor_offset16(q * T + u, ml, KP);
+                        const uint16_t h = tc::bf16_bits(acc[q]);
+                        reinterpret_cast<uint16_t*>(S.ah)[at] = h;
+                        reinterpret_cast<uint16_t*>(S.al)[at] = tc::bf16_bits(acc[q] - tc::bf16_value(h));
+                    } else {
+                        const int at = tc::kmajor_offset(q * T + u, ml, KP);
+                        const float h = tc::to_tf32(acc[q]);
+                        S.ah[at] = h;
+                        S.al[at] = acc[q] - h;
+                    }
                 }
             }
             tc::fence_async_smem();
@@ -239,14 +251,22 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                 if (!tc::mbar_wait(S.ld_bar, S.lph)) *S.abort = 1;
                 S.lph ^= 1;
                 tc::fence_after_sync();
-                const uint32_t id = tc::idesc_tf32(128, NP);
+                const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
 #pragma unroll 1
-                for (int kk = 0; kk < KP / 8; ++kk) {
-                    const uint32_t ko = (uint32_t)kk * 256u;  // 8 tf32 = two core matrices, 128 B apart
-                    tc::mma_tf32(S.tmem, tc::smem_desc(S.al_s + ko, sbo), tc::smem_desc(S.b_s + ko, sbo), id,
-                                 (j | kk) != 0);
-                    tc::mma_tf32(S.tmem, tc::smem_desc(S.ah_s + ko, sbo), tc::smem_desc(S.b_s + half + ko, sbo), id, 1u);
-                    tc::mma_tf32(S.tmem, tc::smem_desc(S.ah_s + ko, sbo), tc::smem_desc(S.b_s + ko, sbo), id, 1u);
+                for (int kk = 0; kk < KP / KSTEP; ++kk) {
+                    // one K step = two core matrices along K, 128 B apart
+                    const uint32_t ko = (uint32_t)kk * 256u;
+                    const uint64_t a_lo = tc::smem_desc(S.al_s + ko, sbo), a_hi = tc::smem_desc(S.ah_s + ko, sbo);
+                    const uint64_t b_hi = tc::smem_desc(S.b_s + ko, sbo), b_lo = tc::smem_desc(S.b_s + half + ko, sbo);
+                    if (BF) {
+                        tc::mma_bf16(S.tmem, a_lo, b_hi, id, (j | kk) != 0);
+                        tc::mma_bf16(S.tmem, a_hi, b_lo, id, 1u);
+                        tc::mma_bf16(S.tmem, a_hi, b_hi, id, 1u);
+                    } else {
+                        tc::mma_tf32(S.tmem, a_lo, b_hi, id, (j | kk) != 0);
+                        tc::mma_tf32(S.tmem, a_hi, b_lo, id, 1u);
+                        tc::mma_tf32(S.tmem, a_hi, b_hi, id, 1u);
+                    }
                 }
                 tc::mma_commit(S.mma_bar);
             }
@@ -425,9 +445,9 @@ __device__ void stash_sweep(float* dst, float* W, const double* q0) {
     }
 }
 
-template <int N, int REF, int NT_>
+template <int N, int REF, int NT_, int BF>
 __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixed_kernel(const K2Params P) {
-    using S = K2Shape<N, REF, NT_>;
+    using S = K2Shape<N, REF, NT_, BF>;
     constexpr int B = S::B, T = S::T, NT = S::NT, QBT = S::QBT, QS = S::QS;
     extern __shared__ __align__(1024) float smf[];
     float* W = smf + S::OFF_W;
@@ -509,7 +529,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             for (int u = 0; u < T; ++u) row[u] = (float)((2 * u + 1) * ((u & 1) ? -1 : 1)) * v;
         }
         __syncthreads();
-        if (!alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
+        if (!alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
         if (REF >= 1) {
             stash_sweep<N, REF, NT_>(Q1, W, q0);
             if (REF == 2)
@@ -521,7 +541,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         for (int sweep = 1; sweep <= REF && ok; ++sweep) {
             residual<N, REF, NT_>(W, Q1, D1, stab, zi, e_dw, g_dw, Yall, P);
             __syncthreads();
-            ok = alg3_sweep_tc<N, NT>(W, sh, zuf, zin, g_dw.x, P, tcs);
+            ok = alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs);
             if (ok && REF == 2 && sweep == 1) {
                 stash_sweep<N, REF, NT_>(D1, W, q0);
                 __syncthreads();
@@ -568,10 +588,10 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     if (tid < 32) tc::tmem_dealloc(tcs.tmem, S::TMEM_COLS);
 }
 
-template <int N, int REF, int NT_>
+template <int N, int REF, int NT_, int BF>
 int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, const double* q0, const double* econst,
               double* qt, double* iout, void* stream) {
-    using S = K2Shape<N, REF, NT_>;
+    using S = K2Shape<N, REF, NT_, BF>;
     K2Params P;
     P.elems = elems;
     P.q0 = q0;
@@ -599,21 +619,21 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     size_t smem = sizeof(float) * S::SMEM_FLOATS;
     const size_t floor_smem = (size_t)sm_smem / (512 / S::TMEM_COLS + 1) + 64;
     if (smem + (size_t)reserved < floor_smem) smem = floor_smem - (size_t)reserved;
-    err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    stp_mixed_kernel<N, REF, NT_><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
+    stp_mixed_kernel<N, REF, NT_, BF><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
     return (int)cudaGetLastError();
 }
 
-template <int N, int NT_>
+template <int N, int NT_, int BF>
 int launch_nv(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
               const double* econst, double* qt, double* iout, void* stream) {
     switch (refine) {
-        case 0: return launch_nr<N, 0, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 1: return launch_nr<N, 1, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_nr<N, 2, NT_>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 0: return launch_nr<N, 0, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_nr<N, 1, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 2: return launch_nr<N, 2, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -621,9 +641,11 @@ int launch_nv(const MixedReference& ref, int refine, const int32_t* elems, int64
 template <int N>
 int launch_n(const MixedReference& ref, int refine, int variant, const int32_t* elems, int64_t count,
              const double* q0, const double* econst, double* qt, double* iout, void* stream) {
+    // the bf16 form is built for the default CTA size only
+    if (ref.bf16) return launch_nv<N, K2Sizes<N>::NT0, 1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
     if (variant == 1)
-        return launch_nv<N, K2Sizes<N>::NT1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-    return launch_nv<N, K2Sizes<N>::NT0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        return launch_nv<N, K2Sizes<N>::NT1, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+    return launch_nv<N, K2Sizes<N>::NT0, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
 }
 
 }  // namespace

@@ -24,6 +24,12 @@ __host__ __device__ constexpr int kmajor_offset(int r, int k, int KP) {
     return (r >> 3) * (KP * 8) + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
 }
 
+// element offset of (r, k) in a K-major no-swizzle tile of KP bf16 columns
+// (core matrices of 8 rows x 8 elements)
+__host__ __device__ constexpr int kmajor_offset16(int r, int k, int KP) {
+    return (r >> 3) * (KP * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
 // shared-memory matrix descriptor: start, LBO = 128 B (K direction), SBO
 // (8-row direction), descriptor version 1, no swizzle
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo_bytes) {
@@ -37,6 +43,32 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo_bytes)
 // instruction descriptor of kind::tf32: D binary32, A and B tf32, both K-major
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// instruction descriptor of kind::f16 with bf16 A and B, D binary32, K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// binary32 -> bf16 bits, nearest even (finite inputs), and back
+__host__ __device__ inline uint16_t bf16_bits(float x) {
+    uint32_t b;
+#ifdef __CUDA_ARCH__
+    b = __float_as_uint(x);
+#else
+    __builtin_memcpy(&b, &x, 4);
+#endif
+    return (uint16_t)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);
+}
+__host__ __device__ inline float bf16_value(uint16_t h) {
+    const uint32_t b = (uint32_t)h << 16;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float x;
+    __builtin_memcpy(&x, &b, 4);
+    return x;
+#endif
 }
 
 // round a binary32 value to tf32 (nearest, ties away from zero: the
@@ -102,6 +134,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, one instruction (M x N x 16 for bf16)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }

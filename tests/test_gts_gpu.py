@@ -102,7 +102,7 @@ def _graded(periodic_x):
                                 tags={"x-": 1, "x+": 2})
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_lts_three_clusters_run(L, precision):
     """Clustered LTS with 3 rate-2 clusters on a graded mesh (free surface at
     x = 0, absorbing at x = 1.6, periodic in y and z), viscous material, a

@@ -126,3 +126,42 @@ def test_cta_size_variants_agree(L, N, sweeps):
         finally:
             L.poro_destroy(ctx)
     np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("N,n", [(3, 17), (4, 9), (5, 7), (6, 5)])
+def test_bf16x3_refined_matches_oracle(L, N, n):
+    """The bf16 split-product form reaches the 1e-10 goal with one refinement
+    sweep (its default) and with two."""
+    d = population(n, N, seed=31 + N)
+    res = {}
+    for sweeps in (1, 2):
+        ctx = L.poro_create(0, N, L.PORO_BF16X3_REFINE)
+        try:
+            L.poro_set_refinement(ctx, sweeps)
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+            L.poro_set_dofs(ctx, d["Q0"])
+            L.poro_predict(ctx)
+            res[sweeps] = L.poro_get_predictor(ctx, 0, n)
+        finally:
+            L.poro_destroy(ctx)
+    errs = {k: max(rel_l2(v[i], oracle_predictor(d, i)) for i in range(n)) for k, v in res.items()}
+    print(f"N={N} bf16x3 max rel error: 1 sweep {errs[1]:.2e}, 2 sweeps {errs[2]:.2e}")
+    assert errs[1] <= TOL_MIXED and errs[2] <= TOL_MIXED
+
+
+def test_bf16x3_unrefined_is_low_precision(L):
+    """Without refinement the bf16 form is far from 1e-10 (so the tolerance
+    above tests the refinement)."""
+    N, n = 4, 9
+    d = population(n, N, seed=77)
+    ctx = L.poro_create(0, N, L.PORO_BF16X3_REFINE)
+    try:
+        L.poro_set_refinement(ctx, 0)
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"])
+        L.poro_predict(ctx)
+        qt = L.poro_get_predictor(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+    err = max(rel_l2(qt[i], oracle_predictor(d, i)) for i in range(n))
+    assert 1e-9 < err < 1e-2
