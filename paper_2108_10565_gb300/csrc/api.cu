@@ -359,8 +359,10 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
         // Residual CSR of Khat^j (all rows): every row l of every Khat^j is an
         // integer row over a common denominator d (the reference matrices are
         // rational with small denominators), so an entry is packed as
-        // (numerator << 7) | column, exact in binary32, and the row carries
-        // 1/d as a double-binary32 pair.
+        // (numerator << 7) | column and the row carries 1/d as a
+        // double-binary32 pair.  The kernel multiplies the numerators with
+        // 21-bit fixed-point values and sums in 64-bit integers, exact while a
+        // row's sum of |numerators| stays below 2^22 (3.6e6 at N = 6).
         const int B = c->B;
         std::vector<float> zf(c->ref.zinv.begin(), c->ref.zinv.end());
         std::vector<int32_t> rrow, rint;
@@ -384,11 +386,13 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
                         break;
                     }
                 }
+                int64_t abs_sum = 0;  // the residual's 64-bit integer sums need sum |c| < 2^22
                 for (int m = 0; m < B && rerr.empty(); ++m) {
                     if (row[m] == 0.0) continue;
                     const double cv = row[m] * (double)d;
                     const int64_t ci = std::llround(cv);
-                    if (std::fabs(cv - (double)ci) > 1e-6 || std::llabs(ci) >= (1 << 23)) {
+                    abs_sum += std::llabs(ci);
+                    if (std::fabs(cv - (double)ci) > 1e-6 || std::llabs(ci) >= (1 << 23) || abs_sum >= (1 << 22)) {
                         rerr = "Khat numerator out of range";
                         break;
                     }

@@ -116,4 +116,39 @@ __device__ __forceinline__ float2 dw_add(float2 a, float2 b) {
     return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
+// ------------------------------------------------------- fixed-point words
+// 2^k as binary32, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// exact binary32 value of an integer v in [-2^22, 2^22]: v is added to the
+// significand of 1.5 * 2^23 (unit last place 1; at v = 2^22 the pattern
+// carries into the exponent of 2^24, still the right value), then that
+// constant is subtracted (exact by Sterbenz's lemma)
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+
+// nearest integer to x * f for |x * f| < 2^22 and f a power of two: the
+// exact product is rounded to the unit last place of 1.5 * 2^23 (a sum that
+// rounds up to 2^24 gives the pattern of 2^24, i.e. v = 2^22)
+__device__ __forceinline__ int round_to_int(float x, float f) {
+    return __float_as_int(__fmaf_rn(x, f, 12582912.0f)) - 0x4B400000;
+}
+
+// exact double-word (h, l) of an integer |v| <= 2^44: v = a 2^22 + b with
+// |a| <= 2^22 and b in [0, 2^22), both exact in binary32, joined by Fast2Sum
+// (|a 2^22| > b unless a = 0)
+__device__ __forceinline__ void int_to_dw(long long v, float& h, float& l) {
+    const float fa = __fmul_rn(small_int_to_float((int)(v >> 22)), 4194304.0f);
+    const float fb = small_int_to_float((int)(v & 0x3FFFFF));
+    h = __fadd_rn(fa, fb);
+    l = __fsub_rn(fb, __fsub_rn(h, fa));
+}
+__device__ __forceinline__ void int_to_dw(int v, float& h, float& l) {
+    const float fa = __fmul_rn(small_int_to_float(v >> 22), 4194304.0f);
+    const float fb = small_int_to_float(v & 0x3FFFFF);
+    h = __fadd_rn(fa, fb);
+    l = __fsub_rn(fb, __fsub_rn(h, fa));
+}
+
 }  // namespace poro

@@ -128,7 +128,8 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int OFF_ZI = OFF_ZUF + 8 * T_;
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
     static constexpr int OFF_STAB = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // float4 [13][STAR_SLOTS]
-    static constexpr int OFF_BAR = OFF_STAB + 4 * NQ * STAR_SLOTS;  // 2 mbarriers, TMEM slot, abort flag
+    static constexpr int OFF_SC = OFF_STAB + 4 * NQ * STAR_SLOTS;  // ints: Q1 exponents [16], D1 exponents [16]
+    static constexpr int OFF_BAR = OFF_SC + 32;  // 2 mbarriers, TMEM slot, abort flag, non-finite flag
     static constexpr int SMEM_FLOATS = OFF_BAR + 8;
     static constexpr int TMEM_COLS = tc_np(N) <= 32 ? 32 : (tc_np(N) <= 64 ? 64 : 128);
     static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
@@ -315,11 +316,12 @@ __host__ __device__ constexpr int r2_slot(int T, int s) {
                         : (SXY + (s - 10 * T) / T) * T + (s - 10 * T) % T;
 }
 
-// Q1 / D1 layout of the residual: mode-major, Q[m * Q1S + p * T + u], so the
-// (q, u) lanes of one mode are consecutive words
+// Q1 / D1 of the residual: fixed-point integers, mode-major,
+// Q[m * Q1S + p * T + u] (the (q, u) lanes of one mode are consecutive
+// words); the value is Q * 2^-sq[p] with |Q| <= 2^22
 template <int N, int REF, int NT_>
-__device__ void residual(float* W, const float* Q1, const float* D1, const float4* stab, const float* zi,
-                         float2 e_dw, float2 g_dw, float2* Yall, const K2Params& P) {
+__device__ void residual(float* W, const int* Q1, const int* D1, const int* sq, const int* sd, const float4* stab,
+                         const int* zneg, float2 e_dw, float2 g_dw, float2* Yall, const K2Params& P) {
     using S = K2Shape<N, REF, NT_>;
     constexpr int B = S::B, T = S::T, PT = S::PT, PUL = S::PUL, QS = S::QS, Q1S = S::Q1S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -328,37 +330,44 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
         const int l = __ldg(P.res_order + S::NW + 1 + i);  // this warp's rows (balanced lists)
-        // R1: Y^j[q, u] = (1 / d_jl) sum_m c_jlm Q[q, m, u] with integer
-        // numerators c (exact in binary32, so every product is an exact
-        // FMA-based pair); each entry is loaded one step ahead
+        // R1: Y^j[q, u] = (1 / d_jl) sum_m c_jlm Q[q, m, u]: integer numerators
+        // times integer Q, summed exactly in 64 bits (sum_m |c_jlm| < 2^22 and
+        // |Q| <= 2^22, so |sum| <= 2^44)
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
-            float yh[PUL], yl[PUL];
+            long long ya[PUL], yd[PUL];
 #pragma unroll
-            for (int k = 0; k < PUL; ++k) yh[k] = yl[k] = 0.f;
+            for (int k = 0; k < PUL; ++k) ya[k] = yd[k] = 0;
             const int32_t* cr = c_res + res_base(N);
             const int32_t* ce = cr + 3 * (B + 1);
             const int n0 = cr[j * (B + 1) + l], n1 = cr[j * (B + 1) + l + 1];
-            int nx = n0 < n1 ? ce[n0] : 0;
+#pragma unroll 4
             for (int n = n0; n < n1; ++n) {
-                const int kv = nx;
-                if (n + 1 < n1) nx = ce[n + 1];
-                const float cv = (float)(kv >> 7);
+                const int kv = ce[n];
+                const long long cv = (long long)(kv >> 7);
                 const int mo = (kv & 127) * Q1S + lane;
 #pragma unroll
                 for (int k = 0; k < PUL; ++k) {
-                    if (REF == 2)
-                        dw_mac_x2(yh[k], yl[k], cv, Q1[mo + 32 * k], D1[mo + 32 * k]);
-                    else
-                        dw_mac_x(yh[k], yl[k], cv, Q1[mo + 32 * k]);
+                    ya[k] += cv * Q1[mo + 32 * k];
+                    if (REF == 2) yd[k] += cv * D1[mo + 32 * k];
                 }
             }
             const float2 inv = __ldg(P.res_inv + j * B + l);
 #pragma unroll
             for (int k = 0; k < PUL; ++k) {
                 const int pu = lane + 32 * k;
+                const int q = pu < PT ? pu / T : 0;
+                float yh, yl;
+                int_to_dw(ya[k], yh, yl);
+                const float f = pow2f(-sq[q]);
+                float2 y = make_float2(__fmul_rn(yh, f), __fmul_rn(yl, f));
+                if (REF == 2) {
+                    int_to_dw(yd[k], yh, yl);
+                    const float fd = pow2f(-sd[q]);
+                    y = dw_add(y, make_float2(__fmul_rn(yh, fd), __fmul_rn(yl, fd)));
+                }
                 float h = 0.f, lo = 0.f;
-                dw_mac(h, lo, inv.x, inv.y, yh[k], yl[k]);
+                dw_mac(h, lo, inv.x, inv.y, y.x, y.y);
                 if (pu < PT) Y[j * PT + pu] = make_float2(h, lo);
             }
         }
@@ -383,25 +392,41 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
             if (pu >= 0) {
                 const int p = pu / T, u = pu % T;
                 const int bq = l * Q1S + p * T;
-                float h = 0.f, lo = 0.f;
-                const float sw = (float)((2 * u + 1) * ((u & 1) ? -1 : 1));
-                dw_mac_x2(h, lo, sw, bv[k].x, bv[k].y);
-                // - sum_s Z_us Q[p, l, s]   (Z entries are exact small integers)
+                // - sum_s Z_us Q[p, l, s]: Z's entries are small integers, so the
+                // sum is an exact integer (|sum| < 2^29)
+                int za = 0, zd = 0;
 #pragma unroll
                 for (int s = 0; s < T; ++s) {
-                    if (REF == 2)
-                        dw_mac_x2(h, lo, -zi[u * T + s], Q1[bq + s], D1[bq + s]);
-                    else
-                        dw_mac_x(h, lo, -zi[u * T + s], Q1[bq + s]);
+                    za += zneg[u * T + s] * Q1[bq + s];
+                    if (REF == 2) zd += zneg[u * T + s] * D1[bq + s];
                 }
+                float h, lo;
+                {
+                    float zh, zl;
+                    int_to_dw(za, zh, zl);
+                    const float f = pow2f(-sq[p]);
+                    h = __fmul_rn(zh, f);
+                    lo = __fmul_rn(zl, f);
+                    if (REF == 2) {
+                        int_to_dw(zd, zh, zl);
+                        const float fd = pow2f(-sd[p]);
+                        const float2 z2 = dw_add(make_float2(h, lo), make_float2(__fmul_rn(zh, fd), __fmul_rn(zl, fd)));
+                        h = z2.x;
+                        lo = z2.y;
+                    }
+                }
+                const float sw = (float)((2 * u + 1) * ((u & 1) ? -1 : 1));
+                dw_mac_x2(h, lo, sw, bv[k].x, bv[k].y);
                 // + E*_pp Q[p, l, u] (u_f rows) and + G Q[u_f, l, u] (u rows)
                 if (p >= QUF || (p >= QU && p <= QW)) {
-                    const int src = p >= QUF ? bq + u : l * Q1S + (p + 4) * T + u;
+                    const int ps = p >= QUF ? p : p + (QUF - QU);
+                    const int src = l * Q1S + ps * T + u;
                     const float2 c = p >= QUF ? e_dw : g_dw;
+                    const float qv = __fmul_rn(small_int_to_float(Q1[src]), pow2f(-sq[ps]));
                     if (REF == 2)
-                        dw_mac(h, lo, c.x, c.y, Q1[src], D1[src]);
+                        dw_mac(h, lo, c.x, c.y, qv, __fmul_rn(small_int_to_float(D1[src]), pow2f(-sd[ps])));
                     else
-                        dw_mac1(h, lo, c.x, c.y, Q1[src]);
+                        dw_mac1(h, lo, c.x, c.y, qv);
                 }
                 // - sum_j sum_q A^{j*}_pq Y^j[q, u]: row p's entries of each
                 // direction, padded to the slot width
@@ -427,18 +452,37 @@ __device__ void residual(float* W, const float* Q1, const float* D1, const float
     tc::fence_async_smem();
 }
 
-// Save the sweep result W into dst (mode-major layout) and put the
-// double-binary32 split of b0 = q0 into W[p, l, 0..1] for the residual
+// Save the sweep result W into dst as fixed-point integers and put the
+// double-binary32 split of b0 = q0 into W[p, l, 0..1] for the residual.
+// Quantity p is rounded to the grid 2^-sc[p] with sc[p] chosen from
+// max_{l,u} |W[p, l, u]| so that every integer has |v| <= 2^22: the residual
+// then takes exact integer products, and the refinement corrects the rounding
+// (~2^-23 of the quantity's largest entry) like any other error of the sweep.
+// A non-finite value raises *nonfinite, which turns the element's output into
+// NaN.
 template <int N, int REF, int NT_>
-__device__ void stash_sweep(float* dst, float* W, const double* q0) {
+__device__ void stash_sweep(int* dst, int* sc, int* nonfinite, float* W, const double* q0) {
     using S = K2Shape<N, REF, NT_>;
     constexpr int B = S::B, T = S::T, QS = S::QS, Q1S = S::Q1S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int p = warp; p < NQ; p += S::NW) {
+        uint32_t m = 0;
+        for (int i = lane; i < B * T; i += 32) m = max(m, __float_as_uint(W[p * QS + i]) & 0x7FFFFFFFu);
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) {
+            const int e = (int)(m >> 23) - 127;  // max in [2^e, 2^(e+1)), so max 2^sc < 2^22
+            sc[p] = min(21 - e, 126);
+            if (e == 128) *nonfinite = 1;
+        }
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < NQ * B; i += NT_) {
         const int p = i / B, l = i - (i / B) * B;
         float* w = W + p * QS + l * T;
-        float* d = dst + l * Q1S + p * T;
+        int* d = dst + l * Q1S + p * T;
+        const float f = pow2f(sc[p]);
 #pragma unroll
-        for (int u = 0; u < T; ++u) d[u] = w[u];
+        for (int u = 0; u < T; ++u) d[u] = round_to_int(w[u], f);
         const float2 b = dw_split(q0[i]);
         w[0] = b.x;
         w[1] = b.y;
@@ -451,19 +495,22 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     constexpr int B = S::B, T = S::T, NT = S::NT, QBT = S::QBT, QS = S::QS;
     extern __shared__ __align__(1024) float smf[];
     float* W = smf + S::OFF_W;
-    float* Q1 = smf + S::OFF_Q1;
-    float* D1 = smf + S::OFF_D1;
+    int* Q1 = reinterpret_cast<int*>(smf + S::OFF_Q1);
+    int* D1 = reinterpret_cast<int*>(smf + S::OFF_D1);
+    int* sq = reinterpret_cast<int*>(smf + S::OFF_SC);
+    int* sd = sq + 16;
     float2* Yall = reinterpret_cast<float2*>(smf + S::OFF_XY);
     float* sh = smf + S::OFF_SH;
     float* sl = smf + S::OFF_SL;
     float* zin = smf + S::OFF_ZIN;
     float* zuf = smf + S::OFF_ZUF;
-    float* zi = smf + S::OFF_ZI;
+    int* zneg = reinterpret_cast<int*>(smf + S::OFF_ZI);
     int* tab = reinterpret_cast<int*>(smf + S::OFF_TAB);
     float4* stab = reinterpret_cast<float4*>(smf + S::OFF_STAB);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::OFF_BAR);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 4);
     volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 5);
+    int* nonfinite = reinterpret_cast<int*>(smf + S::OFF_BAR + 6);
     const int tid = threadIdx.x;
 
     TcState tcs;
@@ -482,7 +529,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     for (int i = tid; i < T * T; i += NT) {
         const int u = i / T, s = i % T;
         zin[8 * u + s] = P.zinv[i];
-        zi[i] = (float)((2 * u + 1) * ((u > s && ((u - s) & 1)) ? -1 : 1));  // Z = S^{-1}(W - K^tau)
+        zneg[i] = -(2 * u + 1) * ((u > s && ((u - s) & 1)) ? -1 : 1);  // -Z, Z = S^{-1}(W - K^tau)
     }
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
     if (tid == 0) {
@@ -502,6 +549,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
         const double* q0 = P.q0 + e * (int64_t)(NQ * B);
         const double* ec = P.econst + e * (int64_t)P.stride;
+        if (tid == 0) *nonfinite = 0;  // read after the barriers below
         for (int i = tid; i < 3 * STAR_NNZ; i += NT) {
             const float2 v = dw_split(ec[i]);
             sh[i] = v.x;
@@ -531,19 +579,21 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         __syncthreads();
         if (!alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
         if (REF >= 1) {
-            stash_sweep<N, REF, NT_>(Q1, W, q0);
-            if (REF == 2)
-                for (int i = tid; i < S::Q1SIZE; i += NT) D1[i] = 0.f;
+            stash_sweep<N, REF, NT_>(Q1, sq, nonfinite, W, q0);
+            if (REF == 2) {
+                for (int i = tid; i < S::Q1SIZE; i += NT) D1[i] = 0;
+                if (tid < NQ) sd[tid] = 0;
+            }
             __syncthreads();
         }
         bool ok = true;
 #pragma unroll 1
         for (int sweep = 1; sweep <= REF && ok; ++sweep) {
-            residual<N, REF, NT_>(W, Q1, D1, stab, zi, e_dw, g_dw, Yall, P);
+            residual<N, REF, NT_>(W, Q1, D1, sq, sd, stab, zneg, e_dw, g_dw, Yall, P);
             __syncthreads();
             ok = alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs);
             if (ok && REF == 2 && sweep == 1) {
-                stash_sweep<N, REF, NT_>(D1, W, q0);
+                stash_sweep<N, REF, NT_>(D1, sd, nonfinite, W, q0);
                 __syncthreads();
             }
         }
@@ -556,8 +606,9 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             for (int i = tid; i < NQ * B; i += NT) {
                 const int p = i / B, l = i - (i / B) * B;
                 const float* w = W + p * QS + l * T;
-                const float* q1 = Q1 + l * S::Q1S + p * T;
-                const float* d1 = D1 + l * S::Q1S + p * T;
+                const int* q1 = Q1 + l * S::Q1S + p * T;
+                const int* d1 = D1 + l * S::Q1S + p * T;
+                const float fq = REF >= 1 ? pow2f(-sq[p]) : 0.f, fd = REF == 2 ? pow2f(-sd[p]) : 0.f;
 #pragma unroll
                 for (int u = 0; u < T; ++u) {
                     double v;
@@ -565,15 +616,16 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
                         v = __longlong_as_double((long long)f2d_bits(w[u]));
                     } else {
                         float sv, ev;
-                        two_sum(q1[u], w[u], sv, ev);
+                        two_sum(__fmul_rn(small_int_to_float(q1[u]), fq), w[u], sv, ev);
                         if (REF == 2) {
                             float s2, e2;
-                            two_sum(sv, d1[u], s2, e2);
+                            two_sum(sv, __fmul_rn(small_int_to_float(d1[u]), fd), s2, e2);
                             ev = __fadd_rn(ev, e2);
                             sv = __fadd_rn(s2, ev);  // renormalise: |ev| <= ulp(sv) / 2
                             ev = __fsub_rn(ev, __fsub_rn(sv, s2));
                         }
                         v = pair_to_double(sv, ev);
+                        if (*nonfinite) v = __longlong_as_double(0x7FF8000000000000LL);
                     }
                     if (qo) qo[(int64_t)i * T + u] = v;
                     if (io && u == 0) io[i] = dt * v;
