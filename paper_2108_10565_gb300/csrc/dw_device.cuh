@@ -67,11 +67,12 @@ __device__ __forceinline__ void dw_mac_x2(float& h, float& l, float a, float bh,
 // so the result is assembled from its binary32 words by bit manipulation.
 
 // exact binary64 bit pattern of a binary32 value (binary32 subnormals,
-// |x| < 1.2e-38, become signed zero)
+// |x| < 1.2e-38, become signed zero; infinities and NaNs stay so)
 __device__ __forceinline__ unsigned long long f2d_bits(float x) {
     const uint32_t b = __float_as_uint(x);
     const uint32_t ex = (b >> 23) & 0xFFu;
-    const uint32_t hi = ex ? ((b & 0x80000000u) | ((ex + 896u) << 20) | ((b >> 3) & 0xFFFFFu)) : (b & 0x80000000u);
+    const uint32_t dex = ex == 0xFFu ? 0x7FFu : ex + 896u;
+    const uint32_t hi = ex ? ((b & 0x80000000u) | (dex << 20) | ((b >> 3) & 0xFFFFFu)) : (b & 0x80000000u);
     const uint32_t lo = ex ? (b << 29) : 0u;
     return ((unsigned long long)hi << 32) | lo;
 }
@@ -84,7 +85,7 @@ __device__ __forceinline__ double pair_to_double(float s, float e) {
     unsigned long long d = f2d_bits(s);
     const uint32_t bs = __float_as_uint(s), be = __float_as_uint(e);
     const int exs = (int)((bs >> 23) & 0xFFu), exe = (int)((be >> 23) & 0xFFu);
-    if (exs != 0 && exe != 0) {
+    if (exs != 0 && exs != 0xFF && exe != 0) {
         const unsigned long long me = (unsigned long long)((be & 0x7FFFFFu) | 0x800000u);
         const bool opposite = ((bs ^ be) >> 31) != 0;
         // e in units of 2^(exp(s) - 52); one binade lower (half the unit) when s

@@ -111,7 +111,11 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int SBOMAX = KPM * 8 * ES / 4;
     static constexpr int AH = (A::PT + 7) / 8 * SBOMAX;
     static constexpr int BIMG = 2 * tc_np(N) * KPM * ES / 4;
-    static constexpr int TC_SIZE = MAX2(2 * AH + BIMG, AH + 16 * SBOMAX);
+    // at least one A tile pair and one Khat image; the bf16 form gets the
+    // room of the tf32 form, where the Khat images of all three directions fit
+    // beside one A pair at every degree (tf32: up to degree 4)
+    static constexpr int TC1 = MAX2(2 * AH + BIMG, AH + 16 * SBOMAX);
+    static constexpr int TC_SIZE = BF ? MAX2(TC1, 2 * AH + 3 * BIMG) : TC1;
     // shared layout in floats; the tensor-core tiles of the sweeps and the
     // per-warp Y buffers of the residual share the first region
     static constexpr int OFF_XY = 0;
@@ -129,8 +133,8 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
     static constexpr int OFF_STAB = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // float4 [13][STAR_SLOTS]
     static constexpr int OFF_SC = OFF_STAB + 4 * NQ * STAR_SLOTS;  // ints: Q1 exponents [16], D1 exponents [16]
-    static constexpr int OFF_BAR = OFF_SC + 32;  // 2 mbarriers, TMEM slot, abort flag, non-finite flag
-    static constexpr int SMEM_FLOATS = OFF_BAR + 8;
+    static constexpr int OFF_BAR = OFF_SC + 32;  // 5 mbarriers, TMEM slot, abort, non-finite and dirty flags
+    static constexpr int SMEM_FLOATS = OFF_BAR + 14;
     static constexpr int TMEM_COLS = tc_np(N) <= 32 ? 32 : (tc_np(N) <= 64 ? 64 : 128);
     static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
     static_assert(NW == 2 || NW == 4 || NW == 8, "2, 4 or 8 warps");
@@ -162,14 +166,90 @@ __device__ __forceinline__ void solve_row8(float* row, const float* Zi) {
 
 // Tensor-core state of one CTA (shared addresses, barrier phases)
 struct TcState {
-    float* ah;  // A tiles (tf32 words, or bf16 values in the same bytes)
-    float* al;
-    uint32_t ah_s, al_s, b_s;
-    uint32_t mma_bar, ld_bar;
+    float* xy;      // operand region: A tiles (tf32 words, or bf16 values in the same bytes), then Khat images
+    uint32_t xy_s;  // its shared address
+    int xy_floats;  // its size
+    uint32_t bar_s;     // mbarriers: MMAs done reading A buffer 0, 1; Khat image in slot 0, 1, 2
     uint32_t tmem;
-    uint32_t mph, lph;
+    uint32_t mph, lph;  // phase parity of each barrier (bit b for buffer or slot b)
     volatile int* abort;
 };
+
+// Operand layout of degree block g in the region (floats): nA A buffers (hi
+// tile, lo tile), then nB Khat image slots (hi image, lo image).  Direction j
+// uses A buffer j % nA and slot j % nB.  An MMA reads 16 row groups of an A
+// tile; the rows past 13 T feed accumulator rows that are never read and
+// stay inside the region.  As many slots as fit (all three directions' images
+// can then be in flight before the block starts), then a second A buffer if
+// it fits (the star products of direction j overlap the MMAs of j - 1).
+struct TcLayout {
+    int KP, NP, ahf, bif, nA, nB;
+    uint32_t sbo, half;  // bytes: 8-row group stride; one Khat image (hi or lo)
+};
+template <int PT, int BF>
+__device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats) {
+    constexpr int ES = BF ? 2 : 4;
+    TcLayout L;
+    L.KP = tc_kp(g, BF != 0);
+    L.NP = tc_np(g);
+    L.sbo = (uint32_t)L.KP * 8u * ES;
+    L.half = (uint32_t)(L.NP * L.KP) * ES;
+    L.ahf = (PT + 7) / 8 * (int)(L.sbo / 4);
+    L.bif = (int)(2u * L.half / 4u);
+    const int over = 16 * (int)(L.sbo / 4) - L.ahf;
+    auto fits = [&](int na, int nb) { return 2 * na * L.ahf + nb * L.bif <= xy_floats && (2 * na - 1) * L.ahf + 16 * (int)(L.sbo / 4) <= xy_floats && over >= 0; };
+    L.nB = fits(1, 3) ? 3 : (fits(1, 2) ? 2 : 1);
+    // direction j >= nB loads once the MMAs of j - nB are done, known at step
+    // j - nB + nA: that is no later than step j only if nA <= nB
+    L.nA = (L.nB >= 2 && fits(2, L.nB)) ? 2 : 1;
+    return L;
+}
+
+// bulk copy of direction j's Khat image of block g into its slot (one thread)
+template <int PT, int BF>
+__device__ __forceinline__ void tc_load_khat(const TcState& S, const TcLayout& L, const K2Params& P, int g, int j) {
+    const int slot = j % L.nB;
+    const uint32_t bar = S.bar_s + 16u + 8u * (uint32_t)slot;
+    const uint32_t dst = S.xy_s + 4u * (uint32_t)(2 * L.nA * L.ahf + slot * L.bif);
+    tc::fence_async_smem();
+    tc::mbar_expect_tx(bar, 2u * L.half);
+    tc::bulk_g2s(dst, reinterpret_cast<const char*>(P.khat_tc) + P.tc_off[g][j], 2u * L.half, bar);
+}
+
+// star products of one item (ml, u) of block g (modes o + ml) for direction
+// j's 54 coefficients: acc[p] = sum_q A^{j*}_pq Q[q, o+ml, u]
+template <int T, int QS>
+__device__ __forceinline__ void star_item(const float* bq, const float* sj, int o, int it, float acc[NQ]) {
+    const int ml = it / T, u = it % T;
+    float qv[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        qv[q] = bq[q * QS + (o + ml) * T + u];
+        acc[q] = 0.f;
+    }
+#pragma unroll
+    for (int n = 0; n < STAR_NNZ; ++n) acc[star_row(n)] = fmaf(sj[n], qv[star_col(n)], acc[star_row(n)]);
+}
+
+// store one item's 13 values as hi + lo (tf32 words, or bf16) into the A tiles
+template <int T, int BF>
+__device__ __forceinline__ void store_item(float* ah, float* al, int it, int KP, const float acc[NQ]) {
+    const int ml = it / T, u = it % T;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (BF) {
+            const int at = tc::kmajor_offset16(q * T + u, ml, KP);
+            const uint16_t h = tc::bf16_bits(acc[q]);
+            reinterpret_cast<uint16_t*>(ah)[at] = h;
+            reinterpret_cast<uint16_t*>(al)[at] = tc::bf16_bits(acc[q] - tc::bf16_value(h));
+        } else {
+            const int at = tc::kmajor_offset(q * T + u, ml, KP);
+            const float h = tc::to_tf32(acc[q]);
+            ah[at] = h;
+            al[at] = acc[q] - h;
+        }
+    }
+}
 
 // One binary32 sweep of Algorithm 3 with the Khat products on the tensor
 // cores.  On entry bq holds b, on exit Q.  Returns false (uniformly across the
@@ -180,6 +260,11 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
     using A = Alg3Shape<N>;
     constexpr int T = A::T, QS = A::QS, PT = A::PT, NW = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the first block's Khat images load while its time solves run
+    if (tid == 0 && N >= 1) {
+        const TcLayout L0 = tc_layout<PT, BF>(N, S.xy_floats);
+        for (int j = 0; j < L0.nB; ++j) tc_load_khat<PT, BF>(S, L0, P, N, j);
+    }
 #pragma unroll 1
     for (int g = N; g >= 0; --g) {
         const int o = block_offset(g), d = block_size(g);
@@ -202,78 +287,82 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         }
         __syncthreads();
         if (g == 0) break;
-        constexpr int ES = BF ? 2 : 4, KSTEP = BF ? 16 : 8;
-        const int KP = tc_kp(g, BF != 0), NP = tc_np(g);
-        const uint32_t sbo = (uint32_t)KP * 8u * ES;
-        const uint32_t half = (uint32_t)(NP * KP) * ES;
+        constexpr int KSTEP = BF ? 16 : 8;
+        const TcLayout L = tc_layout<PT, BF>(g, S.xy_floats);
+        const int KP = L.KP, NP = L.NP;
+        const uint32_t sbo = L.sbo, half = L.half;
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
-            if (j > 0) {  // the previous direction's MMAs have read A and B
-                if (!tc::mbar_wait(S.mma_bar, S.mph)) *S.abort = 1;
-                S.mph ^= 1;
+            const int abuf = j % L.nA, slot = j % L.nB;
+            const uint32_t mma_bar = S.bar_s + 8u * (uint32_t)abuf, ld_bar = S.bar_s + 16u + 8u * (uint32_t)slot;
+            if (j >= L.nA) {  // the MMAs of direction j - nA (and all before) are done
+                if (!tc::mbar_wait(mma_bar, (S.mph >> abuf) & 1u)) *S.abort = 1;
+                S.mph ^= 1u << abuf;
+                // their slots are free: load the images not yet in flight
+                if (tid == 0)
+                    for (int k = L.nB; k < 3; ++k)
+                        if (k - L.nB <= j - L.nA && k - L.nB > j - 1 - L.nA) tc_load_khat<PT, BF>(S, L, P, g, k);
             }
-            if (tid == 0) {
-                tc::fence_async_smem();
-                tc::mbar_expect_tx(S.ld_bar, 2u * half);
-                tc::bulk_g2s(S.b_s, reinterpret_cast<const char*>(P.khat_tc) + P.tc_off[g][j], 2u * half, S.ld_bar);
-            }
+            float* ah = S.xy + 2 * abuf * L.ahf;
+            float* al = ah + L.ahf;
+            const uint32_t ah_s = S.xy_s + 4u * (uint32_t)(2 * abuf * L.ahf), al_s = ah_s + 4u * (uint32_t)L.ahf;
+            const uint32_t b_s = S.xy_s + 4u * (uint32_t)(2 * L.nA * L.ahf + slot * L.bif);
             // X^j[p, ml, u] = sum_q A^{j*}_pq Q[q, o+ml, u], stored as hi + lo
             // (tf32 words, or bf16)
             const float* sj = star + j * STAR_NNZ;
             for (int it = tid; it < d * T; it += NT) {
-                const int ml = it / T, u = it % T;
-                float qv[NQ], acc[NQ];
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    qv[q] = bq[q * QS + (o + ml) * T + u];
-                    acc[q] = 0.f;
-                }
-#pragma unroll
-                for (int n = 0; n < STAR_NNZ; ++n) acc[star_row(n)] = fmaf(sj[n], qv[star_col(n)], acc[star_row(n)]);
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    if (BF) {
-                        const int at = tc::kmajor_offset16(q * T + u, ml, KP);
-                        const uint16_t h = tc::bf16_bits(acc[q]);
-                        reinterpret_cast<uint16_t*>(S.ah)[at] = h;
-                        reinterpret_cast<uint16_t*>(S.al)[at] = tc::bf16_bits(acc[q] - tc::bf16_value(h));
-                    } else {
-                        const int at = tc::kmajor_offset(q * T + u, ml, KP);
-                        const float h = tc::to_tf32(acc[q]);
-                        S.ah[at] = h;
-                        S.al[at] = acc[q] - h;
-                    }
-                }
+                float acc[NQ];
+                star_item<T, QS>(bq, sj, o, it, acc);
+                store_item<T, BF>(ah, al, it, KP, acc);
             }
             tc::fence_async_smem();
             __syncthreads();
             if (*S.abort) return false;
             if (tid == 0) {
-                if (!tc::mbar_wait(S.ld_bar, S.lph)) *S.abort = 1;
-                S.lph ^= 1;
+                if (!tc::mbar_wait(ld_bar, (S.lph >> (2 + slot)) & 1u)) *S.abort = 1;
+                S.lph ^= 1u << (2 + slot);
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
-#pragma unroll 1
-                for (int kk = 0; kk < KP / KSTEP; ++kk) {
-                    // one K step = two core matrices along K, 128 B apart
-                    const uint32_t ko = (uint32_t)kk * 256u;
-                    const uint64_t a_lo = tc::smem_desc(S.al_s + ko, sbo), a_hi = tc::smem_desc(S.ah_s + ko, sbo);
-                    const uint64_t b_hi = tc::smem_desc(S.b_s + ko, sbo), b_lo = tc::smem_desc(S.b_s + half + ko, sbo);
-                    if (BF) {
-                        tc::mma_bf16(S.tmem, a_lo, b_hi, id, (j | kk) != 0);
-                        tc::mma_bf16(S.tmem, a_hi, b_lo, id, 1u);
-                        tc::mma_bf16(S.tmem, a_hi, b_hi, id, 1u);
-                    } else {
-                        tc::mma_tf32(S.tmem, a_lo, b_hi, id, (j | kk) != 0);
-                        tc::mma_tf32(S.tmem, a_hi, b_lo, id, 1u);
-                        tc::mma_tf32(S.tmem, a_hi, b_hi, id, 1u);
+                // one K step = two core matrices along K, 256 B further: 16
+                // units of the descriptors' start-address field (no carry,
+                // shared addresses are below 2^18)
+                const uint64_t dal = tc::smem_desc(al_s, sbo), dah = tc::smem_desc(ah_s, sbo);
+                const uint64_t dbh = tc::smem_desc(b_s, sbo), dbl = tc::smem_desc(b_s + half, sbo);
+                const int nk = KP / KSTEP;
+                constexpr int MAXK = tc_kp(N, BF != 0) / KSTEP;
+#pragma unroll
+                for (int kk = 0; kk < MAXK; ++kk) {
+                    if (kk < nk) {
+                        const uint64_t k16 = 16ull * (uint64_t)kk;
+                        if (BF) {
+                            tc::mma_bf16(S.tmem, dal + k16, dbh + k16, id, (j | kk) != 0);
+                            tc::mma_bf16(S.tmem, dah + k16, dbl + k16, id, 1u);
+                            tc::mma_bf16(S.tmem, dah + k16, dbh + k16, id, 1u);
+                        } else {
+                            tc::mma_tf32(S.tmem, dal + k16, dbh + k16, id, (j | kk) != 0);
+                            tc::mma_tf32(S.tmem, dah + k16, dbl + k16, id, 1u);
+                            tc::mma_tf32(S.tmem, dah + k16, dbh + k16, id, 1u);
+                        }
                     }
                 }
-                tc::mma_commit(S.mma_bar);
+                tc::mma_commit(mma_bar);
             }
         }
-        if (!tc::mbar_wait(S.mma_bar, S.mph)) *S.abort = 1;
-        S.mph ^= 1;
+        // wait for the commits not yet waited for (directions 3 - nA .. 2);
+        // the last one covers every MMA of the block
+#pragma unroll 1
+        for (int j = 3 - L.nA; j < 3; ++j) {
+            const int abuf = j % L.nA;
+            if (!tc::mbar_wait(S.bar_s + 8u * (uint32_t)abuf, (S.mph >> abuf) & 1u)) *S.abort = 1;
+            S.mph ^= 1u << abuf;
+        }
+        // the region is free: the next block's Khat images load during this
+        // block's epilogue and the next time solves (issued by lane 0 of warp
+        // 3, whose TMEM lane quarter holds no rows: 13 T <= 96)
+        if (tid == (NW >= 4 ? 96 : 0) && g > 1) {
+            const TcLayout Ln = tc_layout<PT, BF>(g - 1, S.xy_floats);
+            for (int j = 0; j < Ln.nB; ++j) tc_load_khat<PT, BF>(S, Ln, P, g - 1, j);
+        }
         tc::fence_after_sync();
         // b[p, l, u] -= D[(p, u), l]: warp w reads TMEM lanes 32 (w % 4) ...,
         // with 8 warps the two warps of a lane quarter split the columns
@@ -508,19 +597,17 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     int* tab = reinterpret_cast<int*>(smf + S::OFF_TAB);
     float4* stab = reinterpret_cast<float4*>(smf + S::OFF_STAB);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::OFF_BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 4);
-    volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 5);
-    int* nonfinite = reinterpret_cast<int*>(smf + S::OFF_BAR + 6);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 10);
+    volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 11);
+    int* nonfinite = reinterpret_cast<int*>(smf + S::OFF_BAR + 12);
+    int* dirty = reinterpret_cast<int*>(smf + S::OFF_BAR + 13);  // a result was not finite
     const int tid = threadIdx.x;
 
     TcState tcs;
-    tcs.ah = smf + S::OFF_XY;
-    tcs.al = tcs.ah + S::AH;
-    tcs.ah_s = tc::smem_addr(tcs.ah);
-    tcs.al_s = tc::smem_addr(tcs.al);
-    tcs.b_s = tc::smem_addr(tcs.al + S::AH);
-    tcs.mma_bar = tc::smem_addr(bars);
-    tcs.ld_bar = tc::smem_addr(bars + 1);
+    tcs.xy = smf + S::OFF_XY;
+    tcs.xy_s = tc::smem_addr(tcs.xy);
+    tcs.xy_floats = S::XY_SIZE;
+    tcs.bar_s = tc::smem_addr(bars);
     tcs.mph = tcs.lph = 0;
     tcs.abort = abort;
 
@@ -534,8 +621,8 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
     if (tid == 0) {
         *abort = 0;
-        tc::mbar_init(tcs.mma_bar, 1);
-        tc::mbar_init(tcs.ld_bar, 1);
+        *dirty = 0;
+        for (int b = 0; b < 5; ++b) tc::mbar_init(tcs.bar_s + 8u * (uint32_t)b, 1);
         tc::mbar_init_fence();
     }
     if (tid < 32) tc::tmem_alloc(tc::smem_addr(tslot), S::TMEM_COLS);
@@ -603,6 +690,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             double* qo = P.qt ? P.qt + e * (int64_t)QBT : nullptr;
             double* io = P.iout ? P.iout + e * (int64_t)(NQ * B) : nullptr;
             // one (p, l) row of T time modes per thread
+            bool bad = false;
             for (int i = tid; i < NQ * B; i += NT) {
                 const int p = i / B, l = i - (i / B) * B;
                 const float* w = W + p * QS + l * T;
@@ -611,6 +699,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
                 const float fq = REF >= 1 ? pow2f(-sq[p]) : 0.f, fd = REF == 2 ? pow2f(-sd[p]) : 0.f;
 #pragma unroll
                 for (int u = 0; u < T; ++u) {
+                    bad |= (__float_as_uint(w[u]) & 0x7F800000u) == 0x7F800000u;
                     double v;
                     if (REF == 0) {
                         v = __longlong_as_double((long long)f2d_bits(w[u]));
@@ -631,8 +720,18 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
                     if (io && u == 0) io[i] = dt * v;
                 }
             }
+            if (bad) *dirty = 1;
         }
         __syncthreads();
+        // a non-finite result may have left non-finite words in the operand
+        // region, where the next element's A-tile padding (multiplied by the
+        // zero padding of the Khat images) would turn them into NaN: clear it
+        if (*dirty || (REF >= 1 && *nonfinite)) {
+            for (int i = tid; i < S::XY_SIZE; i += NT) smf[S::OFF_XY + i] = 0.f;
+            tc::fence_async_smem();  // before the bulk copies into the region
+            __syncthreads();
+            if (tid == 0) *dirty = 0;
+        }
     }
     tc::fence_before_sync();
     __syncthreads();

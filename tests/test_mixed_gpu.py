@@ -165,3 +165,34 @@ def test_bf16x3_unrefined_is_low_precision(L):
         L.poro_destroy(ctx)
     err = max(rel_l2(qt[i], oracle_predictor(d, i)) for i in range(n))
     assert 1e-9 < err < 1e-2
+
+
+@pytest.mark.parametrize("precision,sweeps", [(0, None), (1, 0), (1, 1), (1, 2), (2, 1)])
+def test_non_finite_input_stays_in_its_element(L, precision, sweeps):
+    """A NaN in one element's Q0 gives that element a non-finite predictor
+    (every entry NaN once refinement rounds it onto the fixed-point grid) and
+    leaves every other element bitwise as in a clean run."""
+    N, n, bad = 3, 40, 7
+    d = population(n, N, seed=99)
+    out = []
+    for poison in (False, True):
+        q0 = d["Q0"].copy()
+        if poison:
+            q0[bad, 9, 0] = np.nan
+        ctx = L.poro_create(0, N, precision)
+        try:
+            if sweeps is not None:
+                L.poro_set_refinement(ctx, sweeps)
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+            L.poro_set_dofs(ctx, q0)
+            L.poro_predict(ctx)
+            out.append(L.poro_get_predictor(ctx, 0, n))
+        finally:
+            L.poro_destroy(ctx)
+    clean, dirty = out
+    keep = np.arange(n) != bad
+    np.testing.assert_array_equal(clean[keep], dirty[keep])
+    assert np.isfinite(clean).all()
+    assert not np.isfinite(dirty[bad]).all()
+    if precision != 0 and sweeps:
+        assert np.isnan(dirty[bad]).all()
