@@ -178,9 +178,11 @@ INT_MAC_SLOTS = 2.0
 DW_OPS_PER_MAC = 12.0
 # DRAM bytes (read + write) per element of the headline kernels at N = 6, from
 # one ncu capture each of the 20,000-element case (dram__bytes_read.sum +
-# dram__bytes_write.sum divided by the elements; the traffic grows in
-# proportion to the elements, so a launch of n elements moves n times this)
-TRAFFIC_BYTES_PER_ELEMENT = {("fp64", 6, None): 77506.0}
+# dram__bytes_write.sum divided by the elements; for the bf16 form
+# dram__bytes.sum.per_second x gpu__time_duration.sum of its capture); the
+# traffic grows in proportion to the elements, so a launch of n elements
+# moves n times this
+TRAFFIC_BYTES_PER_ELEMENT = {("mixed", 6, 1): 77314.0, ("mixed_bf16", 6, 1): 77352.0, ("fp64", 6, None): 77506.0}
 # nominal tf32 : bf16 dense tensor ratio (1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -505,7 +507,7 @@ def run_ours(args):
         t_tc = tc_tile_flops(N, bf) * sw * n / (tf32_peak * 1e12)
         t_min = max(t_alu, t_tc)
         peak = (f_alu + f_tc + f_res) * n / t_min / 1e12
-        tb = None if bf else TRAFFIC_BYTES_PER_ELEMENT.get(("mixed", N, r["sweeps"]))
+        tb = TRAFFIC_BYTES_PER_ELEMENT.get(("mixed_bf16" if bf else "mixed", N, r["sweeps"]))
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": tb * n if tb else None,
                 "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}" + (",bf16>" if bf else ">"),
