@@ -239,16 +239,20 @@ def test_khat_rows_are_small_rationals(N):
     coefficients, so each row is an integer row over a small common
     denominator (a wrong normalisation factor, e.g. a stray sqrt(2), breaks
     this).  The mixed-precision residual stores Khat in exactly this form:
-    numerators below 2^23 (exact in binary32, packable with a 7-bit column)."""
-    worst_den, worst_num = 1, 0
+    numerators below 2^23 (packable with a 7-bit column), and each row's sum
+    of |numerators| below 2^22, so that its products with 22-bit fixed-point
+    values sum exactly below 2^44 in 64-bit integers."""
+    worst_den, worst_num, worst_sum = 1, 0, 0
     for K in basis.khat_matrices(N):
         rows = khat_row_fractions(K)
         assert rows is not None
         for nums, d in rows:
             worst_den = max(worst_den, d)
             worst_num = max([worst_num] + [abs(c) for c in nums])
+            worst_sum = max(worst_sum, sum(abs(c) for c in nums))
     assert worst_den == KHAT_MAX_DENOMINATOR[N]
     assert worst_num < 2**23
+    assert worst_sum < 2**22
 
 
 # ---------------------------------------------------------------- time matrices
