@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--lu-n3", type=int, default=1024, help="elements factored at N=3 for the LU comparator")
     ap.add_argument("--no-steps", action="store_true", help="skip the time-stepping / LTS sections")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--lts-nz", type=int, default=12,
+                    help="layered graded mesh of the LTS section: 2nz x 2nz x nz Kuhn boxes, 24 nz^3 tets "
+                         "(12: 41,472; 44: 2,044,416)")
     ap.add_argument("--serving-requests", type=int, default=12)
     return ap.parse_args()
 
@@ -311,7 +314,7 @@ def time_stepping_sections(L, local, args):
         r[name] = {"seconds": el, "steps": nsteps, "element_updates_per_s": ne * nsteps / el}
     out[f"periodic_{ne}_N5_gts"] = r
     # clustered LTS vs GTS on the layered graded mesh, same simulated time
-    mesh, mats = inputs.layered_graded_mesh(12, grading=512.0)
+    mesh, mats = inputs.layered_graded_mesh(args.lts_nz, grading=512.0)
     ne = mesh["tets"].shape[0]
     r = {"n_elem": ne, "degree": 5}
     for name, prec in (("fp64", 0), ("mixed", 1)):
