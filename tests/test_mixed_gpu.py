@@ -196,3 +196,24 @@ def test_non_finite_input_stays_in_its_element(L, precision, sweeps):
     assert not np.isfinite(dirty[bad]).all()
     if precision != 0 and sweeps:
         assert np.isnan(dirty[bad]).all()
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e20])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_is_scale_invariant(L, scale, precision):
+    """The predictor is linear in Q0: Q0 scaled by 1e-20 or 1e20 gives the
+    oracle's predictor scaled alike, within 1e-10, so the fixed-point grid of
+    the refinement (a power of two per quantity from its largest entry)
+    follows the data's magnitude."""
+    N, n = 4, 7
+    d = population(n, N, seed=404)
+    ctx = L.poro_create(0, N, precision)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"] * scale)
+        L.poro_predict(ctx)
+        qt = L.poro_get_predictor(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+    err = max(rel_l2(qt[i] / scale, oracle_predictor(d, i)) for i in range(n))
+    assert err <= TOL_MIXED, err
