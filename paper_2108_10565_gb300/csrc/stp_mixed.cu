@@ -200,8 +200,9 @@ __device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats) {
     auto fits = [&](int na, int nb) { return 2 * na * L.ahf + nb * L.bif <= xy_floats && (2 * na - 1) * L.ahf + 16 * (int)(L.sbo / 4) <= xy_floats && over >= 0; };
     L.nB = fits(1, 3) ? 3 : (fits(1, 2) ? 2 : 1);
     // direction j >= nB loads once the MMAs of j - nB are done, known at step
-    // j - nB + nA: that is no later than step j only if nA <= nB
-    L.nA = (L.nB >= 2 && fits(2, L.nB)) ? 2 : 1;
+    // j - nB + nA: that is no later than step j only if nA <= nB.  With three
+    // A buffers (and three slots) the block runs all directions in one pass.
+    L.nA = (L.nB == 3 && fits(3, 3)) ? 3 : ((L.nB >= 2 && fits(2, L.nB)) ? 2 : 1);
     return L;
 }
 
@@ -291,6 +292,53 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         const TcLayout L = tc_layout<PT, BF>(g, S.xy_floats);
         const int KP = L.KP, NP = L.NP;
         const uint32_t sbo = L.sbo, half = L.half;
+        if (L.nA == 3) {
+            // small block: the star products of all three directions in one
+            // pass, one barrier, then every direction's MMAs and one commit
+            for (int it = tid; it < 3 * d * T; it += NT) {
+                const int j = it / (d * T), r = it - j * (d * T);
+                float acc[NQ];
+                star_item<T, QS>(bq, star + j * STAR_NNZ, o, r, acc);
+                store_item<T, BF>(S.xy + 2 * j * L.ahf, S.xy + (2 * j + 1) * L.ahf, r, KP, acc);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (*S.abort) return false;
+            if (tid == 0) {
+                for (int j = 0; j < 3; ++j) {
+                    if (!tc::mbar_wait(S.bar_s + 16u + 8u * (uint32_t)j, (S.lph >> (2 + j)) & 1u)) *S.abort = 1;
+                    S.lph ^= 1u << (2 + j);
+                }
+                tc::fence_after_sync();
+                const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
+                const int nk = KP / KSTEP;
+                constexpr int MAXK = tc_kp(N, BF != 0) / KSTEP;
+                for (int j = 0; j < 3; ++j) {
+                    const uint32_t ah_s = S.xy_s + 4u * (uint32_t)(2 * j * L.ahf), al_s = ah_s + 4u * (uint32_t)L.ahf;
+                    const uint32_t b_s = S.xy_s + 4u * (uint32_t)(6 * L.ahf + j * L.bif);
+                    const uint64_t dal = tc::smem_desc(al_s, sbo), dah = tc::smem_desc(ah_s, sbo);
+                    const uint64_t dbh = tc::smem_desc(b_s, sbo), dbl = tc::smem_desc(b_s + half, sbo);
+#pragma unroll
+                    for (int kk = 0; kk < MAXK; ++kk) {
+                        if (kk < nk) {
+                            const uint64_t k16 = 16ull * (uint64_t)kk;
+                            if (BF) {
+                                tc::mma_bf16(S.tmem, dal + k16, dbh + k16, id, (j | kk) != 0);
+                                tc::mma_bf16(S.tmem, dah + k16, dbl + k16, id, 1u);
+                                tc::mma_bf16(S.tmem, dah + k16, dbh + k16, id, 1u);
+                            } else {
+                                tc::mma_tf32(S.tmem, dal + k16, dbh + k16, id, (j | kk) != 0);
+                                tc::mma_tf32(S.tmem, dah + k16, dbl + k16, id, 1u);
+                                tc::mma_tf32(S.tmem, dah + k16, dbh + k16, id, 1u);
+                            }
+                        }
+                    }
+                }
+                tc::mma_commit(S.bar_s);
+            }
+            if (!tc::mbar_wait(S.bar_s, S.mph & 1u)) *S.abort = 1;
+            S.mph ^= 1u;
+        } else {
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             const int abuf = j % L.nA, slot = j % L.nB;
@@ -355,6 +403,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             const int abuf = j % L.nA;
             if (!tc::mbar_wait(S.bar_s + 8u * (uint32_t)abuf, (S.mph >> abuf) & 1u)) *S.abort = 1;
             S.mph ^= 1u << abuf;
+        }
         }
         // the region is free: the next block's Khat images load during this
         // block's epilogue and the next time solves (issued by lane 0 of warp
