@@ -469,7 +469,6 @@ def run_ours(args):
                  / torch.linalg.vector_norm(b.reshape(n, -1), dim=1)).double().cpu().numpy()
             errs[name] = {"vs": "fp64 kernel (pinned to the oracle at 1e-12)", "median": float(np.median(e)),
                           "p99": float(np.quantile(e, 0.99)), "max": float(e.max())}
-    err = errs.get("mixed")
     del qts
 
     def roofline(name):
@@ -529,12 +528,13 @@ def run_ours(args):
                                   f"tensor cores at {tf32_peak:.0f} TFLOP/s tf32 (measured bf16 burst x {TF32_PER_BF16:.3f}); ")
                                + f"binary32 FMA peak {fp32_alu_peak_tflops(mhz):.1f} TFLOP/s"}
 
-    # headline: the tf32-sweep mixed form, else the bf16 one, when within 1e-10
-    # of the FP64 kernel (or when the FP64 form did not run); else FP64
+    # headline: the faster mixed form among those within 1e-10 of the FP64
+    # kernel on every element (or when the FP64 form did not run); else FP64
     def _accurate(name):
         e = errs.get(name)
         return name in res and (e is None or e["max"] <= 1e-10)
-    head = next((k for k in ("mixed", "mixed_bf16x3") if _accurate(k)), None)
+    ok = [k for k in ("mixed", "mixed_bf16x3") if _accurate(k)]
+    head = min(ok, key=lambda k: res[k]["ms"]) if ok else None
     head = head or ("fp64" if "fp64" in res else next(iter(res)))
     hr = res[head]
     value = n * world / (hr["ms"] * 1e-3)
@@ -602,8 +602,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": hr["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
-        "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": err,
+        "vs_baseline": None, "dtype": {"mixed": "tf32x3+f32+f64", "mixed_bf16x3": "bf16x3+f32+f64"}.get(head, "f64"), "data": "synthetic",
+        "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": errs.get(head),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
         "lu_comparator": lu, "time_stepping": steps, "serving": serving,
     }
