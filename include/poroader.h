@@ -86,7 +86,9 @@ typedef enum {
  * reference matrices (Khat^alpha = M^{-1} K^alpha, Section "Block-wise
  * back-substitution"; Z = S^{-1}(W - K^tau)).  *out receives the handle, or
  * NULL on error.  Errors: PORO_EINVAL (out NULL), PORO_EUNSUPPORTED,
- * PORO_ECUDA, PORO_ENOMEM. */
+ * PORO_ECUDA, PORO_ENOMEM, and PORO_ENUMERIC for a mixed-precision context
+ * whose Khat rows are not integer rows over a common denominator with a sum
+ * of |numerators| below 2^22 (the exact integer residual needs that). */
 poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out);
 
 /* Release every device and host resource of the context (waits for queued
@@ -99,10 +101,15 @@ poro_status poro_destroy(poro_ctx* ctx);
 const char* poro_last_error(const poro_ctx* ctx);
 
 /* Number of refinement sweeps of a mixed-precision context (0, 1 or 2;
- * default 1): each sweep forms
- * the residual of the predictor system in double-binary32 arithmetic
- * (error-free products and sums, ~2^-48 relative) and solves for the
- * correction with the low-precision back-substitution.
+ * default 1).  The binary32 solution is first rounded onto a fixed-point grid
+ * per quantity (integers of at most 22 bits times a power of two set by the
+ * quantity's largest entry).  Each sweep then forms the residual of the
+ * predictor system for that solution, binary64-accurate:
+ *   - the Khat and time-matrix products as exact integer sums;
+ *   - the star, E* and coupling products in double-binary32 arithmetic
+ *     (error-free products and sums, ~2^-48 relative).
+ * It solves for the correction with the low-precision back-substitution.
+ * The result is the rounded solution plus the corrections, in binary64.
  * Errors: PORO_EUNSUPPORTED for a PORO_FP64 context, PORO_EINVAL. */
 poro_status poro_set_refinement(poro_ctx* ctx, int32_t sweeps);
 
