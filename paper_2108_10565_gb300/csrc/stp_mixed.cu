@@ -171,9 +171,32 @@ struct TcState {
     int xy_floats;  // its size
     uint32_t bar_s;     // mbarriers: MMAs done reading A buffer 0, 1; Khat image in slot 0, 1, 2
     uint32_t tmem;
-    uint32_t mph, lph;  // phase parity of each barrier (bit b for buffer or slot b)
+    uint32_t mph, lph;  // phase parity of each barrier (bit b for MMA barrier b, bit 2 + s for slot s)
     volatile int* abort;
 };
+
+// A wait that gives up keeps its phase, so that the abort path can still
+// wait (with a limit) for the operation it was waiting for
+__device__ __forceinline__ void tc_wait(TcState& S, uint32_t bit) {
+    const uint32_t par = ((bit < 2 ? S.mph : S.lph) >> bit) & 1u;
+    if (tc::mbar_wait(S.bar_s + 8u * bit, par)) {
+        if (bit < 2)
+            S.mph ^= 1u << bit;
+        else
+            S.lph ^= 1u << bit;
+    } else {
+        *S.abort = 1;
+    }
+}
+
+// abort path (thread 0): a bounded wait on the next phase of every barrier,
+// so that bulk copies and MMAs still in flight have landed before the CTA
+// frees its TMEM and exits (a barrier with nothing in flight just runs out
+// its limit; this path only follows a wait that already gave up)
+__device__ __forceinline__ void tc_drain(TcState& S) {
+    for (uint32_t bit = 0; bit < 5; ++bit)
+        tc::mbar_wait(S.bar_s + 8u * bit, ((bit < 2 ? S.mph : S.lph) >> bit) & 1u);
+}
 
 // Operand layout of degree block g in the region (floats): nA A buffers (hi
 // tile, lo tile), then nB Khat image slots (hi image, lo image).  Direction j
@@ -305,10 +328,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             __syncthreads();
             if (*S.abort) return false;
             if (tid == 0) {
-                for (int j = 0; j < 3; ++j) {
-                    if (!tc::mbar_wait(S.bar_s + 16u + 8u * (uint32_t)j, (S.lph >> (2 + j)) & 1u)) *S.abort = 1;
-                    S.lph ^= 1u << (2 + j);
-                }
+                for (int j = 0; j < 3; ++j) tc_wait(S, 2u + (uint32_t)j);
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 const int nk = KP / KSTEP;
@@ -336,16 +356,14 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                 }
                 tc::mma_commit(S.bar_s);
             }
-            if (!tc::mbar_wait(S.bar_s, S.mph & 1u)) *S.abort = 1;
-            S.mph ^= 1u;
+            tc_wait(S, 0u);
         } else {
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             const int abuf = j % L.nA, slot = j % L.nB;
             const uint32_t mma_bar = S.bar_s + 8u * (uint32_t)abuf, ld_bar = S.bar_s + 16u + 8u * (uint32_t)slot;
             if (j >= L.nA) {  // the MMAs of direction j - nA (and all before) are done
-                if (!tc::mbar_wait(mma_bar, (S.mph >> abuf) & 1u)) *S.abort = 1;
-                S.mph ^= 1u << abuf;
+                tc_wait(S, (uint32_t)abuf);
                 // their slots are free: load the images not yet in flight
                 if (tid == 0)
                     for (int k = L.nB; k < 3; ++k)
@@ -367,8 +385,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             __syncthreads();
             if (*S.abort) return false;
             if (tid == 0) {
-                if (!tc::mbar_wait(ld_bar, (S.lph >> (2 + slot)) & 1u)) *S.abort = 1;
-                S.lph ^= 1u << (2 + slot);
+                tc_wait(S, 2u + (uint32_t)slot);
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 // one K step = two core matrices along K, 256 B further: 16
@@ -400,9 +417,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         // the last one covers every MMA of the block
 #pragma unroll 1
         for (int j = 3 - L.nA; j < 3; ++j) {
-            const int abuf = j % L.nA;
-            if (!tc::mbar_wait(S.bar_s + 8u * (uint32_t)abuf, (S.mph >> abuf) & 1u)) *S.abort = 1;
-            S.mph ^= 1u << abuf;
+            tc_wait(S, (uint32_t)(j % L.nA));
         }
         }
         // the region is free: the next block's Khat images load during this
@@ -782,6 +797,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             if (tid == 0) *dirty = 0;
         }
     }
+    if (tid == 0 && *abort) tc_drain(tcs);
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && *abort && P.status) atomicExch(P.status, 1);
