@@ -59,6 +59,32 @@ def _workload(args):
             "l2": "inputs larger than L2 (Q0 and Qt streamed every step)"}
 
 
+# ------------------------------------------------------------------ multi-rank
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank sets the job's time);
+    x itself for one rank.  `device` is the rank's GPU under NCCL, "cpu"
+    under gloo."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(per_rank_units, world, seconds):
+    """Whole-job throughput: every rank processes per_rank_units in the
+    slowest rank's time."""
+    return per_rank_units * world / seconds
+
+
+def rank_seed(rank):
+    """Each rank draws its own population (weak scaling, no shared data)."""
+    from paper_2108_10565_gb300 import inputs
+    return inputs.SEED_ISOLATED + rank
+
+
 # ------------------------------------------------------------------ clocks
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -410,7 +436,7 @@ def run_ours(args):
     except Exception:
         pass
     tensor_bf16_burst = float(peaks["bf16_tflops"])
-    d = inputs.isolated_elements(n, N, seed=inputs.SEED_ISOLATED + rank)
+    d = inputs.isolated_elements(n, N, seed=rank_seed(rank))
     dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
     B, T = d["Q0"].shape[2], N + 1
     # pinned host buffers of the end-to-end leg, allocated before the large
@@ -456,11 +482,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         clocks = sampler.stop()
         per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-        ms = evs[0].elapsed_time(evs[-1]) / args.steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(evs[0].elapsed_time(evs[-1]) / args.steps, world, dev)
         f = L.poro_flop_count(ctx, sweeps)
         res[name] = dict(ctx=ctx, ms=ms, per=per, clocks=clocks, flops=f, sweeps=sweeps, prec=prec)
         qts[name] = qt
@@ -541,7 +563,7 @@ def run_ours(args):
     head = min(ok, key=lambda k: res[k]["ms"]) if ok else None
     head = head or ("fp64" if "fp64" in res else next(iter(res)))
     hr = res[head]
-    value = n * world / (hr["ms"] * 1e-3)
+    value = job_rate(n, world, hr["ms"] * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned), headline form
     e2e = None
@@ -557,12 +579,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             L.poro_predict_host(ctx, hq_np, out=hi_np)
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 8),
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+        e2e = {"value": job_rate(n, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 8),
                "d2h_bytes_per_step": int(hi.numel() * 8), "form": head}
     for r in res.values():
         L.poro_destroy(r["ctx"])
@@ -594,7 +612,7 @@ def run_ours(args):
                          f"(numpy/LAPACK float64), {el:.1f} s"}
     forms_out = {}
     for name, r in res.items():
-        forms_out[name] = {"value": n * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
+        forms_out[name] = {"value": job_rate(n, world, r["ms"] * 1e-3), "ms_per_step": r["ms"],
                            "refine_sweeps": r["sweeps"] if name != "fp64" else None,
                            "roofline": roofline(name), "clocks": r["clocks"]}
         if name in errs:
