@@ -39,17 +39,6 @@ __device__ __forceinline__ void dw_mac1(float& h, float& l, float ah, float al, 
     l = __fadd_rn(l, __fadd_rn(er, e));
 }
 
-// acc += a * b with a exact (no low word)
-__device__ __forceinline__ void dw_mac_x(float& h, float& l, float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float e = __fmaf_rn(a, b, -p);
-    const float s = __fadd_rn(h, p);
-    const float bb = __fsub_rn(s, h);
-    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(er, e));
-}
-
 // acc += a * (bh + bl) with a exact
 __device__ __forceinline__ void dw_mac_x2(float& h, float& l, float a, float bh, float bl) {
     const float p = __fmul_rn(a, bh);
