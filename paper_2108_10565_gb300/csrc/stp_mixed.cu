@@ -4,35 +4,40 @@
 // form of Section "Block-wise back-substitution":
 //   (Z (x) I - E* + sum_j A^{j*} (x) Khat^j) Q = (S^{-1} w) o Q0 )
 // as
-//   Q1 = Alg3_f32(b0)                      binary32 back-substitution
-//   r  = b0 - Y Q1                         residual, double-binary32 exact
-//   d  = Alg3_f32(fl32(r));  Q = Q1 + d    (one sweep; a second repeats with
-//                                           Q1 + d in the residual)
-// The binary32 sweeps are Algorithm 3 (degree blocks, time solves with
+//   Q1 = Alg3_lo(b0)                       binary32 back-substitution
+//   Q1' = Q1 on a fixed-point grid          integers |v| <= 2^22 times 2^-s_p
+//   r  = b0 - Y Q1'                        residual, binary64-accurate
+//   d  = Alg3_lo(fl32(r));  Q = Q1' + d    (one sweep; a second repeats with
+//                                           Q1' + d in the residual)
+// The low-precision sweeps are Algorithm 3 (degree blocks, time solves with
 // (Z - E*_pp I)^{-1}, G coupling, star and Khat products).  Their dominant
 // step, b[p, l, u] -= sum_j sum_m Khat^j[l, m] X^j[p, m, u] over the rows
 // l < o_g of degree block g, is a dense contraction whose left operand Khat is
-// the same for every element: it runs on the tensor cores (tcgen05.mma
-// kind::tf32, accumulator in TMEM) with both operands split into tf32 hi + lo
-// words and the three products hi*hi + hi*lo + lo*hi accumulated (binary32
-// accuracy).  One MMA tile per (g, j): M = 128 rows (p, u) of the element,
-// N = rows l (o_g rounded up to 16), K = columns m of the block (d_g rounded up
-// to 8).  X^j (A operand) is written by the star-product threads straight
-// into shared memory in the K-major core-matrix layout; the Khat^j block (B
-// operand, prebuilt on the host in the same layout) arrives by bulk copy while
-// the star products run.  The
-// residual needs ~47 significant bits because Y Q1 cancels b0 to ~1e-7; GB300
-// issues binary64 FMAs at ~1/60 of its binary32 rate, so the residual runs on
-// the binary32 pipe with error-free transformations: FMA-based exact products
-// (p + e = a*b) and Knuth's TwoSum, accumulating pairs (hi, lo) as in the
-// double-word dot product of Ogita, Rump and Oishi (2005).  Every product of
-// the residual is formed exactly from double-word operands (Khat, A*, E* split
-// into hi + lo binary32 words; Z's entries are small integers, exact).
+// the same for every element: it runs on the tensor cores (tcgen05.mma,
+// accumulator in TMEM) with both operands split into hi + lo words (tf32, or
+// bf16 for the bf16 form) and the three products hi*hi + hi*lo + lo*hi
+// accumulated.  One MMA tile per (g, j): M = 128 rows (p, u) of the element,
+// N = rows l (o_g rounded up to 16), K = columns m of the block.  X^j (A
+// operand) is written by the star-product threads straight into shared memory
+// in the K-major core-matrix layout; the Khat^j block images (B operand,
+// prebuilt on the host in the same layout) arrive by bulk copy, prefetched
+// during the previous block (tc_layout says which buffers fit per block).
 //
-// Residual layout: one warp per Khat row l (rows round-robin over warps).
-//   R1: lanes over the 13 T (q, u) pairs: Y^j[q,u] = sum_m Khat^j[l,m] Q[q,m,u]
-//   R2: lanes over the (p, u) pairs: r[p,l,u] = b0 - sum_s Z_us Q[p,l,s]
-//       + E*_pp Q[p,l,u] + G Q[uf,l,u] - sum_j sum_q A^{j*}_pq Y^j[q,u]
+// The residual needs ~47 significant bits because Y Q1' cancels b0 to ~1e-7,
+// and GB300 issues binary64 FMAs at ~1/60 of its binary32 rate.  So:
+//   - the Khat rows are integer rows over a common denominator d_jl and Q1' is
+//     integer, so sum_m c_jlm Q1'[q,m,u] is an exact 64-bit integer sum (R1),
+//     and so is the time-matrix term sum_s Z_us Q1'[p,l,s] (Z is integer);
+//   - the star, E* and coupling products use double-binary32 arithmetic on
+//     the FP32 pipe: FMA-based exact products (p + e = a*b) and Knuth's
+//     TwoSum, accumulating pairs (hi, lo) as in the double-word dot product of
+//     Ogita, Rump and Oishi (2005).
+//
+// Residual layout: each warp takes its rows l from a balanced list.
+//   R1: lanes over the 13 T (q, u) pairs: Y^j[q,u] = (1/d_jl) sum_m c_jlm Q'[q,m,u]
+//   R2: lanes over the (p, u) pairs, dealt by star-row width:
+//       r[p,l,u] = b0 - sum_s Z_us Q'[p,l,s] + E*_pp Q'[p,l,u] + G Q'[uf,l,u]
+//                  - sum_j sum_q A^{j*}_pq Y^j[q,u]
 #include <cuda_runtime.h>
 
 #include <mutex>
