@@ -105,8 +105,10 @@ def _jacobi_homogenised(n, alpha, lo, hi):
     return r
 
 
+@lru_cache(maxsize=None)
 def dubiner_poly(i, j, k):
-    """Monomial expansion (integer coefficients) of phi_ijk."""
+    """Monomial expansion (integer coefficients) of phi_ijk.  The returned
+    dict is cached and shared: callers read it and never modify it."""
     L = _padd(_ONE, _pscale(_padd(_ETA, _ZETA), -1))          # 1 - eta - zeta
     f1 = _jacobi_homogenised(i, 0, _padd(_XI, _pscale(L, -1)), _XI)
     L2 = _padd(_ONE, _pscale(_ZETA, -1))                       # 1 - zeta

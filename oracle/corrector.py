@@ -23,6 +23,8 @@ Readings: the source or receiver on a shared vertex/edge/face belongs to
 the lowest element id whose barycentric coordinates are all >= -1e-12;
 receivers are sampled at the end of every step.
 """
+from functools import lru_cache
+
 import numpy as np
 from scipy.special import roots_legendre
 
@@ -34,15 +36,26 @@ FACE_TAGS = {0: "interior", 1: "free_surface", 2: "absorbing"}
 
 
 # ---------------------------------------------------------------- basis in float
-def basis_values(N, pts):
-    """phi_l at reference points pts[n][3] -> [n][B], from the exact integer
-    monomial expansions."""
-    pts = np.atleast_2d(pts)
-    out = np.zeros((pts.shape[0], basis.n_modes(N)))
+@lru_cache(maxsize=None)
+def _monomial_table(N):
+    """Exponents [n_mono][3] of every monomial of degree <= N and the
+    coefficient matrix C[l][mono] of the exact integer expansions of phi_l."""
+    exps = [(a, b, c) for a in range(N + 1) for b in range(N + 1 - a) for c in range(N + 1 - a - b)]
+    col = {e: i for i, e in enumerate(exps)}
+    C = np.zeros((basis.n_modes(N), len(exps)))
     for l, (i, j, k) in enumerate(basis.mode_triples(N)):
         for e, c in basis.dubiner_poly(i, j, k).items():
-            out[:, l] += float(c) * pts[:, 0] ** e[0] * pts[:, 1] ** e[1] * pts[:, 2] ** e[2]
-    return out
+            C[l, col[e]] = float(c)
+    return np.array(exps), C
+
+
+def basis_values(N, pts):
+    """phi_l at reference points pts[n][3] -> [n][B], from the exact integer
+    monomial expansions: sum over monomials of coefficient x xi^a eta^b zeta^c."""
+    pts = np.atleast_2d(np.asarray(pts, float))
+    exps, C = _monomial_table(N)
+    mono = np.prod(pts[:, None, :] ** exps[None, :, :], axis=2)   # [n][n_mono]
+    return mono @ C.T
 
 
 def triangle_quadrature(N):
@@ -85,8 +98,11 @@ def predict_alg3_batch(N, Astar, Estar, Q0):
                 if np.any(G != 0.0):
                     b[:, o, blk, :] += G[:, None, None] * Qt[:, p, blk, :]
         if g > 0:
+            # green update: two n-mode products, the star matrix on the
+            # quantity index, then Khat^j restricted to the block's columns
             for j in range(3):
-                b -= np.einsum("epq,lm,eqmu->eplu", Astar[:, j], Kh[j][:, blk], Qt[:, :, blk, :])
+                X = np.einsum("epq,eqmu->epmu", Astar[:, j], Qt[:, :, blk, :])
+                b -= np.einsum("lm,epmu->eplu", Kh[j][:, blk], X)
     return Qt
 
 

@@ -294,6 +294,70 @@ def test_block_algorithms_equal_dense(N, stiff):
             assert np.linalg.norm(alg(N, As, Es, q0) - ref) / nrm < 1e-13
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_batched_algorithm3_equals_dense(N):
+    """The batched Algorithm 3 that the time-stepping oracle (GTS and LTS)
+    calls reaches the dense LU solution of Eq. stp-lineq for every element
+    of one batch that mixes materials: inviscid, the reference viscosity,
+    10x and 100x stiff (e down to ~-2e4).  Every degree block g >= 3 takes the
+    green update, so an index slip there fails this pin."""
+    from oracle import corrector
+
+    scales = (0.0, 1.0, 10.0, 100.0) if N <= 4 else ((0.0, 100.0) if N == 5 else (100.0,))
+    d = inputs.isolated_elements(len(scales), N, seed=40 + N)
+    ops = []
+    for i, s in enumerate(scales):
+        mat = inputs.material_dict(d["materials"][i])
+        mat["nu"] *= s
+        dt = geometry.cfl_dt(d["vertices"][i], mat, N)
+        ops.append(predictor.element_operators(d["vertices"][i], mat, dt))
+    As = np.stack([o[0] for o in ops])
+    Es = np.stack([o[1] for o in ops])
+    Qb = corrector.predict_alg3_batch(N, As, Es, d["Q0"])
+    for i in range(len(scales)):
+        ref = predictor.predict_dense(N, As[i], Es[i], d["Q0"][i])
+        # at N >= 5 the 100x stiff system is the worst conditioned (|Qt| ~
+        # 1e7 |r|): dense LU and back-substitution then differ by ~6e-13,
+        # both within their rounding bound
+        tol = 1e-12 if (N >= 5 and scales[i] >= 100.0) else 1e-13
+        assert np.linalg.norm(Qb[i] - ref) / np.linalg.norm(ref) < tol, (N, scales[i])
+        # and the batch takes the same steps as the per-element Algorithm 3
+        q3 = predictor.predict_alg3(N, As[i], Es[i], d["Q0"][i])
+        assert np.linalg.norm(Qb[i] - q3) / np.linalg.norm(q3) < 1e-14
+    if N == 6:
+        # the fastest Darcy mode of the batch reaches the stiff range
+        assert Es[0][material.UF, material.UF] < -1e3
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_c_algorithm3_equals_dense(N):
+    """The plain-loop C statement of Algorithm 3 (oracle/alg3_loop.c: the timed
+    CPU baseline) reaches the dense LU solution of Eq. stp-lineq for a batch
+    mixing inviscid to 100x stiff elements, with 1 and with 3 threads (the
+    element loop's schedule changes nothing)."""
+    from oracle import alg3_c
+
+    scales = (0.0, 1.0, 10.0, 100.0) if N <= 4 else (1.0, 100.0)
+    d = inputs.isolated_elements(len(scales), N, seed=60 + N)
+    ops = []
+    for i, s in enumerate(scales):
+        mat = inputs.material_dict(d["materials"][i])
+        mat["nu"] *= s
+        dt = geometry.cfl_dt(d["vertices"][i], mat, N)
+        ops.append(predictor.element_operators(d["vertices"][i], mat, dt))
+    As = np.stack([o[0] for o in ops])
+    Es = np.stack([o[1] for o in ops])
+    q1 = alg3_c.predict_alg3_c(N, As, Es, d["Q0"], threads=1)
+    q3 = alg3_c.predict_alg3_c(N, As, Es, d["Q0"], threads=3)
+    assert np.array_equal(q1, q3)
+    for i in range(len(scales)):
+        ref = predictor.predict_dense(N, As[i], Es[i], d["Q0"][i])
+        # the 100x stiff systems are the worst conditioned (|Qt| ~ 1e7 |r|):
+        # dense LU and back-substitution differ there by up to a few 1e-13
+        tol = 1e-12 if scales[i] >= 100.0 else 1e-13
+        assert np.linalg.norm(q1[i] - ref) / np.linalg.norm(ref) < tol, (N, scales[i])
+
+
 # ---------------------------------------------------------------- P3: stiff source path
 def _pade_exp(k, m, z):
     """(k, m) Pade approximant of exp(z) (closed form)."""
