@@ -113,6 +113,21 @@ const char* poro_last_error(const poro_ctx* ctx);
  * Errors: PORO_EUNSUPPORTED for a PORO_FP64 context, PORO_EINVAL. */
 poro_status poro_set_refinement(poro_ctx* ctx, int32_t sweeps);
 
+/* Limit of the bounded waits of a mixed-precision context's predictor (the
+ * tensor-core and bulk-copy completions of its low-precision sweeps), in SM
+ * clock cycles; 0 restores the default (2e9 cycles, about 1 s).  The paper has
+ * no counterpart: every wait in the library's kernels gives up after its
+ * limit instead of spinning forever.  When a wait gives up, the CTA stops,
+ * waits with the default limit for its own copies and MMAs still in flight,
+ * frees its tensor memory and raises the context's device status; CTAs of the
+ * context that start an element after that skip it.  The next synchronising
+ * call (poro_sync, poro_get_*, poro_advance, poro_predict_host) then returns
+ * PORO_ETIMEOUT once and clears the status; the context stays usable.  A
+ * limit of 1 makes every wait that finds its operation unfinished give up at
+ * once (tests use it to exercise that path).
+ * Errors: PORO_EUNSUPPORTED for a PORO_FP64 context, PORO_EINVAL (negative). */
+poro_status poro_set_wait_limit(poro_ctx* ctx, int64_t cycles);
+
 /* Degree and precision the context was created with; n_elem after
  * poro_set_isolated (0 before). */
 poro_status poro_get_info(const poro_ctx* ctx, int32_t* degree_N, int32_t* precision, int64_t* n_elem);
@@ -321,7 +336,10 @@ poro_status poro_lu_release(poro_ctx* ctx);
  * N = 4, none at N >= 5) is rejected with PORO_EINVAL and a message giving the
  * bytes needed.  The first call for a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the one array and each
+ * call before any stream capture.  The address is kept for the life of the
+ * process, so do not use the library across a cudaDeviceReset of that
+ * device.  The caller's current device is restored before the call returns.
+ * Every call shares the one array and each
  * call zeroes what must start at zero (factor area, zero-pivot flag) before
  * use; calls whose work overlaps on the GPU (different streams, or a second
  * call before the first finished on another stream) race on the array.

@@ -13,7 +13,10 @@
 // Host code cannot use the array's name as a device address (on the host it
 // is only a stand-in), so the device address is looked up with
 // cudaGetSymbolAddress once per device, with that device current, on the
-// first call made for that device.
+// first call made for that device.  The address is cached for the life of the
+// process: a cudaDeviceReset (or any teardown of the device's primary
+// context) reloads the module, possibly elsewhere, so the library must not be
+// used across a reset of a device it has run on.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -88,10 +91,16 @@ extern "C" poro_status poro_lu_predict_static(poro_ctx* ctx, int64_t first, int6
         return PORO_EINVAL;
     }
     if (count == 0) return PORO_OK;
-    cudaError_t e = cudaSetDevice(v.device);
+    // a launch error reported below must be this call's, not one left over by
+    // an earlier unrelated call; and the caller's current device is restored
+    (void)cudaGetLastError();
+    int caller_device = -1;
+    cudaError_t e = cudaGetDevice(&caller_device);
+    if (e == cudaSuccess) e = cudaSetDevice(v.device);
     void* base = nullptr;
     if (e == cudaSuccess) e = static_scratch(v.device, &base);
     if (e != cudaSuccess) {
+        if (caller_device >= 0) cudaSetDevice(caller_device);
         ctx_set_error(ctx, std::string("poro_lu_predict_static: ") + cudaGetErrorString(e));
         return PORO_ECUDA;
     }
@@ -107,6 +116,7 @@ extern "C" poro_status poro_lu_predict_static(poro_ctx* ctx, int64_t first, int6
     // launch_lu_factor zeroes the factor area and the zero-pivot flag first
     int rc = launch_lu_factor(*v.lref, count, v.econst + first * v.stride, w, st);
     if (rc == 0) rc = launch_lu_solve(*v.lref, count, w, 0, q0, v.econst + first * v.stride, qt, iout, st);
+    cudaSetDevice(caller_device);
     if (rc != 0) {
         ctx_set_error(ctx, std::string("poro_lu_predict_static: ") + cudaGetErrorString((cudaError_t)rc));
         return PORO_ECUDA;

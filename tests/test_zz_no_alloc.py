@@ -85,3 +85,38 @@ def test_static_lu_rejects_oversized_batches(L):
             assert "static buffer holds" in str(ex.value)
         finally:
             L.poro_destroy(ctx)
+
+
+def test_static_lu_one_element_n4_integrated_only_on_its_own_stream(L):
+    """N = 4 with one element (the most that fits at N = 4), only the
+    time-integrated output (Qt_dev = NULL), on a caller stream other than the
+    context's, twice in a row; against poro_lu_factor + PORO_SOLVE_LU."""
+    import torch
+
+    N, n = 4, 3
+    d = population(n, N, seed=902)
+    ctx = L.poro_create(0, N, L.PORO_FP64)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        q0 = torch.tensor(d["Q0"], device="cuda")
+        B = q0.shape[2]
+        L.poro_lu_factor(ctx, 0, n)
+        ref_io = torch.full((n, 13, B), np.nan, dtype=torch.float64, device="cuda")
+        L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), None, ref_io.data_ptr(), L.PORO_SOLVE_LU, None)
+        L.poro_sync(ctx)
+        L.poro_lu_release(ctx)
+        side = torch.cuda.Stream()
+        outs = []
+        for first in (2, 1):
+            io = torch.full((1, 13, B), np.nan, dtype=torch.float64, device="cuda")
+            # one N = 4 element is 13 x 35 doubles, not a multiple of 16 bytes:
+            # the element's Q0 is passed from its own (aligned) buffer
+            q1 = q0[first:first + 1].clone()
+            L.poro_lu_predict_static(ctx, first, 1, q1.data_ptr(), None, io.data_ptr(), side.cuda_stream)
+            side.synchronize()
+            outs.append((first, io.cpu().numpy()[0]))
+        ri = ref_io.cpu().numpy()
+        for first, io in outs:
+            assert rel_l2(io, ri[first]) <= TOL
+    finally:
+        L.poro_destroy(ctx)
