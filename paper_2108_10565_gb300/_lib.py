@@ -54,6 +54,7 @@ SIGNATURES = [
     ("poro_predict_host", _i32, [_vp, _vp, _vp, _i64, _c.c_int]),
     ("poro_flop_count", _i32, [_vp, _i32, _pd]),
     ("poro_set_refinement", _i32, [_vp, _i32]),
+    ("poro_set_wait_limit", _i32, [_vp, _i64]),
     ("poro_lu_bytes", _i32, [_c.c_int, _i64, _c.POINTER(_c.c_size_t)]),
     ("poro_lu_factor", _i32, [_vp, _i64, _i64]),
     ("poro_lu_release", _i32, [_vp]),
@@ -238,6 +239,10 @@ def poro_predict_dev(ctx, first, count, q0_ptr, qt_ptr, i_ptr, solver=PORO_SOLVE
 
 def poro_set_refinement(ctx, sweeps):
     return _check(lib().poro_set_refinement(ctx, sweeps), ctx)
+
+
+def poro_set_wait_limit(ctx, cycles):
+    return _check(lib().poro_set_wait_limit(ctx, cycles), ctx)
 
 
 def poro_lu_bytes(N, count):

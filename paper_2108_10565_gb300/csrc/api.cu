@@ -490,6 +490,14 @@ poro_status poro_set_refinement(poro_ctx* c, int32_t sweeps) {
     return PORO_OK;
 }
 
+poro_status poro_set_wait_limit(poro_ctx* c, int64_t cycles) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_wait_limit: ctx is NULL");
+    if (c->prec == PORO_FP64) return fail(c, PORO_EUNSUPPORTED, "poro_set_wait_limit: context is not mixed precision");
+    if (cycles < 0) return fail(c, PORO_EINVAL, "poro_set_wait_limit: cycles must be >= 0");
+    c->mref.wait_limit = (long long)cycles;
+    return PORO_OK;
+}
+
 poro_status poro_destroy(poro_ctx* c) {
     if (!c) return PORO_OK;
     cudaSetDevice(c->device);

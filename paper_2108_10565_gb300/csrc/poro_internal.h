@@ -151,6 +151,7 @@ struct MixedReference {
     float* khat_tc = nullptr;
     int32_t tc_off[MAX_N + 1][3] = {};
     int32_t* status = nullptr;      // device word: 1 after a bounded wait gave up
+    long long wait_limit = 0;       // SM clocks a wait of the sweeps may take (0: about 1 s)
 };
 
 // Fill the constant-memory residual table of degree N on the current device

@@ -65,6 +65,7 @@ struct K2Params {
     const float* khat_tc;     // tensor-core images of the Khat^j blocks (hi then lo)
     int32_t tc_off[MAX_N + 1][3];
     int32_t* status;          // set to 1 if a bounded wait gave up
+    long long wait_limit;     // SM clocks after which a wait of the sweeps gives up
 };
 
 // Residual CSR of every degree in constant memory: the table depends only on
@@ -169,7 +170,11 @@ __device__ __forceinline__ void solve_row8(float* row, const float* Zi) {
     }
 }
 
-// Tensor-core state of one CTA (shared addresses, barrier phases)
+// Tensor-core state of one CTA (shared addresses, barrier phases).  Thread 0
+// issues every bulk copy and every MMA commit, and only while all of its own
+// waits have succeeded: then no barrier ever gets a second operation while
+// an earlier one may still be in flight, and `pend` (thread 0's record of the
+// barriers with an operation it has not seen complete) is exact.
 struct TcState {
     float* xy;      // operand region: A tiles (tf32 words, or bf16 values in the same bytes), then Khat images
     uint32_t xy_s;  // its shared address
@@ -177,30 +182,36 @@ struct TcState {
     uint32_t bar_s;     // mbarriers: MMAs done reading A buffer 0, 1; Khat image in slot 0, 1, 2
     uint32_t tmem;
     uint32_t mph, lph;  // phase parity of each barrier (bit b for MMA barrier b, bit 2 + s for slot s)
+    uint32_t pend;      // thread 0: barriers (same bits) with an operation in flight
+    bool gave_up;       // thread 0: one of its waits gave up, it issues nothing more
+    long long limit;    // SM clocks a wait of the sweeps may take
     volatile int* abort;
 };
 
 // A wait that gives up keeps its phase, so that the abort path can still
-// wait (with a limit) for the operation it was waiting for
+// wait (with the full limit) for the operation it was waiting for
 __device__ __forceinline__ void tc_wait(TcState& S, uint32_t bit) {
     const uint32_t par = ((bit < 2 ? S.mph : S.lph) >> bit) & 1u;
-    if (tc::mbar_wait(S.bar_s + 8u * bit, par)) {
+    if (tc::mbar_wait(S.bar_s + 8u * bit, par, S.limit)) {
         if (bit < 2)
             S.mph ^= 1u << bit;
         else
             S.lph ^= 1u << bit;
+        S.pend &= ~(1u << bit);
     } else {
         *S.abort = 1;
+        S.gave_up = true;
     }
 }
 
-// abort path (thread 0): a bounded wait on the next phase of every barrier,
-// so that bulk copies and MMAs still in flight have landed before the CTA
-// frees its TMEM and exits (a barrier with nothing in flight just runs out
-// its limit; this path only follows a wait that already gave up)
+// abort path (thread 0): a wait with the full limit on every barrier that
+// still has a bulk copy or MMA in flight, so that they have landed before
+// the CTA frees its TMEM and exits.  Barriers with nothing in flight are
+// skipped.
 __device__ __forceinline__ void tc_drain(TcState& S) {
     for (uint32_t bit = 0; bit < 5; ++bit)
-        tc::mbar_wait(S.bar_s + 8u * bit, ((bit < 2 ? S.mph : S.lph) >> bit) & 1u);
+        if ((S.pend >> bit) & 1u)
+            tc::mbar_wait(S.bar_s + 8u * bit, ((bit < 2 ? S.mph : S.lph) >> bit) & 1u);
 }
 
 // Operand layout of degree block g in the region (floats): nA A buffers (hi
@@ -234,10 +245,13 @@ __device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats) {
     return L;
 }
 
-// bulk copy of direction j's Khat image of block g into its slot (one thread)
+// bulk copy of direction j's Khat image of block g into its slot (thread 0,
+// unless one of its waits gave up)
 template <int PT, int BF>
-__device__ __forceinline__ void tc_load_khat(const TcState& S, const TcLayout& L, const K2Params& P, int g, int j) {
+__device__ __forceinline__ void tc_load_khat(TcState& S, const TcLayout& L, const K2Params& P, int g, int j) {
+    if (S.gave_up) return;
     const int slot = j % L.nB;
+    S.pend |= 1u << (2 + slot);
     const uint32_t bar = S.bar_s + 16u + 8u * (uint32_t)slot;
     const uint32_t dst = S.xy_s + 4u * (uint32_t)(2 * L.nA * L.ahf + slot * L.bif);
     tc::fence_async_smem();
@@ -334,6 +348,8 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             if (*S.abort) return false;
             if (tid == 0) {
                 for (int j = 0; j < 3; ++j) tc_wait(S, 2u + (uint32_t)j);
+            }
+            if (tid == 0 && !S.gave_up) {
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 const int nk = KP / KSTEP;
@@ -360,6 +376,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                     }
                 }
                 tc::mma_commit(S.bar_s);
+                S.pend |= 1u;
             }
             tc_wait(S, 0u);
         } else {
@@ -389,8 +406,8 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             tc::fence_async_smem();
             __syncthreads();
             if (*S.abort) return false;
-            if (tid == 0) {
-                tc_wait(S, 2u + (uint32_t)slot);
+            if (tid == 0) tc_wait(S, 2u + (uint32_t)slot);
+            if (tid == 0 && !S.gave_up) {
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 // one K step = two core matrices along K, 256 B further: 16
@@ -416,6 +433,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                     }
                 }
                 tc::mma_commit(mma_bar);
+                S.pend |= 1u << abuf;
             }
         }
         // wait for the commits not yet waited for (directions 3 - nA .. 2);
@@ -426,9 +444,8 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         }
         }
         // the region is free: the next block's Khat images load during this
-        // block's epilogue and the next time solves (issued by lane 0 of warp
-        // 3, whose TMEM lane quarter holds no rows: 13 T <= 96)
-        if (tid == (NW >= 4 ? 96 : 0) && g > 1) {
+        // block's epilogue and the next time solves
+        if (tid == 0 && g > 1) {
             const TcLayout Ln = tc_layout<PT, BF>(g - 1, S.xy_floats);
             for (int j = 0; j < Ln.nB; ++j) tc_load_khat<PT, BF>(S, Ln, P, g - 1, j);
         }
@@ -439,7 +456,10 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             const int sp = warp & 3;
             const int ncol = NW == 8 ? NP / 2 : NP;
             const int c_begin = NW == 8 ? (warp >> 2) * ncol : 0;
-            if (sp * 32 < PT) {
+            // a warp with a lane whose wait gave up reads no TMEM (the MMAs
+            // may still be writing it); the CTA leaves the sweep below
+            const bool skip = __any_sync(0xffffffffu, S.gave_up);
+            if (sp * 32 < PT && !skip) {
                 const int r = sp * 32 + lane;
                 const int p = r / T, u = r - (r / T) * T;
                 float* dst = bq + p * QS + u;
@@ -678,6 +698,9 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     tcs.xy_floats = S::XY_SIZE;
     tcs.bar_s = tc::smem_addr(bars);
     tcs.mph = tcs.lph = 0;
+    tcs.pend = 0;
+    tcs.gave_up = false;
+    tcs.limit = P.wait_limit > 0 ? P.wait_limit : tc::WAIT_LIMIT_CYCLES;
     tcs.abort = abort;
 
     // operand region starts finite (K padding of A meets zeros of B)
@@ -705,6 +728,9 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
         const double* q0 = P.q0 + e * (int64_t)(NQ * B);
         const double* ec = P.econst + e * (int64_t)P.stride;
+        // a wait of another CTA of this context gave up: skip the remaining
+        // elements (the launch's results are reported as failed anyway)
+        const int failed = (tid == 0 && P.status) ? *reinterpret_cast<volatile const int32_t*>(P.status) : 0;
         if (tid == 0) *nonfinite = 0;  // read after the barriers below
         for (int i = tid; i < 3 * STAR_NNZ; i += NT) {
             const float2 v = dw_split(ec[i]);
@@ -732,7 +758,9 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
 #pragma unroll
             for (int u = 0; u < T; ++u) row[u] = (float)((2 * u + 1) * ((u & 1) ? -1 : 1)) * v;
         }
+        if (failed) *abort = 1;
         __syncthreads();
+        if (*abort) break;
         if (!alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
         if (REF >= 1) {
             stash_sweep<N, REF, NT_>(Q1, sq, nonfinite, W, q0);
@@ -802,7 +830,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             if (tid == 0) *dirty = 0;
         }
     }
-    if (tid == 0 && *abort) tc_drain(tcs);
+    if (tid == 0 && tcs.pend) tc_drain(tcs);
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && *abort && P.status) atomicExch(P.status, 1);
@@ -828,10 +856,16 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     for (int g = 0; g <= MAX_N; ++g)
         for (int j = 0; j < 3; ++j) P.tc_off[g][j] = ref.tc_off[g][j];
     P.status = ref.status;
+    P.wait_limit = ref.wait_limit;
     // one CTA per element; every resident CTA holds TMEM_COLS columns of the
     // SM's 512, so the shared-memory request is raised where needed to keep
-    // at most 512 / TMEM_COLS CTAs of this kernel resident on an SM (so none
-    // of them waits for TMEM)
+    // at most 512 / TMEM_COLS CTAs of this kernel resident on an SM (so no
+    // CTA of this kernel waits for TMEM behind another one of it).  Kernels
+    // of different degrees running concurrently on other streams (the
+    // server's requests) can together ask for more than 512 columns; a CTA
+    // then waits in tcgen05.alloc until a CTA of the other kernel exits and
+    // frees its columns.  That CTA depends on nothing of this one and all of
+    // its waits are bounded, so the allocation wait ends too.
     int dev = 0, sm_smem = 0, reserved = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);

@@ -4,8 +4,9 @@
 // 8-row x 16-byte core matrices, element (r, k) at float offset
 //   (r / 8) * SBO + (k / 4) * 32 + (r % 8) * 4 + (k % 4)
 // with the K-adjacent core matrices 128 bytes apart (LBO) and the 8-row groups
-// SBO = 8 * K floats apart.  Every wait is bounded: it gives up after about a
-// second of SM clocks and reports failure instead of spinning forever.
+// SBO = 8 * K floats apart.  Every mbarrier wait is bounded: it gives up after
+// a set number of SM clocks (by default about a second) and reports failure
+// instead of spinning forever.
 #pragma once
 
 #include <cstdint>
@@ -86,10 +87,27 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// non-blocking probe: has the phase with the given parity completed?
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity to complete: a
+// non-blocking probe, then blocking probes until `limit` SM clocks have
+// passed.  A limit of 1 gives up on any phase not complete at the first probe.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = WAIT_LIMIT_CYCLES) {
     const long long t0 = clock64();
     for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -99,7 +117,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
     }
 }
 

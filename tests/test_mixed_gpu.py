@@ -217,3 +217,89 @@ def test_mixed_is_scale_invariant(L, scale, precision):
         L.poro_destroy(ctx)
     err = max(rel_l2(qt[i] / scale, oracle_predictor(d, i)) for i in range(n))
     assert err <= TOL_MIXED, err
+
+
+def _pade_exp(k, m, z):
+    """(k, m) Pade approximant of exp(z), closed form (the P3 pin of the oracle)."""
+    from math import factorial
+
+    num = sum(factorial(k + m - j) * factorial(k) / (factorial(k + m) * factorial(j) * factorial(k - j)) * z ** j
+              for j in range(k + 1))
+    den = sum(factorial(k + m - j) * factorial(m) / (factorial(k + m) * factorial(j) * factorial(m - j)) * (-z) ** j
+              for j in range(m + 1))
+    return num / den
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("N", [3, 6])
+def test_stiff_limit_is_radau_pade(L, N, precision):
+    """Stiff Darcy limit on the GPU (the oracle's P3 pin, here for every
+    precision form): constant-in-space data (mode 0 only) makes every spatial
+    term vanish, so the predictor is DG in time for q' = E* q.  Its end value
+    is the (N, N+1) Pade approximant R(e) of exp: uf(1) = R(e) uf0 and
+    u(1) = u0 + g/e (R(e) - 1) uf0, the other quantities stay constant.
+    The fluid viscosity is scaled by 1 ... 1e6, which puts e = dt E*_ufuf from
+    about -2e2 down to about -2e8 (L-stable: R(e) -> 0)."""
+    from oracle import material, predictor
+    from paper_2108_10565_gb300 import inputs
+
+    for scale in (1.0, 1e2, 1e4, 1e6):
+        d = population(6, N, seed=500 + N, viscosity_scale=scale)
+        q0 = np.zeros_like(d["Q0"])
+        q0[:, :, 0] = d["Q0"][:, :, 0]
+        d["Q0"] = q0
+        ctx = L.poro_create(0, N, precision)
+        try:
+            L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+            L.poro_set_dofs(ctx, q0)
+            L.poro_predict(ctx)
+            qt = L.poro_get_predictor(ctx, 0, 6)
+        finally:
+            L.poro_destroy(ctx)
+        assert np.abs(qt[:, :, 1:, :]).max() == 0.0  # higher modes stay exactly zero
+        tol = 1e-12 if precision == 0 else TOL_MIXED
+        for i in range(6):
+            As, Es = predictor.element_operators(d["vertices"][i], inputs.material_dict(d["materials"][i]), d["dt"][i])
+            end = qt[i].sum(axis=2)  # chi_s(1) = 1
+            for v_, f_ in ((material.U, material.UF), (material.V, material.VF), (material.W, material.WF)):
+                e, g = Es[f_, f_], Es[v_, f_]
+                R = _pade_exp(N, N + 1, e)
+                sc = np.abs(q0[i, :, 0]).max()
+                assert abs(end[f_, 0] - R * q0[i, f_, 0]) <= tol * sc, (scale, e)
+                assert abs(end[v_, 0] - (q0[i, v_, 0] + g / e * (R - 1) * q0[i, f_, 0])) <= tol * sc, (scale, e)
+            for q in (0, 1, 2, 3, 4, 5, 9):
+                assert abs(end[q, 0] - q0[i, q, 0]) <= tol * np.abs(q0[i, :, 0]).max()
+            ref = predictor.predict_alg3(N, As, Es, q0[i])
+            assert rel_l2(qt[i], ref) <= tol, (scale, rel_l2(qt[i], ref))
+        if scale == 1e6:
+            assert Es[material.UF, material.UF] < -1e7
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_bounded_wait_gives_up_and_context_recovers(L, precision):
+    """The bounded-wait path of the mixed kernel: with a wait limit of one SM
+    clock every wait that finds its MMA or bulk copy unfinished gives up.  The
+    CTA then waits (with the default limit) for what it has in flight, frees
+    its tensor memory and raises the context's status; the next synchronising
+    call returns PORO_ETIMEOUT once.  With the default limit restored, the
+    same context computes the correct predictor."""
+    N, n = 4, 48
+    d = population(n, N, seed=77)
+    ctx = L.poro_create(0, N, precision)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"])
+        L.poro_set_wait_limit(ctx, 1)
+        L.poro_predict(ctx)
+        with pytest.raises(L.PoroError) as ei:
+            L.poro_sync(ctx)
+        assert ei.value.status == L.PORO_ETIMEOUT
+        L.poro_sync(ctx)  # reported once, then cleared
+        L.poro_set_wait_limit(ctx, 0)
+        L.poro_predict(ctx)
+        L.poro_sync(ctx)
+        qt = L.poro_get_predictor(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+    errs = [rel_l2(qt[i], oracle_predictor(d, i)) for i in range(n)]
+    assert max(errs) <= TOL_MIXED
