@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed", "bf16x3"])
     ap.add_argument("--refine", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--cpu-elems", type=int, default=16384,
+                    help="elements of the workload the timed CPU baseline runs (repeated over the budget)")
+    ap.add_argument("--ref-elems", type=int, default=4096, help="elements per step of the --impl reference arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-lu", action="store_true")
@@ -134,9 +137,46 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ cpu baseline
-def cpu_oracle_rate(args, budget_s, n_min=1):
-    """Time the oracle (dense equilibrated LU of Eq. stp-lineq, numpy/LAPACK
-    float64) on the host cores on the first elements of the same workload."""
+def _cpu_population(N, n, seed):
+    """Operators A^{j*}, E* and Q0 of the first n elements of the workload,
+    computed by the oracle (not timed)."""
+    from oracle import geometry, predictor
+    from paper_2108_10565_gb300 import inputs
+
+    d = inputs.isolated_elements(n, N, seed=seed)
+    As = np.empty((n, 3, 13, 13))
+    Es = np.empty((n, 13, 13))
+    for i in range(n):
+        mat = inputs.material_dict(d["materials"][i])
+        dt = geometry.cfl_dt(d["vertices"][i], mat, N)
+        As[i], Es[i] = predictor.element_operators(d["vertices"][i], mat, dt)
+    return As, Es, d["Q0"]
+
+
+def cpu_alg3_rate(N, budget_s, threads, n_elem, seed=None):
+    """Element-updates/s of the oracle's plain-loop C Algorithm 3 (binary64,
+    OpenMP over elements, no BLAS) on the first n_elem elements of the
+    workload, repeated until budget_s has passed.  Returns (rate, threads
+    used, elements per pass, passes, seconds)."""
+    from oracle import alg3_c
+    from paper_2108_10565_gb300 import inputs
+
+    As, Es, Q0 = _cpu_population(N, n_elem, inputs.SEED_ISOLATED if seed is None else seed)
+    ref = alg3_c.reference_arrays(N)
+    alg3_c.predict_alg3_c(N, As[:64], Es[:64], Q0[:64], threads, ref)  # warm-up (threads, pages)
+    t0 = time.perf_counter()
+    passes = 0
+    while passes == 0 or time.perf_counter() - t0 < budget_s:
+        alg3_c.predict_alg3_c(N, As, Es, Q0, threads, ref)
+        passes += 1
+    el = time.perf_counter() - t0
+    used = threads if threads > 0 else alg3_c.default_threads()
+    return n_elem * passes / el, used, n_elem, passes, el
+
+
+def cpu_dense_lu_rate(args, budget_s, n_min=1):
+    """The oracle's definition (dense equilibrated LU of Eq. stp-lineq,
+    numpy/LAPACK float64) on the host cores, first elements of the workload."""
     from oracle import geometry, predictor
     from paper_2108_10565_gb300 import inputs
 
@@ -160,35 +200,47 @@ def cpu_oracle_rate(args, budget_s, n_min=1):
     return done / el, cores, done, el
 
 
+def cpu_baseline(args):
+    """The oracle timed on the host cores: the plain-loop C Algorithm 3 on all
+    cores (the baseline), on one core, and the dense-LU definition."""
+    nall = args.cpu_elems
+    rate, cores, k, passes, el = cpu_alg3_rate(args.degree, args.cpu_budget_s, 0, nall)
+    r1, _, k1, p1, el1 = cpu_alg3_rate(args.degree, args.cpu_budget_s / 3, 1, max(64, nall // 16))
+    lu, lu_cores, lu_k, lu_el = cpu_dense_lu_rate(args, args.cpu_budget_s / 3)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle Algorithm 3 as plain C loops (binary64, OpenMP over elements, no BLAS, "
+                      f"-ffp-contract=off): first {k} elements of the N={args.degree} workload, {passes} passes, "
+                      f"{el:.1f} s on {cores} threads",
+            "one_core": {"value": r1, "sample": f"first {k1} elements, {p1} passes, {el1:.1f} s"},
+            "dense_lu_definition": {"value": lu, "cores": lu_cores,
+                                    "sample": f"first {lu_k} elements, dense equilibrated LU (numpy/LAPACK), "
+                                              f"{lu_el:.1f} s"}}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle on the host cores: each step runs the plain-loop C
+    Algorithm 3 (binary64, all cores) on a sample of the workload's
+    elements (the first --ref-elems elements)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import geometry, predictor
+    from oracle import alg3_c
     from paper_2108_10565_gb300 import inputs
 
-    n_total = args.steps + args.warmup
-    d = inputs.isolated_elements(n_total, args.degree)
-    ops = []
-    for i in range(n_total):
-        mat = inputs.material_dict(d["materials"][i])
-        dt = geometry.cfl_dt(d["vertices"][i], mat, args.degree)
-        ops.append(predictor.element_operators(d["vertices"][i], mat, dt))
-    for i in range(args.warmup):
-        predictor.predict_dense(args.degree, *ops[i], d["Q0"][i])
+    N, n = args.degree, args.ref_elems
+    As, Es, Q0 = _cpu_population(N, n, inputs.SEED_ISOLATED)
+    ref = alg3_c.reference_arrays(N)
+    for _ in range(args.warmup):
+        alg3_c.predict_alg3_c(N, As, Es, Q0, 0, ref)
     t0 = time.perf_counter()
-    for i in range(args.warmup, n_total):
-        predictor.predict_dense(args.degree, *ops[i], d["Q0"][i])
+    for _ in range(args.steps):
+        alg3_c.predict_alg3_c(N, As, Es, Q0, 0, ref)
     el = time.perf_counter() - t0
-    rate = args.steps / el
-    try:
-        from threadpoolctl import threadpool_info
-
-        cores = max(int(i.get("num_threads", 1)) for i in threadpool_info())
-    except Exception:
-        cores = os.cpu_count()
-    sample = f"1 element per step ({args.steps} timed steps) of the N={args.degree} workload"
+    rate = n * args.steps / el
+    cores = alg3_c.default_threads()
+    sample = (f"{n} elements per step (the first {n} of the N={N} workload), oracle Algorithm 3 as plain C loops "
+              f"(binary64, OpenMP over elements, no BLAS)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -431,11 +483,14 @@ def run_ours(args):
     N, n = args.degree, args.n_elem
     dev = f"cuda:{local}"
     peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}  # fallback when no measured peaks are present
+    peaks_src = "fallback (6.8 TB/s, 1.9 PFLOP/s bf16)"
     try:
         peaks.update(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))))
+        peaks_src = "MEASURED_PEAKS.json"
     except Exception:
         pass
     tensor_bf16_burst = float(peaks["bf16_tflops"])
+    hbm_gbs = float(peaks["hbm_gbs"])
     d = inputs.isolated_elements(n, N, seed=rank_seed(rank))
     dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
     B, T = d["Q0"].shape[2], N + 1
@@ -498,61 +553,75 @@ def run_ours(args):
     del qts
 
     def roofline(name):
+        """Roofline of one form's kernel against the measured peaks
+        (MEASURED_PEAKS.json): HBM copy bandwidth and dense bf16 tensor
+        throughput (tf32 = bf16 x the nominal tf32 : bf16 ratio).  `frac` is
+        the largest fraction over those roofs and `bound` names it; the
+        binary64 kernel, which neither roof bounds, reports its FP64 pipe
+        against the nominal unit count x the sampled clock.  `model` keeps the
+        kernel's own issue-slot model apart from these."""
         r = res[name]
         mhz = (r["clocks"] or {}).get("sm_mhz") or 2070.0
         t = statistics.mean(r["per"]) * 1e-3
+        Bm, Tm = (N + 1) * (N + 2) * (N + 3) // 6, N + 1
+        stride = (3 * 54 + Tm * Tm + 4 + 1) & ~1
+        alg_bytes = 8.0 * (13 * Bm + stride + 13 * Bm * Tm + 13 * Bm)  # Q0, constants in; Qt, I out
+        hbm_ach = alg_bytes * n / t / 1e9
+        terms = {"hbm": {"achieved": hbm_ach, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_ach / hbm_gbs,
+                         "algorithmic_bytes_per_element": alg_bytes}}
         if r["prec"] == L.PORO_FP64:
             ach = r["flops"][0] * n / t / 1e12
             peak = fp64_alu_peak_tflops(mhz)
             tb = TRAFFIC_BYTES_PER_ELEMENT.get(("fp64", N, None))
+            terms["fp64_pipe"] = {"achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
             return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                     "traffic": tb * n if tb else None, "kernel": f"stp_fp64_kernel<{N}>",
-                    "flops_per_element": r["flops"][0],
-                    "peak_source": "binary64 FMA pipe: nominal 1.25 TFLOP/s at 2070 MHz, scaled to the sampled clock"}
-        # Algorithm 3 flops split by engine: the Khat products (S4b) run on the
-        # tensor cores (tf32 hi/lo, 3 products), the rest of the sweeps and
-        # the double-word residual on the binary32 pipe
-        Bm, Tm = (N + 1) * (N + 2) * (N + 3) // 6, N + 1
+                    "flops_per_element": r["flops"][0], "terms": terms,
+                    "peak_source": "binary64 FMA pipe, nominal (152 SM x 2 FMA/clk x 2 flop x 2.07 GHz = 1.25 "
+                                   "TFLOP/s) scaled to the sampled clock; no measured FP64 peak exists"}
+        # the Khat products of the sweeps on the tensor cores: dense degree
+        # blocks (o_g rows x d_g columns, 13 T right-hand columns, 3
+        # directions), 3 split products, per sweep (algorithmic); the tiles as
+        # issued pad rows to 128 and columns to the MMA shape
+        bf = r["prec"] == L.PORO_BF16X3_REFINE
+        sw = 1 + r["sweeps"]
+        tc_alg = sum(3 * (g * (g + 1) * (g + 2) // 6) * ((g + 1) * (g + 2) // 2) * 13 * Tm * 2 * 3
+                     for g in range(1, N + 1)) * sw
+        tc_peak = tensor_bf16_burst * (1.0 if bf else TF32_PER_BF16)
+        tc_ach = tc_alg * n / t / 1e12
+        terms["tensor"] = {"achieved": tc_ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_ach / tc_peak,
+                           "dtype": "bf16" if bf else "tf32",
+                           "peak_source": "measured bf16 burst" + ("" if bf else f" x {TF32_PER_BF16:.3f}"),
+                           "algorithmic_flops_per_element": tc_alg,
+                           "issued_flops_per_element": tc_tile_flops(N, bf) * sw}
+        bound = max(("hbm", "tensor"), key=lambda k: terms[k]["frac"])
+        b = terms[bound]
+        # the kernel's own issue model (not a hardware roof): binary32 pipe
+        # at 152 x 128 lanes per clock, 1 slot per FMA, INT_MAC_SLOTS per
+        # integer MAC, DW_OPS_PER_MAC per double-word MAC, overlapped with the
+        # issued tensor tiles
         s3 = 2.0 * 13 * Bm * Tm * Tm + 2.0 * 3 * Bm * Tm
         s4a = 2.0 * 3 * 54 * (Bm - 1) * Tm
         s15 = 13 * Bm * Tm + 13 * Bm
         s4b = r["flops"][0] - (s3 + s4a + s15)
-        sw = 1 + r["sweeps"]
-        f_alu, f_tc, f_res = (s3 + s4a + s15) * sw, s4b * sw, r["flops"][2]
-        ach = (f_alu + f_tc + f_res) * n / t / 1e12
-        # residual multiply-adds per element: integer (Khat, time matrix) and
-        # double-word (star terms, E* and coupling)
+        f_alu = (s3 + s4a + s15) * sw
         int_macs = (s4b / 2 + 13 * Bm * Tm * Tm) * r["sweeps"]
         dw_macs = (6 * Bm * Tm + 3 * 54 * Bm * Tm) * r["sweeps"]
-        # fastest this work runs: binary32 pipe at its issue rate (1 instruction
-        # per FMA, INT_MAC_SLOTS per integer MAC, DW_OPS_PER_MAC per double-word
-        # MAC, 152 x 128 per clock) overlapped with the tensor tiles at the tf32
-        # peak (measured bf16 burst x nominal tf32 ratio); the slower of the two
-        # bounds the kernel
         t_alu = (f_alu / 2 + INT_MAC_SLOTS * int_macs + DW_OPS_PER_MAC * dw_macs) * n / (152 * 128 * mhz * 1e6)
-        bf = r["prec"] == L.PORO_BF16X3_REFINE
-        tf32_peak = tensor_bf16_burst * (1.0 if bf else TF32_PER_BF16)
-        t_tc = tc_tile_flops(N, bf) * sw * n / (tf32_peak * 1e12)
-        t_min = max(t_alu, t_tc)
-        peak = (f_alu + f_tc + f_res) * n / t_min / 1e12
+        t_tc = tc_tile_flops(N, bf) * sw * n / (tc_peak * 1e12)
         tb = TRAFFIC_BYTES_PER_ELEMENT.get(("mixed_bf16" if bf else "mixed", N, r["sweeps"]))
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+        return {"bound": bound, "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"], "frac": b["frac"],
                 "traffic": tb * n if tb else None,
                 "kernel": f"stp_mixed_kernel<{N},{r['sweeps']}" + (",bf16>" if bf else ">"),
-                "flops_per_element": {"binary32_pipe": f_alu,
-                                      ("tensor_khat_bf16x3" if bf else "tensor_khat_tf32x3"): f_tc,
-                                      "residual": f_res},
-                "residual_macs_per_element": {"integer": int_macs, "double_word": dw_macs},
-                "tensor": {"issued_tflops": tc_tile_flops(N, bf) * sw * n / t / 1e12, "peak": tf32_peak,
-                           "dtype": "bf16" if bf else "tf32",
-                           "frac": (tc_tile_flops(N, bf) * sw * n / t / 1e12) / tf32_peak},
-                "bound_times_ms": {"binary32_pipe": 1e3 * t_alu, "tensor": 1e3 * t_tc},
-                "peak_source": f"binary32 pipe issue rate (152 SM x 128 lanes x {mhz:.0f} MHz): 1 instr per FMA, "
-                               f"{INT_MAC_SLOTS:g} slots per integer MAC (IMAD), "
-                               f"{DW_OPS_PER_MAC:g} instr per double-word MAC, overlapped with the Khat tiles on the "
-                               + (f"tensor cores at {tf32_peak:.0f} TFLOP/s bf16 (measured burst); " if bf else
-                                  f"tensor cores at {tf32_peak:.0f} TFLOP/s tf32 (measured bf16 burst x {TF32_PER_BF16:.3f}); ")
-                               + f"binary32 FMA peak {fp32_alu_peak_tflops(mhz):.1f} TFLOP/s"}
+                "peak_source": peaks_src + " (" + ("hbm_gbs" if bound == "hbm" else "bf16_tflops burst") + ")",
+                "terms": terms,
+                "model": {"frac": max(t_alu, t_tc) / t, "bound_times_ms": {"binary32_issue": 1e3 * t_alu,
+                                                                           "tensor_tiles": 1e3 * t_tc},
+                          "residual_macs_per_element": {"integer": int_macs, "double_word": dw_macs},
+                          "derivation": f"binary32 pipe issue at 152 SM x 128 lanes x {mhz:.0f} MHz: 1 slot per "
+                                        f"FMA, {INT_MAC_SLOTS:g} per integer MAC, {DW_OPS_PER_MAC:g} per "
+                                        "double-word MAC, overlapped with the issued tensor tiles at the measured "
+                                        "tensor peak; the kernel's own instruction mix, not a hardware roof"}}
 
     # headline: the faster mixed form among those within 1e-10 of the FP64
     # kernel on every element (or when the FP64 form did not run); else FP64
@@ -606,10 +675,7 @@ def run_ours(args):
         return
     cpu = None
     if world == 1 and not args.no_cpu:
-        rate, cores, k, el = cpu_oracle_rate(args, args.cpu_budget_s)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {k} elements of the N={args.degree} workload, dense equilibrated LU "
-                         f"(numpy/LAPACK float64), {el:.1f} s"}
+        cpu = cpu_baseline(args)
     forms_out = {}
     for name, r in res.items():
         forms_out[name] = {"value": job_rate(n, world, r["ms"] * 1e-3), "ms_per_step": r["ms"],

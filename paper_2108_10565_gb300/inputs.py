@@ -250,3 +250,29 @@ def uniform_box_mesh_for(n_target, extent=(20e3, 20e3, 10e3)):
     n = (2 * nz, 2 * nz, nz)
     return kuhn_box_mesh(n, lo=(0.0, 0.0, -extent[2]), hi=(extent[0], extent[1], 0.0),
                          periodic=(False, False, False), tags={"z+": 1})
+
+
+# receivers of the LOHp layout (Section "Layer over half-space"): at the free
+# surface, in the middle of the 500 m layer, 10 m below the interface and
+# 200 m below the 1010 m deep source, at horizontal offsets from the source
+LOH_RECEIVERS = np.array([
+    [0.0, 0.0, -0.5], [500.0, 0.0, -0.5], [1000.0, 0.0, -0.5], [1900.0, 0.0, -0.5],
+    [250.0, 0.0, -250.0], [1000.0, 0.0, -250.0], [500.0, 0.0, -510.0], [0.0, 0.0, -1210.0]])
+EXPLOSIVE_WEIGHTS = -np.r_[np.ones(3), np.zeros(6), -1.0, np.zeros(3)]
+
+
+def cfg3_mini_scenario(nz=8):
+    """The small clustered-LTS case: `layered_graded_mesh(nz)` (nz = 8: 16 x 16 x
+    8 boxes, 12,288 tets) with 32x grading, degree 3, rate-2 clusters capped at
+    6, the explosive source at 1010 m depth (Ricker f0 = 5 Hz, t0 = 0.25 s),
+    the 8 LOHp receivers, 20 steps of the largest cluster.  Initial DOFs are
+    seeded N(0, 1), so that every element carries data from the first tick
+    (the source alone reaches a few elements in this time)."""
+    mesh, mats = layered_graded_mesh(nz, grading=32.0)
+    ne = mesh["tets"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(SEED_LOH))
+    q0 = rng.standard_normal((ne, 13, 20))
+    return dict(mesh=mesh, materials=mats, N=3, max_clusters=6, n_cycles=20, Q0=q0,
+                source=dict(x=np.array([0.0, 0.0, -1010.0]), w=EXPLOSIVE_WEIGHTS.copy(), f0=5.0, t0=0.25,
+                            amplitude=1e9),
+                receivers=LOH_RECEIVERS.copy())

@@ -6,7 +6,7 @@ import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-ARGS = ["--impl", "reference", "--steps", "2", "--warmup", "1", "--degree", "2", "--n-elem", "50"]
+ARGS = ["--impl", "reference", "--steps", "2", "--warmup", "1", "--degree", "2", "--n-elem", "50", "--ref-elems", "256"]
 
 
 def _run(env_extra=None):
