@@ -74,6 +74,17 @@ typedef enum {
     PORO_FACE_ABSORBING = 2     /* no incoming waves (Section "Homogeneous full-space") */
 } poro_face;
 
+/* The linear hyperbolic system of a context.  Section "Other applications":
+ * the predictor and Algorithm 3 apply to any such system whose source matrix
+ * E is upper triangular; besides Biot's equations the library builds the
+ * damped Maxwell equations (eps E_t = curl H - sigma E, mu H_t = -curl E,
+ * quantities (E_x, E_y, E_z, H_x, H_y, H_z), E = diag(-sigma/eps x 3, 0 x 3))
+ * for the isolated-element predictor in binary64. */
+typedef enum {
+    PORO_SYSTEM_BIOT = 0,     /* 13 quantities, the paper's poroelastic system */
+    PORO_SYSTEM_MAXWELL = 1   /* 6 quantities, damped Maxwell */
+} poro_system;
+
 typedef enum {
     PORO_SOLVE_BLOCK = 0,   /* Algorithm 3: degree-block back-substitution */
     PORO_SOLVE_LU = 1       /* dense LU of the whole predictor system (comparator) */
@@ -90,6 +101,19 @@ typedef enum {
  * whose Khat rows are not integer rows over a common denominator with a sum
  * of |numerators| below 2^22 (the exact integer residual needs that). */
 poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out);
+
+/* poro_create for a given system.  PORO_SYSTEM_MAXWELL contexts support
+ * PORO_FP64 and the isolated-element calls (poro_set_isolated_maxwell,
+ * poro_set_dofs, poro_predict*, poro_get_predictor, poro_get_integrated,
+ * poro_flop_count); DOF arrays then have 6 quantities ([n][6][B] and
+ * [n][6][B][N+1]).  Meshes, the LU comparator and the autotuner return
+ * PORO_EUNSUPPORTED on them.  Errors: as poro_create, PORO_EUNSUPPORTED
+ * (unknown system, Maxwell with a mixed precision). */
+poro_status poro_create_system(int device, int degree_N, poro_precision precision, poro_system system,
+                               poro_ctx** out);
+
+/* System and number of quantities of the context. */
+poro_status poro_get_system(const poro_ctx* ctx, int32_t* system, int32_t* n_quantities);
 
 /* Release every device and host resource of the context (waits for queued
  * work first).  NULL is accepted and ignored. */
@@ -167,6 +191,16 @@ poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_
  * tetrahedron, unphysical material, dt <= 0), PORO_ENOMEM. */
 poro_status poro_set_isolated(poro_ctx* ctx, int64_t n_elem, const double* vert,
                               const poro_material* mat, const double* dt);
+
+/* Isolated damped-Maxwell elements (Section "Other applications"): like
+ * poro_set_isolated with mat[n][3] = (eps, mu, sigma) per element (eps > 0,
+ * mu > 0, sigma >= 0; host, copied).  Per element the library builds
+ * A^{j*} = dt sum_d (d xi_j / d x_d) A_d on the 12-entry pattern of the curl
+ * operator, e = -sigma dt / eps and (Z - e I)^{-1}.  Errors: PORO_EINVAL
+ * (degenerate element or material), PORO_EUNSUPPORTED (not a Maxwell
+ * context). */
+poro_status poro_set_isolated_maxwell(poro_ctx* ctx, int64_t n, const double* vert, const double* mat,
+                                      const double* dt);
 
 /* Copy DOFs Q[n_elem][13][B] (host) into the context.  Errors: PORO_ESTATE
  * before poro_set_isolated. */
@@ -273,6 +307,15 @@ poro_status poro_add_receiver(poro_ctx* ctx, const double xyz[3], int32_t* id_ou
  * collects the new seismogram samples. */
 poro_status poro_advance(poro_ctx* ctx, double t_end);
 
+/* poro_advance without CUDA graphs, timing every cluster's launches: the
+ * same cycles and results, and ms_out[C] (caller-owned, C = the context's
+ * cluster count) receives the GPU milliseconds spent in each cluster's
+ * predictor, buffer, corrector, source and receiver launches (CUDA events
+ * around each cluster's group of launches on the context stream).  The
+ * paper reports only whole-run LTS times (Section "Scaling"); this splits
+ * them.  Errors: as poro_advance, PORO_EINVAL (NULL ms_out). */
+poro_status poro_cluster_times(poro_ctx* ctx, double t_end, double* ms_out);
+
 /* Replay a CUDA graph of one cycle (default on) or enqueue every cycle's
  * launches from the host (off); results are identical. */
 poro_status poro_set_graphs(poro_ctx* ctx, int32_t on);
@@ -361,6 +404,31 @@ poro_status poro_autotune(poro_ctx* ctx, int64_t sample, int32_t* variant_out, d
 /* Select a predictor CTA-size variant explicitly (0 or 1). */
 poro_status poro_set_variant(poro_ctx* ctx, int32_t variant);
 
+/* Tile choices of the predictor kernels: choice = 6 * cta + layout, with cta
+ * the CTA-size variant (as poro_set_variant) and layout capping the operand
+ * buffers of the mixed kernel's tensor-core sweeps per degree block
+ * (A-tile buffers, Khat image slots): 0 (3, 3) = as many as fit (default),
+ * 1 (2, 3), 2 (1, 3), 3 (2, 2), 4 (1, 2), 5 (1, 1).  Fewer buffers serialise
+ * the star products, image copies and MMAs of the three directions; more
+ * buffers take shared memory the block may not have, so the kernel still
+ * uses only what fits.  Every choice gives bitwise the same predictor.
+ * Available: FP64 contexts layouts 0 only (choices 0 and 6), the bf16 form
+ * cta 0 only (choices 0..5), the tf32 form all 12. */
+#define PORO_TILE_CHOICES 12
+
+/* Autotuner over the available tile choices: times each on the first
+ * `sample` elements of the loaded population (<= 0: all; two warm-ups,
+ * three timed runs) and keeps the fastest for this context.  *choice_out
+ * (nullable) receives it, ms_out[PORO_TILE_CHOICES] (nullable) the mean
+ * milliseconds per run of each choice (-1 for choices not available).  The
+ * DOFs are kept; the predictor buffers are overwritten.  The paper has no
+ * counterpart (its kernels are generated per architecture).
+ * Errors: PORO_ESTATE (no population), PORO_EUNSUPPORTED (not Biot). */
+poro_status poro_autotune_tiles(poro_ctx* ctx, int64_t sample, int32_t* choice_out, double* ms_out);
+
+/* Select a tile choice explicitly.  Errors: PORO_EINVAL (not available). */
+poro_status poro_set_tiles(poro_ctx* ctx, int32_t choice);
+
 /* Floating-point operations one predictor of this context performs, counted
  * from the structural non-zeros the kernels touch (Khat blocks, the 54-entry
  * star pattern, the (N+1)^2 time solves): used for rooflines.  flops_out[0]
@@ -411,6 +479,17 @@ typedef struct {
 /* Server on `device` with a device-memory budget in bytes and at most
  * max_slots concurrently running requests. */
 poro_status poro_server_create(int device, size_t hbm_budget, int32_t max_slots, poro_server** out);
+
+/* Execution mode for requests admitted after the call.  on != 0 (the
+ * default): batched.  One executor thread advances the running requests in
+ * groups of equal degree, precision, refinement and cluster count; every
+ * tick's predictors of a group's requests are one kernel launch over all of
+ * their due elements, followed by each request's buffers, correctors, sources
+ * and receivers, one cycle captured as a CUDA graph and replayed; groups of
+ * different degrees run concurrently on their own streams.  on == 0: each
+ * request advances on its own thread, context and stream.  Results are
+ * identical in both modes and alone.  Errors: PORO_EINVAL (NULL server). */
+poro_status poro_server_set_batching(poro_server* s, int32_t on);
 /* Cancel queued and running requests, wait for the workers, free. */
 poro_status poro_server_destroy(poro_server* srv);
 const char* poro_server_last_error(poro_server* srv);

@@ -33,11 +33,12 @@ def element_operators(vert, mat, dt):
 
 
 def assemble_dense(N, Astar, Estar):
-    """Y of Eq. stp-lineq with the unrolling (p, k, r) -> (p*B + k)*T + r."""
+    """Y of Eq. stp-lineq with the unrolling (p, k, r) -> (p*B + k)*T + r
+    (any number of quantities: the size of E*)."""
     M = basis.mass_matrix(N)
     K = basis.stiffness_matrices(N)
     W, w, S, Kt = timebasis.time_matrices(N)
-    Y = np.kron(np.eye(NQ), np.kron(M, W - Kt))
+    Y = np.kron(np.eye(Estar.shape[0]), np.kron(M, W - Kt))
     Y -= np.kron(Estar, np.kron(M, S))
     for j in range(3):
         Y += np.kron(Astar[j], np.kron(K[j], S))
@@ -66,14 +67,14 @@ def equilibrate(Y):
 def predict_dense(N, Astar, Estar, Q0, return_factors=False):
     """Qt[q, l, s] by dense LU of Y (the oracle's definition): solve
     (R Y C) z = R r by LU with partial pivoting, Qt = C z."""
-    B, T = basis.n_modes(N), N + 1
+    B, T, nq = basis.n_modes(N), N + 1, Estar.shape[0]
     Y = assemble_dense(N, Astar, Estar)
     R, C = equilibrate(Y)
     lu = sla.lu_factor(Y * R[:, None] * C[None, :], check_finite=True)
     x = C * sla.lu_solve(lu, R * rhs_dense(N, Q0))
     if return_factors:
-        return x.reshape(NQ, B, T), (lu, R, C)
-    return x.reshape(NQ, B, T)
+        return x.reshape(nq, B, T), (lu, R, C)
+    return x.reshape(nq, B, T)
 
 
 def _common(N):
@@ -90,14 +91,15 @@ def predict_alg1(N, Astar, Estar, Q0):
     (d_pq Z_us - E*_pq d_us) Qt[q, m, s] = b[p, m, u], with b pulled from the
     already solved modes l > m through Eq. b_pmu."""
     B, T, Kh, Sinv_w, Z = _common(N)
-    Qt = np.zeros((NQ, B, T))
-    Ablk = np.kron(np.eye(NQ), Z) - np.kron(Estar, np.eye(T))
+    nq = Estar.shape[0]
+    Qt = np.zeros((nq, B, T))
+    Ablk = np.kron(np.eye(nq), Z) - np.kron(Estar, np.eye(T))
     for m in range(B - 1, -1, -1):
         b = np.outer(Q0[:, m], Sinv_w)
         for l in range(m + 1, B):
             for j in range(3):
                 b -= Kh[j][m, l] * (Astar[j] @ Qt[:, l, :])
-        Qt[:, m, :] = np.linalg.solve(Ablk, b.reshape(-1)).reshape(NQ, T)
+        Qt[:, m, :] = np.linalg.solve(Ablk, b.reshape(-1)).reshape(nq, T)
     return Qt
 
 
@@ -105,12 +107,13 @@ def predict_alg2(N, Astar, Estar, Q0):
     """Algorithm 2: unrolled over modes m and quantities p; E* = F + G with
     F diagonal and G strictly upper triangular."""
     B, T, Kh, Sinv_w, Z = _common(N)
+    nq = Estar.shape[0]
     F = np.diag(Estar)
     G = Estar - np.diag(F)
     b = Q0[:, :, None] * Sinv_w[None, None, :]
-    Qt = np.zeros((NQ, B, T))
+    Qt = np.zeros((nq, B, T))
     for m in range(B - 1, -1, -1):
-        for p in range(NQ - 1, -1, -1):
+        for p in range(nq - 1, -1, -1):
             Qt[p, m, :] = np.linalg.solve(Z - F[p] * np.eye(T), b[p, m, :])
             for o in range(p):
                 if G[o, p] != 0.0:
@@ -126,13 +129,14 @@ def predict_alg3(N, Astar, Estar, Q0):
     (degree blocks g = N..0, modes [o_g, o_g + d_g)); the green update is the
     pair of n-mode products A^{j*} x_1 Qt[:, blk, :] x_2 Khat^j[:, blk]."""
     B, T, Kh, Sinv_w, Z = _common(N)
+    nq = Estar.shape[0]
     F = np.diag(Estar)
     G = Estar - np.diag(F)
     b = Q0[:, :, None] * Sinv_w[None, None, :]
-    Qt = np.zeros((NQ, B, T))
+    Qt = np.zeros((nq, B, T))
     for g in range(N, -1, -1):
         blk = slice(basis.block_offset(g), basis.block_offset(g) + basis.block_size(g))
-        for p in range(NQ - 1, -1, -1):
+        for p in range(nq - 1, -1, -1):
             Zinv_T = np.linalg.inv(Z - F[p] * np.eye(T)).T
             Qt[p, blk, :] = b[p, blk, :] @ Zinv_T
             for o in range(p):

@@ -16,6 +16,7 @@ PORO_OK, PORO_EINVAL, PORO_ENOMEM, PORO_ECUDA, PORO_ETIMEOUT, PORO_ESTATE, PORO_
     0, -1, -2, -3, -4, -5, -6, -7)
 PORO_FP64, PORO_FP32_REFINE, PORO_BF16X3_REFINE = 0, 1, 2
 PORO_SOLVE_BLOCK, PORO_SOLVE_LU = 0, 1
+PORO_SYSTEM_BIOT, PORO_SYSTEM_MAXWELL = 0, 1
 
 _c = ctypes
 _i32, _i64, _dbl, _vp = _c.c_int32, _c.c_int64, _c.c_double, _c.c_void_p
@@ -37,6 +38,9 @@ PORO_REQ_QUEUED, PORO_REQ_RUNNING, PORO_REQ_DONE, PORO_REQ_FAILED, PORO_REQ_CANC
 # (name, restype, argtypes) for every symbol declared in include/poroader.h
 SIGNATURES = [
     ("poro_create", _i32, [_c.c_int, _c.c_int, _c.c_int, _c.POINTER(_vp)]),
+    ("poro_create_system", _i32, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_vp)]),
+    ("poro_get_system", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32)]),
+    ("poro_set_isolated_maxwell", _i32, [_vp, _i64, _vp, _vp, _vp]),
     ("poro_destroy", _i32, [_vp]),
     ("poro_last_error", _c.c_char_p, [_vp]),
     ("poro_get_info", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32), _c.POINTER(_i64)]),
@@ -65,6 +69,7 @@ SIGNATURES = [
     ("poro_add_point_source", _i32, [_vp, _vp, _vp, _dbl, _dbl, _dbl]),
     ("poro_add_receiver", _i32, [_vp, _vp, _c.POINTER(_i32)]),
     ("poro_advance", _i32, [_vp, _dbl]),
+    ("poro_cluster_times", _i32, [_vp, _dbl, _vp]),
     ("poro_correct", _i32, [_vp, _i32]),
     ("poro_get_dofs", _i32, [_vp, _vp]),
     ("poro_get_seismogram", _i32, [_vp, _i32, _i64, _vp, _vp, _c.POINTER(_i64)]),
@@ -72,9 +77,12 @@ SIGNATURES = [
     ("poro_flux_matrices", _i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
     ("poro_autotune", _i32, [_vp, _i64, _c.POINTER(_i32), _vp]),
     ("poro_set_variant", _i32, [_vp, _i32]),
+    ("poro_autotune_tiles", _i32, [_vp, _i64, _c.POINTER(_i32), _vp]),
+    ("poro_set_tiles", _i32, [_vp, _i32]),
     ("poro_set_graphs", _i32, [_vp, _i32]),
     ("poro_server_create", _i32, [_c.c_int, _c.c_size_t, _i32, _c.POINTER(_vp)]),
     ("poro_server_destroy", _i32, [_vp]),
+    ("poro_server_set_batching", _i32, [_vp, _i32]),
     ("poro_server_last_error", _c.c_char_p, [_vp]),
     ("poro_submit", _i32, [_vp, _c.POINTER(poro_scenario), _c.POINTER(_c.c_uint64)]),
     ("poro_poll", _i32, [_vp, _c.c_uint64, _c.POINTER(_i32), _pd]),
@@ -133,10 +141,19 @@ def _f64(a):
 
 
 # ------------------------------------------------------------ same-name wrappers
-def poro_create(device, degree_N, precision=PORO_FP64):
+def poro_create(device, degree_N, precision=PORO_FP64, system=PORO_SYSTEM_BIOT):
     h = _vp()
-    _check(lib().poro_create(device, degree_N, precision, ctypes.byref(h)))
+    if system == PORO_SYSTEM_BIOT:
+        _check(lib().poro_create(device, degree_N, precision, ctypes.byref(h)))
+    else:
+        _check(lib().poro_create_system(device, degree_N, precision, system, ctypes.byref(h)))
     return h.value
+
+
+def poro_get_system(ctx):
+    s, q = _i32(), _i32()
+    _check(lib().poro_get_system(ctx, ctypes.byref(s), ctypes.byref(q)), ctx)
+    return s.value, q.value
 
 
 def poro_destroy(ctx):
@@ -189,6 +206,12 @@ def poro_set_isolated(ctx, vert, mat, dt):
     return _check(lib().poro_set_isolated(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
 
 
+def poro_set_isolated_maxwell(ctx, vert, mat, dt):
+    """mat[n][3] = (eps, mu, sigma) per element."""
+    v, m, d = _f64(vert), _f64(mat), _f64(dt)
+    return _check(lib().poro_set_isolated_maxwell(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
+
+
 def poro_set_dofs(ctx, Q):
     q = _f64(Q)
     return _check(lib().poro_set_dofs(ctx, _ptr(q)), ctx)
@@ -200,18 +223,20 @@ def poro_predict(ctx, cluster=-1, solver=PORO_SOLVE_BLOCK):
 
 def poro_get_predictor(ctx, first, count, out=None):
     N, _, _ = poro_get_info(ctx)
+    nq = poro_get_system(ctx)[1]
     B, T = (N + 1) * (N + 2) * (N + 3) // 6, N + 1
     if out is None:
-        out = np.empty((count, 13, B, T))
+        out = np.empty((count, nq, B, T))
     _check(lib().poro_get_predictor(ctx, first, count, _ptr(out)), ctx)
     return out
 
 
 def poro_get_integrated(ctx, first, count, out=None):
     N, _, _ = poro_get_info(ctx)
+    nq = poro_get_system(ctx)[1]
     B = (N + 1) * (N + 2) * (N + 3) // 6
     if out is None:
-        out = np.empty((count, 13, B))
+        out = np.empty((count, nq, B))
     _check(lib().poro_get_integrated(ctx, first, count, _ptr(out)), ctx)
     return out
 
@@ -300,6 +325,14 @@ def poro_advance(ctx, t_end):
     return _check(lib().poro_advance(ctx, t_end), ctx)
 
 
+def poro_cluster_times(ctx, t_end, n_clusters):
+    """poro_advance without graphs; returns the GPU ms of each of the
+    context's n_clusters clusters' launches."""
+    ms = np.zeros(max(1, n_clusters))
+    _check(lib().poro_cluster_times(ctx, t_end, _ptr(ms)), ctx)
+    return ms
+
+
 def poro_correct(ctx, cluster=-1):
     return _check(lib().poro_correct(ctx, cluster), ctx)
 
@@ -355,6 +388,21 @@ def poro_set_variant(ctx, variant):
     return _check(lib().poro_set_variant(ctx, variant), ctx)
 
 
+PORO_TILE_CHOICES = 12
+
+
+def poro_autotune_tiles(ctx, sample=0):
+    """Returns (chosen tile choice, ms per choice; -1 where not available)."""
+    c = _i32()
+    ms = np.zeros(PORO_TILE_CHOICES)
+    _check(lib().poro_autotune_tiles(ctx, sample, ctypes.byref(c), _ptr(ms)), ctx)
+    return c.value, ms
+
+
+def poro_set_tiles(ctx, choice):
+    return _check(lib().poro_set_tiles(ctx, choice), ctx)
+
+
 def poro_flop_count(ctx, refine_sweeps=0):
     f = (ctypes.c_double * 3)()
     _check(lib().poro_flop_count(ctx, refine_sweeps, f), ctx)
@@ -376,6 +424,10 @@ def poro_server_create(device, hbm_budget, max_slots):
 
 def poro_server_destroy(srv):
     return lib().poro_server_destroy(srv)
+
+
+def poro_server_set_batching(srv, on):
+    return _srv_check(lib().poro_server_set_batching(srv, 1 if on else 0), srv)
 
 
 def make_scenario(N, mesh, materials, t_end, precision=PORO_FP64, max_clusters=1, refine_sweeps=1, cfl_c=0.5,

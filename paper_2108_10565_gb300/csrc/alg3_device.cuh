@@ -18,16 +18,41 @@ namespace poro {
 
 __host__ __device__ constexpr int bank_stride(int n, int T) { return n + ((T - n % 32) + 32) % 32; }
 
-template <int N>
+// The linear system of the predictor: its quantities, the union pattern of
+// its reference Jacobians and the structure of its source matrix E (upper
+// triangular, Section "Block-wise back-substitution"): per mode the time
+// solves are NPLAIN rows with Z^{-1} (E_pp = 0), NSHIFT rows with
+// (Z - e I)^{-1} and no coupling, and NPAIR pairs: src solved with
+// (Z - e I)^{-1}, then b_dst += g Q_src, then dst with Z^{-1}.
+struct BiotSystem {  // Biot's equations: G couples u_f -> u, v_f -> v, w_f -> w
+    static constexpr int NQ = poro::NQ, NNZ = STAR_NNZ, NPLAIN = 7, NSHIFT = 0, NPAIR = 3;
+    PORO_HD static constexpr int row(int n) { return star_row(n); }
+    PORO_HD static constexpr int col(int n) { return star_col(n); }
+    PORO_HD static constexpr int plain(int k) { return k < 6 ? k : QP; }
+    PORO_HD static constexpr int shifted(int) { return 0; }
+    PORO_HD static constexpr int pair_src(int i) { return QUF + i; }
+    PORO_HD static constexpr int pair_dst(int i) { return QU + i; }
+};
+struct MaxwellSystem {  // damped Maxwell: E diagonal, -sigma/eps on the electric rows
+    static constexpr int NQ = maxwell::NQ, NNZ = maxwell::STAR_NNZ, NPLAIN = 3, NSHIFT = 3, NPAIR = 0;
+    PORO_HD static constexpr int row(int n) { return maxwell::star_row(n); }
+    PORO_HD static constexpr int col(int n) { return maxwell::star_col(n); }
+    PORO_HD static constexpr int plain(int k) { return 3 + k; }
+    PORO_HD static constexpr int shifted(int k) { return k; }
+    PORO_HD static constexpr int pair_src(int) { return 0; }
+    PORO_HD static constexpr int pair_dst(int) { return 0; }
+};
+
+template <int N, int NQ_ = NQ>
 struct Alg3Shape {
     static constexpr int B = n_modes(N);
     static constexpr int T = N + 1;
-    static constexpr int QBT = NQ * B * T;                 // dense size (global layout)
+    static constexpr int QBT = NQ_ * B * T;                // dense size (global layout)
     static constexpr int QS = bank_stride(B * T, T);       // shared quantity stride
-    static constexpr int SQ = NQ * QS;                     // shared size of b / Q
+    static constexpr int SQ = NQ_ * QS;                    // shared size of b / Q
     static constexpr int DMAX = block_size(N);
     static constexpr int XSMAX = bank_stride(DMAX * T, T);
-    static constexpr int PT = NQ * T;                      // (p, u) pairs of one mode
+    static constexpr int PT = NQ_ * T;                     // (p, u) pairs of one mode
     static constexpr int PUL = (PT + 31) / 32;             // pairs per lane
 };
 
@@ -59,10 +84,10 @@ __device__ __forceinline__ void solve_row(Real* row, const Real* Zi) {
 }
 
 // b[p,l,u] = (S^{-1} w)_u q0[p,l] with (S^{-1} w)_u = (2u+1)(-1)^u
-template <int N, int NT, class Real, class In>
+template <int N, int NT, class Real, class In, int NQ_ = NQ>
 __device__ __forceinline__ void init_rhs(Real* bq, const In* q0) {
-    using S = Alg3Shape<N>;
-    for (int i = threadIdx.x; i < NQ * S::B; i += NT) {
+    using S = Alg3Shape<N, NQ_>;
+    for (int i = threadIdx.x; i < NQ_ * S::B; i += NT) {
         const Real v = (Real)q0[i];
         const int p = i / S::B, l = i % S::B;
         Real* row = bq + p * S::QS + l * S::T;
@@ -72,14 +97,15 @@ __device__ __forceinline__ void init_rhs(Real* bq, const In* q0) {
 }
 
 // In-place sweep: on entry bq holds b, on exit the solution Q.  X is a
-// scratch area of JX * 13 * XSMAX values in shared memory; star[3][54] the
-// element's reference Jacobians on the union pattern; zuf = (Z - e I)^{-1},
-// zin = Z^{-1}; gcoup = E*_{u,uf}.  JX directions are handled per pass
-// (1 or 3).  Ends with a barrier.
-template <int N, int NT, class Real, int JX>
+// scratch area of JX * Sys::NQ * XSMAX values in shared memory; star[3][NNZ]
+// the element's reference Jacobians on the union pattern; zuf = (Z - e I)^{-1},
+// zin = Z^{-1}; gcoup = the coupling entry g of E* (Biot: E*_{u,uf}).  JX
+// directions are handled per pass (1 or 3).  Ends with a barrier.
+template <int N, int NT, class Real, int JX, class Sys = BiotSystem>
 __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf, const Real* zin,
                            const Real gcoup, const KhatBlocks<Real>& K) {
-    using S = Alg3Shape<N>;
+    constexpr int NQ = Sys::NQ, STAR_NNZ = Sys::NNZ;
+    using S = Alg3Shape<N, NQ>;
     constexpr int T = S::T, QS = S::QS, PT = S::PT, PUL = S::PUL, NW = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int lp[PUL], lu[PUL];
@@ -92,17 +118,20 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
 #pragma unroll 1
     for (int g = N; g >= 0; --g) {
         const int o = block_offset(g), d = block_size(g);
-        // time solves of block g: 7 plain rows (6 stresses, p) and 3 coupled
-        // pairs (u_f then u, v_f then v, w_f then w) per mode
-        for (int it = tid; it < 10 * d; it += NT) {
+        // time solves of block g, per mode: the plain rows, the shifted rows,
+        // and the coupled pairs (Biot: 6 stresses and p; u_f then u, v_f
+        // then v, w_f then w)
+        constexpr int NKIND = Sys::NPLAIN + Sys::NSHIFT + Sys::NPAIR;
+        for (int it = tid; it < NKIND * d; it += NT) {
             const int kind = it / d, m = o + it % d;
-            if (kind < 7) {
-                const int p = kind < 6 ? kind : QP;
-                solve_row<T>(bq + p * QS + m * T, zin);
+            if (kind < Sys::NPLAIN) {
+                solve_row<T>(bq + Sys::plain(kind) * QS + m * T, zin);
+            } else if (kind < Sys::NPLAIN + Sys::NSHIFT) {
+                solve_row<T>(bq + Sys::shifted(kind - Sys::NPLAIN) * QS + m * T, zuf);
             } else {
-                const int i = kind - 7;
-                Real* rf = bq + (QUF + i) * QS + m * T;
-                Real* rv = bq + (QU + i) * QS + m * T;
+                const int i = kind - Sys::NPLAIN - Sys::NSHIFT;
+                Real* rf = bq + Sys::pair_src(i) * QS + m * T;
+                Real* rv = bq + Sys::pair_dst(i) * QS + m * T;
                 solve_row<T>(rf, zuf);
 #pragma unroll
                 for (int u = 0; u < T; ++u) rv[u] = fma(gcoup, rf[u], rv[u]);
@@ -128,7 +157,7 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
                     for (int p = 0; p < NQ; ++p) acc[p] = Real(0);
 #pragma unroll
                     for (int n = 0; n < STAR_NNZ; ++n)
-                        acc[star_row(n)] = fma(sj[n], qv[star_col(n)], acc[star_row(n)]);
+                        acc[Sys::row(n)] = fma(sj[n], qv[Sys::col(n)], acc[Sys::row(n)]);
                     Real* xj = X + jj * NQ * S::XSMAX + ml * T + u;
 #pragma unroll
                     for (int p = 0; p < NQ; ++p) xj[p * XS] = acc[p];

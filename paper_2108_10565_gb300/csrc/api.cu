@@ -21,6 +21,8 @@ using poro::NQ;
 struct poro_ctx {
     int device = 0;
     int N = 0, B = 0, T = 0;
+    int system = PORO_SYSTEM_BIOT;
+    int nq = NQ;                   // quantities of the system (13 Biot, 6 damped Maxwell)
     poro_precision prec = PORO_FP64;
     cudaStream_t stream = nullptr;
     // copy streams and chunk events of poro_predict_host (created on first use)
@@ -185,7 +187,7 @@ void free_reference(poro_ctx* c) {
 
 namespace poro {
 bool ctx_view(const poro_ctx* c, CtxView& v) {
-    if (!c || !c->d_econst) return false;
+    if (!c || !c->d_econst || c->system != PORO_SYSTEM_BIOT) return false;
     v.device = c->device;
     v.N = c->N;
     v.n_elem = c->n_elem;
@@ -256,8 +258,17 @@ static bool rational_of(double x, int64_t& num, int64_t& den) {
 }
 
 poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out) {
+    return poro_create_system(device, degree_N, precision, PORO_SYSTEM_BIOT, out);
+}
+
+poro_status poro_create_system(int device, int degree_N, poro_precision precision, poro_system system,
+                               poro_ctx** out) {
     if (!out) return fail(nullptr, PORO_EINVAL, "poro_create: out is NULL");
     *out = nullptr;
+    if (system != PORO_SYSTEM_BIOT && system != PORO_SYSTEM_MAXWELL)
+        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: unknown system");
+    if (system == PORO_SYSTEM_MAXWELL && precision != PORO_FP64)
+        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: the damped Maxwell system is built in FP64 only");
     if (degree_N < 1 || degree_N > poro::MAX_N)
         return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: degree N must be in 1..6");
     if (precision != PORO_FP64 && precision != PORO_FP32_REFINE && precision != PORO_BF16X3_REFINE)
@@ -272,6 +283,8 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
     c->device = device;
     c->N = degree_N;
     c->prec = precision;
+    c->system = system;
+    c->nq = system == PORO_SYSTEM_MAXWELL ? poro::maxwell::NQ : NQ;
     c->refine = 1;  // one sweep reaches the 1e-10 goal in both mixed forms (measured)
     std::string err;
     if (!poro::reference_data(degree_N, c->ref, err)) {
@@ -280,7 +293,8 @@ poro_status poro_create(int device, int degree_N, poro_precision precision, poro
     }
     c->B = c->ref.B;
     c->T = c->ref.T;
-    c->stride = poro::elem_const_stride(degree_N);
+    c->stride = system == PORO_SYSTEM_MAXWELL ? poro::maxwell::elem_const_stride(degree_N)
+                                              : poro::elem_const_stride(degree_N);
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -563,7 +577,7 @@ poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_
 }
 
 static poro_status upload_population(poro_ctx* c, int64_t n, const std::vector<double>& ec) {
-    const size_t nd = (size_t)n * NQ * c->B;
+    const size_t nd = (size_t)n * c->nq * c->B;
     cudaError_t e;
     if ((e = upload((void**)&c->d_econst, ec.data(), ec.size() * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void**)&c->d_q0, nd * sizeof(double) + 16)) != cudaSuccess ||
@@ -580,6 +594,8 @@ static poro_status upload_population(poro_ctx* c, int64_t n, const std::vector<d
 poro_status poro_set_isolated(poro_ctx* c, int64_t n, const double* vert, const poro_material* mat,
                               const double* dt) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT)
+        return fail(c, PORO_EUNSUPPORTED, "poro_set_isolated: Biot materials on a context of another system");
     if (n < 0 || (n > 0 && (!vert || !mat || !dt))) return fail(c, PORO_EINVAL, "poro_set_isolated: bad argument");
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
@@ -594,12 +610,40 @@ poro_status poro_set_isolated(poro_ctx* c, int64_t n, const double* vert, const 
     return upload_population(c, n, ec);
 }
 
+poro_status poro_set_isolated_maxwell(poro_ctx* c, int64_t n, const double* vert, const double* mat,
+                                      const double* dt) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated_maxwell: ctx is NULL");
+    if (c->system != PORO_SYSTEM_MAXWELL)
+        return fail(c, PORO_EUNSUPPORTED, "poro_set_isolated_maxwell: context is not a damped Maxwell context");
+    if (n < 0 || (n > 0 && (!vert || !mat || !dt)))
+        return fail(c, PORO_EINVAL, "poro_set_isolated_maxwell: bad argument");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    c->mesh_mode = false;
+    std::vector<double> ec((size_t)n * c->stride);
+    for (int64_t i = 0; i < n; ++i) {
+        std::string err;
+        if (!poro::maxwell_element_constants(c->ref, vert + 12 * i, mat + 3 * i, dt[i], ec.data() + (size_t)i * c->stride,
+                                             err))
+            return fail(c, PORO_EINVAL, "poro_set_isolated_maxwell: element " + std::to_string(i) + ": " + err);
+    }
+    return upload_population(c, n, ec);
+}
+
+poro_status poro_get_system(const poro_ctx* c, int32_t* system, int32_t* n_quantities) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_system: ctx is NULL");
+    if (system) *system = c->system;
+    if (n_quantities) *n_quantities = c->nq;
+    return PORO_OK;
+}
+
 poro_status poro_set_dofs(poro_ctx* c, const double* Q) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_dofs: ctx is NULL");
     if (!c->d_econst) return fail(c, PORO_ESTATE, "poro_set_dofs: no element population loaded");
     if (c->n_elem > 0 && !Q) return fail(c, PORO_EINVAL, "poro_set_dofs: Q is NULL");
     cudaSetDevice(c->device);
-    cudaError_t e = cudaMemcpyAsync(c->d_q0, Q, (size_t)c->n_elem * NQ * c->B * sizeof(double),
+    cudaError_t e = cudaMemcpyAsync(c->d_q0, Q, (size_t)c->n_elem * c->nq * c->B * sizeof(double),
                                     cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "poro_set_dofs");
     e = cudaStreamSynchronize(c->stream);
@@ -613,6 +657,8 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     const double* ec = c->d_econst + first * c->stride;
     int rc = 0;
     if (solver == PORO_SOLVE_LU) {
+        if (c->system != PORO_SYSTEM_BIOT)
+            return fail(c, PORO_EUNSUPPORTED, "predict (LU): the dense-LU comparator is built for Biot's system");
         if (count > 0 && (first < c->lu_first || first + count > c->lu_first + c->lu_count))
             return fail(c, PORO_ESTATE, "predict (LU): elements not factored; call poro_lu_factor first");
         rc = poro::launch_lu_solve(c->lref, count, c->lu, first - c->lu_first, q0, ec, qt, iout, st);
@@ -620,7 +666,9 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
         return PORO_OK;
     }
     if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
-    if (c->prec == PORO_FP64) {
+    if (c->system == PORO_SYSTEM_MAXWELL) {
+        rc = poro::launch_stp_fp64_maxwell(c->dref, nullptr, count, q0, ec, qt, iout, st);
+    } else if (c->prec == PORO_FP64) {
         rc = poro::launch_stp_fp64(c->dref, nullptr, count, q0, ec, qt, iout, st, c->variant);
     } else {
         rc = poro::launch_stp_mixed(c->mref, c->refine, nullptr, count, q0, ec, qt, iout, st, c->variant);
@@ -683,7 +731,7 @@ poro_status poro_predict_host(poro_ctx* c, const double* q0_host, double* I_out,
     }
     // nothing queued earlier on the context stream may still use the buffers
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "poro_predict_host");
-    const size_t per = (size_t)NQ * c->B;
+    const size_t per = (size_t)c->nq * c->B;
     for (int64_t i = 0; i < nchunks; ++i) {
         const int64_t first = i * chunk, cnt = std::min(chunk, n - first);
         if ((e = cudaMemcpyAsync(c->d_q0 + first * per, q0_host + first * per, cnt * per * sizeof(double),
@@ -721,6 +769,7 @@ poro_status poro_lu_bytes(int degree_N, int64_t count, size_t* bytes) {
 
 poro_status poro_lu_factor(poro_ctx* c, int64_t first, int64_t count) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_lu_factor: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_lu_factor: the dense-LU comparator is built for Biot's system");
     if (!c->d_econst) return fail(c, PORO_ESTATE, "poro_lu_factor: no element population loaded");
     if (first < 0 || count < 0 || first + count > c->n_elem || count > 65535)
         return fail(c, PORO_EINVAL, "poro_lu_factor: element range outside the population (or > 65535)");
@@ -816,26 +865,28 @@ static poro_status copy_out(poro_ctx* c, const double* src, int64_t first, int64
 }
 
 poro_status poro_get_predictor(poro_ctx* c, int64_t first, int64_t count, double* out) {
-    return copy_out(c, c ? c->d_qt : nullptr, first, count, c ? (size_t)NQ * c->B * c->T : 0, out,
+    return copy_out(c, c ? c->d_qt : nullptr, first, count, c ? (size_t)c->nq * c->B * c->T : 0, out,
                     "poro_get_predictor");
 }
 
 poro_status poro_get_integrated(poro_ctx* c, int64_t first, int64_t count, double* out) {
-    return copy_out(c, c ? c->d_iout : nullptr, first, count, c ? (size_t)NQ * c->B : 0, out,
+    return copy_out(c, c ? c->d_iout : nullptr, first, count, c ? (size_t)c->nq * c->B : 0, out,
                     "poro_get_integrated");
 }
 
 poro_status poro_flop_count(const poro_ctx* c, int32_t refine_sweeps, double* f) {
     if (!c || !f) return fail(nullptr, PORO_EINVAL, "poro_flop_count: NULL argument");
-    const double B = c->B, T = c->T;
-    // S3: 13 B rows of T x T time solves + the 3 G couplings per mode
-    const double s3 = 2.0 * NQ * B * T * T + 2.0 * 3 * B * T;
-    // S4a: 54-entry star products of all modes of degree >= 1, 3 directions
-    const double s4a = 2.0 * 3 * poro::STAR_NNZ * (B - 1) * T;
-    // S4b: structural non-zeros of the Khat blocks, each applied to 13 T columns
-    const double s4b = 2.0 * (double)c->ref.khat_block_nnz * NQ * T;
+    const double B = c->B, T = c->T, nq = c->nq;
+    const bool mx = c->system == PORO_SYSTEM_MAXWELL;
+    const double nnz = mx ? poro::maxwell::STAR_NNZ : poro::STAR_NNZ, npair = mx ? 0 : 3;
+    // S3: nq B rows of T x T time solves + the G couplings per mode (Biot: 3)
+    const double s3 = 2.0 * nq * B * T * T + 2.0 * npair * B * T;
+    // S4a: star products (Biot 54, Maxwell 12 entries) of all modes of degree >= 1, 3 directions
+    const double s4a = 2.0 * 3 * nnz * (B - 1) * T;
+    // S4b: structural non-zeros of the Khat blocks, each applied to nq T columns
+    const double s4b = 2.0 * (double)c->ref.khat_block_nnz * nq * T;
     // S1 (scaling of Q0) and S5 (time integration)
-    const double s15 = NQ * B * T + NQ * B;
+    const double s15 = nq * B * T + nq * B;
     const double alg3 = s3 + s4a + s4b + s15;
     f[0] = alg3;
     f[1] = alg3 * (1 + refine_sweeps);
@@ -849,6 +900,7 @@ poro_status poro_flop_count(const poro_ctx* c, int32_t refine_sweeps, double* f)
 poro_status poro_set_mesh(poro_ctx* c, int64_t n_vert, const double* xyz, int64_t n_elem, const int64_t* tet,
                           const int64_t* nb, const int32_t* face_tag) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_mesh: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_set_mesh: meshes and time stepping are built for Biot's system");
     if (n_vert <= 0 || n_elem <= 0 || !xyz || !tet || !nb || !face_tag)
         return fail(c, PORO_EINVAL, "poro_set_mesh: empty mesh or NULL array");
     for (int64_t i = 0; i < 4 * n_elem; ++i) {
@@ -1252,47 +1304,137 @@ poro_status poro_add_receiver(poro_ctx* c, const double xyz[3], int32_t* id_out)
 // Ticks inside the kernels are relative to the cycle (only their residues
 // modulo 2^c matter); the absolute tick for the sources is read from
 // d_tick, which the cycle advances at its end.
-static int enqueue_cycle(poro_ctx* c, const int64_t* d_re, const double* d_rp, double* d_seis, int64_t cap,
-                         int32_t* d_cnt) {
+// One tick k of the cycle for context c on stream st: predictors of the
+// clusters that start a step at k (skipped when a batched launch over
+// several runs already did them: predict = false), LTS buffers, correctors of
+// the clusters whose step ends at k + 1, point sources and receivers.
+// (prof, nullable: an event pair recorded around each cluster's launches,
+// for poro_cluster_times)
+struct ClusterEvent {
+    int cl;
+    cudaEvent_t a, b;
+};
+static int mark(std::vector<ClusterEvent>* prof, int cl, bool begin, cudaStream_t st) {
+    if (!prof) return 0;
+    if (begin) {
+        ClusterEvent ev{cl, nullptr, nullptr};
+        cudaError_t e = cudaEventCreate(&ev.a);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.a, st);
+        prof->push_back(ev);
+        return (int)e;
+    }
+    return (int)cudaEventRecord(prof->back().b, st);
+}
+
+static int enqueue_tick(poro_ctx* c, int64_t k, bool predict, const double* d_rp, double* d_seis, int64_t cap,
+                        int32_t* d_cnt, cudaStream_t st, std::vector<ClusterEvent>* prof = nullptr) {
     const int C = c->C;
-    const int64_t cycle = (int64_t)1 << (C - 1);
     const int nrec = (int)c->rec_elem.size();
     const bool want_qt = C > 1;
     int rc = 0;
-    for (int64_t k = 0; k < cycle && rc == 0; ++k) {
-        for (int cl = 0; cl < C && rc == 0; ++cl) {
-            if (k % ((int64_t)1 << cl) || c->cl_elems[cl].empty()) continue;
-            const int32_t* el = C > 1 ? c->d_cl_elems[cl] : nullptr;
-            const int64_t cnt = (int64_t)c->cl_elems[cl].size();
-            if (c->prec == PORO_FP64)
-                rc = poro::launch_stp_fp64(c->dref, el, cnt, c->d_q0, c->d_econst, want_qt ? c->d_qt : nullptr,
-                                           c->d_iout, c->stream, c->variant);
-            else
-                rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
-                                            want_qt ? c->d_qt : nullptr, c->d_iout, c->stream, c->variant);
-            if (rc == 0 && C > 1)
-                rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, c->stream);
-        }
+    for (int cl = 0; cl < C && rc == 0; ++cl) {
+        if (k % ((int64_t)1 << cl) || c->cl_elems[cl].empty()) continue;
+        rc = mark(prof, cl, true, st);
+        const int32_t* el = C > 1 ? c->d_cl_elems[cl] : nullptr;
+        const int64_t cnt = (int64_t)c->cl_elems[cl].size();
+        if (predict && c->prec == PORO_FP64)
+            rc = poro::launch_stp_fp64(c->dref, el, cnt, c->d_q0, c->d_econst, want_qt ? c->d_qt : nullptr,
+                                       c->d_iout, st, c->variant);
+        else if (predict)
+            rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
+                                        want_qt ? c->d_qt : nullptr, c->d_iout, st, c->variant);
+        if (rc == 0 && C > 1)
+            rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, st);
+        if (rc == 0) rc = mark(prof, cl, false, st);
+    }
+    {
         for (int cl = 0; cl < C && rc == 0; ++cl) {
             const int64_t len = (int64_t)1 << cl;
             if ((k + 1) % len || c->cl_elems[cl].empty()) continue;
+            rc = mark(prof, cl, true, st);
             poro::CorrectorData d = c->cd;
             d.tick = k;
-            rc = poro::launch_corrector(d, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(),
-                                        c->stream);
+            rc = poro::launch_corrector(d, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(), st);
             for (auto& src : c->sources)
                 if (rc == 0 && c->h_cl[src.elem] == cl)
                     rc = poro::launch_point_source_tick(c->N, c->d_q0, src.elem, src.d_coef, src.f0, src.t0, c->dt, len,
-                                                        k, c->d_tick, c->stream);
+                                                        k, c->d_tick, st);
             for (int r = 0; r < nrec && rc == 0; ++r)
                 if (c->h_cl[c->rec_elem[r]] == cl)
                     rc = poro::launch_receiver_count(c->N, c->d_q0, c->rec_elem[r], d_rp + (size_t)r * c->B,
-                                                     d_seis + (size_t)r * cap * NQ, d_cnt + r, c->stream);
+                                                     d_seis + (size_t)r * cap * NQ, d_cnt + r, st);
+            if (rc == 0) rc = mark(prof, cl, false, st);
         }
     }
-    if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
-    (void)d_re;
     return rc;
+}
+
+static int enqueue_cycle(poro_ctx* c, const double* d_rp, double* d_seis, int64_t cap, int32_t* d_cnt) {
+    const int64_t cycle = (int64_t)1 << (c->C - 1);
+    int rc = 0;
+    for (int64_t k = 0; k < cycle && rc == 0; ++k) rc = enqueue_tick(c, k, true, d_rp, d_seis, cap, d_cnt, c->stream);
+    if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
+    return rc;
+}
+
+// Before `ticks` ticks of c on stream st: the device tick counter and the
+// receiver staging buffers (kept across calls, grown only when a call needs
+// more samples).
+static poro_status prepare_advance(poro_ctx* c, int64_t ticks, cudaStream_t st, const char* who) {
+    const int nrec = (int)c->rec_elem.size();
+    cudaError_t er = cudaSuccess;
+    if (!c->d_tick && (er = cudaMalloc((void**)&c->d_tick, sizeof(int64_t))) != cudaSuccess) return cuda_fail(c, er, who);
+    if ((er = cudaMemcpyAsync(c->d_tick, &c->tick, sizeof(int64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, er, who);
+    if (nrec > 0) {
+        if (c->rp_n != (size_t)nrec) {
+            dfree(c->d_rp);
+            dfree(c->d_cnt);
+            c->rp_n = 0;
+            if ((er = upload((void**)&c->d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
+                (er = cudaMalloc((void**)&c->d_cnt, nrec * sizeof(int32_t))) != cudaSuccess)
+                return cuda_fail(c, er, who);
+            c->rp_n = nrec;
+            dfree(c->d_seis);
+            c->seis_cap = 0;
+        }
+        if (c->seis_cap < ticks) {
+            dfree(c->d_seis);
+            c->seis_cap = 0;
+            if ((er = cudaMalloc((void**)&c->d_seis, (size_t)nrec * ticks * NQ * sizeof(double))) != cudaSuccess)
+                return cuda_fail(c, er, who);
+            c->seis_cap = ticks;
+        }
+        if ((er = cudaMemsetAsync(c->d_cnt, 0, nrec * sizeof(int32_t), st)) != cudaSuccess) return cuda_fail(c, er, who);
+    }
+    return PORO_OK;
+}
+
+// Receiver samples of the advance to the host staging buffer (asynchronous on st).
+static cudaError_t stage_seismograms(poro_ctx* c, cudaStream_t st) {
+    const int nrec = (int)c->rec_elem.size();
+    if (nrec == 0) return cudaSuccess;
+    c->h_seis.resize((size_t)nrec * c->seis_cap * NQ);
+    return cudaMemcpyAsync(c->h_seis.data(), c->d_seis, c->h_seis.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+}
+
+// After the stream of an advance of `ticks` ticks finished: append the staged
+// receiver samples and move the clock.
+static void finish_advance(poro_ctx* c, int64_t ticks) {
+    const int nrec = (int)c->rec_elem.size();
+    const std::vector<double>& h = c->h_seis;
+    const int64_t cap = c->seis_cap;
+    for (int r = 0; r < nrec; ++r) {
+        const int cl = c->h_cl[c->rec_elem[r]];
+        const int64_t len = (int64_t)1 << cl, ns = ticks / len;
+        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * cap * NQ,
+                            h.begin() + ((size_t)r * cap + ns) * NQ);
+        for (int64_t j = 1; j <= ns; ++j) c->seis_t[r].push_back((double)(c->tick + j * len) * c->dt);
+    }
+    c->tick += ticks;
+    c->t = (double)c->tick * c->dt;
+    c->have_pred = true;
 }
 
 poro_status poro_advance(poro_ctx* c, double t_end) {
@@ -1305,49 +1447,22 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
     const int64_t n_cycles = (int64_t)std::floor((t_end - c->t) / dt_max + 1e-9);
     if (n_cycles <= 0) return PORO_OK;
     const int64_t ticks = n_cycles * cycle;
-    const int nrec = (int)c->rec_elem.size();
-    cudaError_t er = cudaSuccess;
-    if (!c->d_tick && (er = cudaMalloc((void**)&c->d_tick, sizeof(int64_t))) != cudaSuccess)
-        return cuda_fail(c, er, "poro_advance");
-    if ((er = cudaMemcpyAsync(c->d_tick, &c->tick, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-        return cuda_fail(c, er, "poro_advance");
-    if (nrec > 0) {
-        // buffers are kept across calls; they grow only when a call needs more
-        if (c->rp_n != (size_t)nrec) {
-            dfree(c->d_rp);
-            dfree(c->d_cnt);
-            c->rp_n = 0;
-            if ((er = upload((void**)&c->d_rp, c->rec_phi.data(), c->rec_phi.size() * sizeof(double))) != cudaSuccess ||
-                (er = cudaMalloc((void**)&c->d_cnt, nrec * sizeof(int32_t))) != cudaSuccess)
-                return cuda_fail(c, er, "poro_advance");
-            c->rp_n = nrec;
-            dfree(c->d_seis);
-            c->seis_cap = 0;
-        }
-        if (c->seis_cap < ticks) {
-            dfree(c->d_seis);
-            c->seis_cap = 0;
-            if ((er = cudaMalloc((void**)&c->d_seis, (size_t)nrec * ticks * NQ * sizeof(double))) != cudaSuccess)
-                return cuda_fail(c, er, "poro_advance");
-            c->seis_cap = ticks;
-        }
-        if ((er = cudaMemsetAsync(c->d_cnt, 0, nrec * sizeof(int32_t), c->stream)) != cudaSuccess)
-            return cuda_fail(c, er, "poro_advance");
-    }
+    if (poro_status st = prepare_advance(c, ticks, c->stream, "poro_advance")) return st;
     double* d_rp = c->d_rp;
     double* d_seis = c->d_seis;
     int32_t* d_cnt = c->d_cnt;
     const int64_t cap = c->seis_cap;
+    cudaError_t er = cudaSuccess;
     // the first cycle runs directly (it also sets the kernels' attributes);
     // the others replay a CUDA graph of one cycle
-    int rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
+    int rc = enqueue_cycle(c, d_rp, d_seis, cap, d_cnt);
     if (rc == 0 && n_cycles > 1) {
         if (c->use_graphs) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             er = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
             if (er == cudaSuccess) {
-                rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
+                rc = enqueue_cycle(c, d_rp, d_seis, cap, d_cnt);
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
                 if (rc == 0 && e2 != cudaSuccess) rc = (int)e2;
             } else {
@@ -1358,28 +1473,244 @@ poro_status poro_advance(poro_ctx* c, double t_end) {
             if (exec) cudaGraphExecDestroy(exec);
             if (graph) cudaGraphDestroy(graph);
         } else {
-            for (int64_t k = 1; k < n_cycles && rc == 0; ++k) rc = enqueue_cycle(c, nullptr, d_rp, d_seis, cap, d_cnt);
+            for (int64_t k = 1; k < n_cycles && rc == 0; ++k) rc = enqueue_cycle(c, d_rp, d_seis, cap, d_cnt);
         }
     }
-    std::vector<double>& h = c->h_seis;
-    if (rc == 0 && nrec > 0) {
-        h.resize((size_t)nrec * cap * NQ);
-        er = cudaMemcpyAsync(h.data(), d_seis, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    }
+    if (rc == 0) er = stage_seismograms(c, c->stream);
     if (rc == 0 && er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_advance: kernel launch / graph");
     if (er != cudaSuccess) return cuda_fail(c, er, "poro_advance");
     if (poro_status st = device_status(c, "poro_advance")) return st;
-    for (int r = 0; r < nrec; ++r) {
-        const int cl = c->h_cl[c->rec_elem[r]];
-        const int64_t len = (int64_t)1 << cl, ns = ticks / len;
-        c->seis_q[r].insert(c->seis_q[r].end(), h.begin() + (size_t)r * cap * NQ,
-                            h.begin() + ((size_t)r * cap + ns) * NQ);
-        for (int64_t j = 1; j <= ns; ++j) c->seis_t[r].push_back((double)(c->tick + j * len) * c->dt);
+    finish_advance(c, ticks);
+    return PORO_OK;
+}
+
+// ------------------------------------------------------ batched groups of runs
+// Several simulations of one degree, precision, refinement, CTA variant and
+// cluster count advance together: every tick's predictors of all runs' due
+// clusters are one launch (items = (run, element) pairs), then each run's LTS
+// buffers, correctors, sources and receivers; a cycle is captured once as a
+// CUDA graph and replayed.  Results are those of each run advanced alone:
+// every element's predictor is computed by one CTA with the same code.
+}  // extern "C"
+
+namespace poro {
+
+struct RunGroup {
+    std::vector<poro_ctx*> runs;
+    int device = 0, C = 1;
+    int64_t cycle = 1;
+    cudaStream_t stream = nullptr;
+    RunPtrs* d_runs = nullptr;
+    int32_t* d_items = nullptr;      // elements of all runs' due clusters, tick residue by tick residue
+    int32_t* d_item_run = nullptr;
+    std::vector<int64_t> k_off, k_cnt;
+    int64_t pending = 0;             // ticks enqueued since the last group_finish
+    // captured cycle, valid while every run's receiver buffers stay the same
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> exec_key;
+};
+
+static int enqueue_group_cycle(RunGroup* g) {
+    poro_ctx* lead = g->runs[0];
+    int rc = 0;
+    for (int64_t k = 0; k < g->cycle && rc == 0; ++k) {
+        const int64_t cnt = g->k_cnt[k];
+        if (cnt > 0) {
+            const int32_t* el = g->d_items + g->k_off[k];
+            const int32_t* ir = g->d_item_run + g->k_off[k];
+            if (lead->prec == PORO_FP64)
+                rc = launch_stp_fp64(lead->dref, el, cnt, nullptr, nullptr, nullptr, nullptr, g->stream, lead->variant,
+                                     g->d_runs, ir);
+            else
+                rc = launch_stp_mixed(lead->mref, lead->refine, el, cnt, nullptr, nullptr, nullptr, nullptr, g->stream,
+                                      lead->variant, g->d_runs, ir);
+        }
+        for (poro_ctx* c : g->runs)
+            if (rc == 0) rc = enqueue_tick(c, k, false, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, g->stream);
     }
-    c->tick += ticks;
-    c->t = (double)c->tick * c->dt;
-    c->have_pred = true;
+    for (poro_ctx* c : g->runs)
+        if (rc == 0) rc = launch_tick_advance(c->d_tick, g->cycle, g->stream);
+    return rc;
+}
+
+void group_destroy(RunGroup* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    dfree(g->d_runs);
+    dfree(g->d_items);
+    dfree(g->d_item_run);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+RunGroup* group_create(poro_ctx* const* runs, int n, std::string& err) {
+    if (n <= 0 || !runs) {
+        err = "group_create: no runs";
+        return nullptr;
+    }
+    poro_ctx* a = runs[0];
+    for (int i = 0; i < n; ++i) {
+        poro_ctx* c = runs[i];
+        if (!c || !c->ready) {
+            err = "group_create: a run has no mesh set-up";
+            return nullptr;
+        }
+        if (c->device != a->device || c->N != a->N || c->prec != a->prec || c->C != a->C || c->variant != a->variant ||
+            (c->prec != PORO_FP64 && (c->refine != a->refine || c->mref.wait_limit != a->mref.wait_limit))) {
+            err = "group_create: runs differ in device, degree, precision, refinement, variant or clusters";
+            return nullptr;
+        }
+        if (c->tick % ((int64_t)1 << (c->C - 1))) {
+            err = "group_create: a run is not at the end of a cycle";
+            return nullptr;
+        }
+    }
+    RunGroup* g = new RunGroup();
+    g->runs.assign(runs, runs + n);
+    g->device = a->device;
+    g->C = a->C;
+    g->cycle = (int64_t)1 << (a->C - 1);
+    cudaSetDevice(g->device);
+    std::vector<RunPtrs> rp(n);
+    for (int i = 0; i < n; ++i) {
+        poro_ctx* c = runs[i];
+        rp[i] = RunPtrs{c->d_q0, c->d_econst, g->C > 1 ? c->d_qt : nullptr, c->d_iout};
+    }
+    std::vector<int32_t> items, item_run;
+    for (int64_t k = 0; k < g->cycle; ++k) {
+        g->k_off.push_back((int64_t)items.size());
+        for (int i = 0; i < n; ++i)
+            for (int cl = 0; cl < g->C; ++cl) {
+                if (k % ((int64_t)1 << cl)) continue;
+                const std::vector<int32_t>& el = runs[i]->cl_elems[cl];
+                items.insert(items.end(), el.begin(), el.end());
+                item_run.insert(item_run.end(), el.size(), (int32_t)i);
+            }
+        g->k_cnt.push_back((int64_t)items.size() - g->k_off.back());
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = upload((void**)&g->d_runs, rp.data(), rp.size() * sizeof(RunPtrs));
+    if (e == cudaSuccess) e = upload((void**)&g->d_items, items.data(), items.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = upload((void**)&g->d_item_run, item_run.data(), item_run.size() * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        err = std::string("group_create: ") + cudaGetErrorString(e);
+        group_destroy(g);
+        return nullptr;
+    }
+    return g;
+}
+
+// Enqueue n_cycles cycles of every run of the group (asynchronous on the
+// group's stream); group_finish completes them.
+int group_enqueue(RunGroup* g, int64_t n_cycles, std::string& err) {
+    if (n_cycles <= 0) return 0;
+    cudaSetDevice(g->device);
+    const int64_t ticks = n_cycles * g->cycle;
+    for (poro_ctx* c : g->runs)
+        if (prepare_advance(c, ticks, g->stream, "group_enqueue") != PORO_OK) {
+            err = c->err;
+            return -1;
+        }
+    std::vector<const void*> key;
+    for (poro_ctx* c : g->runs) {
+        key.push_back(c->d_seis);
+        key.push_back((const void*)(intptr_t)c->seis_cap);
+    }
+    int rc = 0;
+    int64_t done = 0;
+    if (!g->exec || key != g->exec_key) {
+        // first cycle directly (sets the kernels' attributes), then capture
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+        rc = enqueue_group_cycle(g);
+        done = 1;
+        if (rc == 0 && n_cycles > 1) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t er = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+            if (er == cudaSuccess) {
+                rc = enqueue_group_cycle(g);
+                cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+                if (rc == 0 && e2 != cudaSuccess) rc = (int)e2;
+            } else {
+                rc = (int)er;
+            }
+            if (rc == 0) rc = (int)cudaGraphInstantiate(&g->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (rc == 0) g->exec_key = key;
+        }
+    }
+    for (int64_t k = done; k < n_cycles && rc == 0; ++k) rc = (int)cudaGraphLaunch(g->exec, g->stream);
+    for (poro_ctx* c : g->runs)
+        if (rc == 0) rc = (int)stage_seismograms(c, g->stream);
+    if (rc != 0) {
+        err = std::string("group_enqueue: ") + cudaGetErrorString((cudaError_t)rc);
+        return rc;
+    }
+    g->pending += ticks;
+    return 0;
+}
+
+// Wait for the enqueued cycles and complete every run's bookkeeping.  A
+// bounded wait of the batched predictor that gave up fails the whole group
+// (PORO_ETIMEOUT).
+poro_status group_finish(RunGroup* g, std::string& err) {
+    cudaSetDevice(g->device);
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        err = std::string("group_finish: ") + cudaGetErrorString(e);
+        return PORO_ECUDA;
+    }
+    const int64_t ticks = g->pending;
+    g->pending = 0;
+    poro_ctx* lead = g->runs[0];
+    if (poro_status st = device_status(lead, "group_finish")) {
+        err = lead->err;
+        return st;
+    }
+    for (poro_ctx* c : g->runs) finish_advance(c, ticks);
+    return PORO_OK;
+}
+
+}  // namespace poro
+
+extern "C" {
+
+poro_status poro_cluster_times(poro_ctx* c, double t_end, double* ms_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_cluster_times: ctx is NULL");
+    if (!c->ready) return fail(c, PORO_ESTATE, "poro_cluster_times: call poro_set_clusters first");
+    if (!ms_out) return fail(c, PORO_EINVAL, "poro_cluster_times: ms_out is NULL");
+    cudaSetDevice(c->device);
+    const int C = c->C;
+    for (int cl = 0; cl < C; ++cl) ms_out[cl] = 0.0;
+    const int64_t cycle = (int64_t)1 << (C - 1);
+    const int64_t n_cycles = (int64_t)std::floor((t_end - c->t) / std::ldexp(c->dt, C - 1) + 1e-9);
+    if (n_cycles <= 0) return PORO_OK;
+    const int64_t ticks = n_cycles * cycle;
+    if (poro_status st = prepare_advance(c, ticks, c->stream, "poro_cluster_times")) return st;
+    std::vector<ClusterEvent> prof;
+    int rc = 0;
+    for (int64_t n = 0; n < n_cycles && rc == 0; ++n) {
+        for (int64_t k = 0; k < cycle && rc == 0; ++k)
+            rc = enqueue_tick(c, k, true, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, c->stream, &prof);
+        if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
+    }
+    cudaError_t er = cudaSuccess;
+    if (rc == 0) er = stage_seismograms(c, c->stream);
+    if (rc == 0 && er == cudaSuccess) er = cudaStreamSynchronize(c->stream);
+    for (ClusterEvent& ev : prof) {
+        float ms = 0.f;
+        if (rc == 0 && er == cudaSuccess && ev.a && ev.b && cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess)
+            ms_out[ev.cl] += ms;
+        if (ev.a) cudaEventDestroy(ev.a);
+        if (ev.b) cudaEventDestroy(ev.b);
+    }
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "poro_cluster_times: kernel launch");
+    if (er != cudaSuccess) return cuda_fail(c, er, "poro_cluster_times");
+    if (poro_status st = device_status(c, "poro_cluster_times")) return st;
+    finish_advance(c, ticks);
     return PORO_OK;
 }
 
@@ -1443,6 +1774,7 @@ poro_status poro_flux_matrices(const poro_material* mL, const poro_material* mR,
 
 poro_status poro_autotune(poro_ctx* c, int64_t sample, int32_t* variant_out, double* ms_out) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_autotune: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_autotune: the autotuner is built for Biot's system");
     if (!c->d_econst || c->n_elem <= 0) return fail(c, PORO_ESTATE, "poro_autotune: no element population loaded");
     cudaSetDevice(c->device);
     const int64_t n = std::max<int64_t>(1, std::min(sample > 0 ? sample : c->n_elem, c->n_elem));
@@ -1480,6 +1812,81 @@ poro_status poro_autotune(poro_ctx* c, int64_t sample, int32_t* variant_out, dou
     cudaEventDestroy(e1);
     c->variant = bestv;
     if (variant_out) *variant_out = bestv;
+    return PORO_OK;
+}
+
+// tile choices: CTA-size variant x operand layout caps (A buffers, Khat slots)
+static const int kTileCaps[6][2] = {{3, 3}, {2, 3}, {1, 3}, {2, 2}, {1, 2}, {1, 1}};
+
+static bool tile_choice_valid(const poro_ctx* c, int choice) {
+    if (choice < 0 || choice >= PORO_TILE_CHOICES) return false;
+    const int cta = choice / 6, lay = choice % 6;
+    if (c->prec == PORO_FP64) return lay == 0;       // the FP64 kernel has no tensor-core tiles
+    if (c->prec == PORO_BF16X3_REFINE) return cta == 0;  // bf16 sweeps: default CTA size only
+    return true;
+}
+
+static void apply_tile_choice(poro_ctx* c, int choice) {
+    c->variant = choice / 6;
+    c->mref.cap_a = kTileCaps[choice % 6][0];
+    c->mref.cap_b = kTileCaps[choice % 6][1];
+}
+
+poro_status poro_set_tiles(poro_ctx* c, int32_t choice) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_tiles: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_set_tiles: Biot contexts only");
+    if (!tile_choice_valid(c, choice)) return fail(c, PORO_EINVAL, "poro_set_tiles: choice not available here");
+    apply_tile_choice(c, choice);
+    return PORO_OK;
+}
+
+poro_status poro_autotune_tiles(poro_ctx* c, int64_t sample, int32_t* choice_out, double* ms_out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_autotune_tiles: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_autotune_tiles: Biot contexts only");
+    if (!c->d_econst || c->n_elem <= 0) return fail(c, PORO_ESTATE, "poro_autotune_tiles: no element population loaded");
+    cudaSetDevice(c->device);
+    const int64_t n = std::max<int64_t>(1, std::min(sample > 0 ? sample : c->n_elem, c->n_elem));
+    const int saved_v = c->variant, saved_a = c->mref.cap_a, saved_b = c->mref.cap_b;
+    auto restore = [&] {
+        c->variant = saved_v;
+        c->mref.cap_a = saved_a;
+        c->mref.cap_b = saved_b;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaErrorMemoryAllocation, "poro_autotune_tiles: events");
+    }
+    double best = 1e300;
+    int bestc = 0;
+    poro_status st = PORO_OK;
+    for (int choice = 0; choice < PORO_TILE_CHOICES && st == PORO_OK; ++choice) {
+        if (ms_out) ms_out[choice] = -1.0;
+        if (!tile_choice_valid(c, choice)) continue;
+        apply_tile_choice(c, choice);
+        for (int w = 0; w < 2 && st == PORO_OK; ++w)
+            st = dispatch_predict(c, 0, n, c->d_q0, c->d_qt, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && st == PORO_OK; ++r)
+            st = dispatch_predict(c, 0, n, c->d_q0, c->d_qt, c->d_iout, PORO_SOLVE_BLOCK, c->stream);
+        cudaEventRecord(e1, c->stream);
+        const cudaError_t er = cudaEventSynchronize(e1);
+        if (st == PORO_OK && er != cudaSuccess) st = cuda_fail(c, er, "poro_autotune_tiles");
+        if (st == PORO_OK) st = device_status(c, "poro_autotune_tiles");
+        float ms = 0.f;
+        if (st == PORO_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (st == PORO_OK && ms_out) ms_out[choice] = ms / 3.0;
+        if (st == PORO_OK && ms < best) {
+            best = ms;
+            bestc = choice;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    restore();
+    if (st != PORO_OK) return st;
+    apply_tile_choice(c, bestc);
+    if (choice_out) *choice_out = bestc;
     return PORO_OK;
 }
 

@@ -60,6 +60,22 @@ PORO_HD constexpr int star_col(int n) {
     return t[n];
 }
 
+// Damped Maxwell equations (Section "Other applications"): 6 quantities
+// (E_x, E_y, E_z, H_x, H_y, H_z), eps E_t = curl H - sigma E, mu H_t =
+// -curl E.  Union pattern of the reference Jacobians: row p couples the two
+// field components of the other kind that its curl row involves.
+namespace maxwell {
+constexpr int NQ = 6;
+constexpr int STAR_NNZ = 12;
+PORO_HD constexpr int star_row(int n) { return n / 2; }
+PORO_HD constexpr int star_col(int n) {
+    constexpr int t[STAR_NNZ] = {4, 5, 3, 5, 3, 4, 1, 2, 0, 2, 0, 1};
+    return t[n];
+}
+// per-element constants: star[3][12], (Z - e I)^{-1} [T][T], e, 0, dt, pad
+PORO_HD constexpr int elem_const_stride(int N) { return (3 * STAR_NNZ + (N + 1) * (N + 1) + 4 + 1) & ~1; }
+}  // namespace maxwell
+
 // Per-element constants, in doubles, in this order:
 //   star[3][54]       A^{j*} = dt A^j on the union pattern
 //   zinv_uf[T][T]     (Z - e I)^{-1}, e = E*_{uf,uf} (row-major, [u][s])
@@ -102,6 +118,10 @@ bool invert_small(int n, const double* a, double* ainv);
 // fills one element's constants block (elem_const_stride(N) doubles)
 bool element_constants(const ReferenceData& ref, const double* v12, const poro_material& mat,
                        double dt, double* out, std::string& err);
+// the same for a damped-Maxwell element, mat = (eps, mu, sigma)
+// (maxwell::elem_const_stride(N) doubles)
+bool maxwell_element_constants(const ReferenceData& ref, const double* v12, const double mat[3], double dt,
+                               double* out, std::string& err);
 
 // ----- corrector set-up (mesh.cpp) -----
 // Godunov flux solver matrices of one face: A_n^L q* = Fm q_L + Fp q_R.
@@ -152,6 +172,10 @@ struct MixedReference {
     int32_t tc_off[MAX_N + 1][3] = {};
     int32_t* status = nullptr;      // device word: 1 after a bounded wait gave up
     long long wait_limit = 0;       // SM clocks a wait of the sweeps may take (0: about 1 s)
+    // operand layout of the tensor-core sweeps (the autotuner's tile choice):
+    // at most cap_a A-tile buffers and cap_b Khat image slots per degree block
+    // (3, 3: as many as fit in the operand region)
+    int cap_a = 3, cap_b = 3;
 };
 
 // Fill the constant-memory residual table of degree N on the current device
@@ -159,16 +183,24 @@ struct MixedReference {
 // context of that degree.
 int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, int n_entries);
 
-// Fill the constant-memory residual table of degree N on the current device
-// (row pointers relative to the entries); idempotent, same data for every
-// context of that degree.
-int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, int n_entries);
+// Per-run buffers of a predictor launch that covers the elements of several
+// simulations of the same degree and precision (the server's batched mode):
+// item i of the launch is element elems[i] of run item_run[i], read from and
+// written to that run's buffers.
+struct RunPtrs {
+    const double* q0;      // [ne][13][B]
+    const double* econst;  // [ne][stride]
+    double* qt;            // [ne][13][B][T] or nullptr
+    double* iout;          // [ne][13][B] or nullptr
+};
 
 // Launch the mixed-precision predictor (binary32 sweeps, `refine` residual
-// corrections in double-binary32) for `count` elements.
+// corrections in double-binary32) for `count` elements.  With `runs`
+// (device array) and `item_run`, the items come from several runs and q0,
+// econst, qt, iout are ignored.
 int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count,
                      const double* q0, const double* econst, double* qt, double* iout, void* stream,
-                     int variant = 0);
+                     int variant = 0, const RunPtrs* runs = nullptr, const int32_t* item_run = nullptr);
 
 // Dense-LU comparator: reference data and per-batch scratch (factors,
 // pivots, permutation, equilibration factors, singularity flag).
@@ -251,12 +283,31 @@ int launch_tick_advance(int64_t* tick, int64_t n, void* stream);
 int launch_receivers(int N, const double* q, int32_t nrec, const int64_t* elems, const double* phi, double* out,
                      int64_t stride_out, void* stream);
 
+// Batched advance of several simulations (the server): runs of one degree,
+// precision, refinement, CTA variant and cluster count, each at the end of a
+// cycle.  Every tick's predictors of all runs are one launch; each run's
+// results are those it gets when advanced alone.  group_enqueue queues
+// n_cycles cycles on the group's own stream; group_finish waits for them and
+// appends the receiver samples.  The runs must not be used otherwise while
+// the group exists.
+struct RunGroup;
+RunGroup* group_create(poro_ctx* const* runs, int n, std::string& err);
+int group_enqueue(RunGroup* g, int64_t n_cycles, std::string& err);
+poro_status group_finish(RunGroup* g, std::string& err);
+void group_destroy(RunGroup* g);
+
 // Launch the FP64 Algorithm-3 predictor for `count` elements.
 // q0[count][13][B], econst[count][stride], qt (nullable), iout (nullable).
 // `elems` (nullable): element index list; outputs are indexed by element.
 // `variant` selects the CTA size (0: default, 1: the alternative the
-// autotuner may pick).
+// autotuner may pick).  `runs` / `item_run`: items of several runs, as for
+// launch_stp_mixed.
 int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-                    const double* econst, double* qt, double* iout, void* stream, int variant = 0);
+                    const double* econst, double* qt, double* iout, void* stream, int variant = 0,
+                    const RunPtrs* runs = nullptr, const int32_t* item_run = nullptr);
+// The same kernel for the damped Maxwell system (q0 [count][6][B], econst
+// [count][maxwell::elem_const_stride(N)], qt [count][6][B][T]).
+int launch_stp_fp64_maxwell(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                            const double* econst, double* qt, double* iout, void* stream);
 
 }  // namespace poro

@@ -3,12 +3,26 @@
 //
 // A scheduler thread admits queued requests in arrival order while a slot
 // is free and the sum of the admitted requests' device-memory footprints
-// stays within the budget; each admitted request runs on a worker thread
-// with its own context and CUDA stream, advancing its clustered time
-// stepping one chunk of cycles at a time (so requests admitted while others
-// run overlap with them on the device, and a cancel takes effect between
-// chunks).  A request that fails (invalid input, footprint above the whole
-// budget, a CUDA error of its own calls) ends in PORO_REQ_FAILED alone.
+// stays within the budget.  Each admitted request is set up (context, mesh,
+// flux solvers, clusters, sources, receivers) on a worker thread of its own.
+//
+// Batched mode (the default): set-up requests join one executor thread.  It
+// groups the running requests by degree, precision, refinement, CTA variant
+// and cluster count, and advances every group a chunk of cycles at a time
+// with poro::group_enqueue: each tick's predictors of all of a group's runs
+// are a single launch, followed by each run's LTS buffers, correctors,
+// sources and receivers, the cycle captured once as a CUDA graph.  Groups of
+// different degrees run concurrently on their own streams.  Requests that
+// arrive while others run join their group at the next chunk.
+//
+// Stream mode (poro_server_set_batching(s, 0)): each request runs on its
+// worker thread with its own context and CUDA stream, advancing one chunk of
+// cycles at a time, so requests overlap on the device through streams.
+//
+// In both modes a cancel takes effect between chunks, and a request that
+// fails (invalid input, footprint above the whole budget, a CUDA error of its
+// own calls) ends in PORO_REQ_FAILED alone; in batched mode a failure of a
+// group's shared predictor launch fails that group's requests.
 // The paper has no counterpart: it runs one simulation per MPI job.
 #include <algorithm>
 #include <chrono>
@@ -21,6 +35,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "poro_internal.h"
@@ -47,6 +62,10 @@ struct Request {
     double sim_t = 0.0;
     clk::time_point t_submit, t_start, t_done;
     std::vector<std::vector<double>> seis_t, seis_q;
+    // batched mode: the set-up context and the cycles to run
+    poro_ctx* ctx = nullptr;
+    int64_t total = 0, done = 0;
+    double dt_cycle = 0.0;
 };
 }  // namespace
 
@@ -64,6 +83,12 @@ struct poro_server {
     std::thread scheduler;
     std::vector<std::thread> workers;
     std::string err;
+    // batched mode
+    bool batched = true;
+    std::deque<uint64_t> ready;      // set up, waiting to join the executor
+    bool exec_stop = false;
+    std::condition_variable exec_cv;
+    std::thread executor;
 };
 
 namespace {
@@ -90,7 +115,9 @@ size_t footprint_bytes(int N, int64_t ne, int C, int nrec) {
     return (size_t)((double)(per * (size_t)ne + fixed) * 1.25) + (64u << 20);
 }
 
-poro_status run_request(poro_server* s, Request& r) {
+// Context, mesh, materials, clusters, sources and receivers of a request;
+// on success r.ctx, r.total (cycles) and r.dt_cycle are set.
+poro_status setup_request(poro_server* s, Request& r) {
     poro_ctx* ctx = nullptr;
     poro_status st = poro_create(s->device, r.N, (poro_precision)r.prec, &ctx);
     if (st != PORO_OK) {
@@ -103,7 +130,7 @@ poro_status run_request(poro_server* s, Request& r) {
         return e;
     };
     const int64_t ne = (int64_t)r.tet.size() / 4;
-    if (r.prec == PORO_FP32_REFINE && (st = poro_set_refinement(ctx, r.refine)) != PORO_OK) return bail(st);
+    if (r.prec != PORO_FP64 && (st = poro_set_refinement(ctx, r.refine)) != PORO_OK) return bail(st);
     if ((st = poro_set_mesh(ctx, (int64_t)r.xyz.size() / 3, r.xyz.data(), ne, r.tet.data(), r.nb.data(),
                             r.tag.data())) != PORO_OK)
         return bail(st);
@@ -118,26 +145,17 @@ poro_status run_request(poro_server* s, Request& r) {
     const int nrec = (int)(r.rec_xyz.size() / 3);
     for (int i = 0; i < nrec; ++i)
         if ((st = poro_add_receiver(ctx, &r.rec_xyz[3 * i], nullptr)) != PORO_OK) return bail(st);
-    const double dt_cycle = std::ldexp(dtmin, r.C - 1);
-    const int64_t total = (int64_t)std::floor(r.t_end / dt_cycle + 1e-9);
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(64, total / 8 + 1));
-    int64_t done = 0;
-    while (done < total) {
-        {
-            std::lock_guard<std::mutex> l(s->mu);
-            if (r.cancel) {
-                poro_destroy(ctx);
-                return PORO_ETIMEOUT;  // marker: cancelled
-            }
-        }
-        const int64_t n = std::min(chunk, total - done);
-        if ((st = poro_advance(ctx, (double)(done + n) * dt_cycle * (1.0 + 1e-12))) != PORO_OK) return bail(st);
-        done += n;
-        double t = 0.0;
-        poro_get_time(ctx, &t, nullptr);
-        std::lock_guard<std::mutex> l(s->mu);
-        r.sim_t = t;
-    }
+    r.ctx = ctx;
+    r.dt_cycle = std::ldexp(dtmin, r.C - 1);
+    r.total = (int64_t)std::floor(r.t_end / r.dt_cycle + 1e-9);
+    r.done = 0;
+    return PORO_OK;
+}
+
+// Receiver samples into the request, context released.
+void collect_request(Request& r) {
+    poro_ctx* ctx = r.ctx;
+    const int nrec = (int)(r.rec_xyz.size() / 3);
     r.seis_t.assign(nrec, {});
     r.seis_q.assign(nrec, {});
     for (int i = 0; i < nrec; ++i) {
@@ -148,16 +166,43 @@ poro_status run_request(poro_server* s, Request& r) {
         poro_get_seismogram(ctx, i, n, r.seis_t[i].data(), r.seis_q[i].data(), &n);
     }
     poro_destroy(ctx);
+    r.ctx = nullptr;
+}
+
+// Stream mode: the request's own context and stream, one chunk of cycles at a
+// time.
+poro_status run_request(poro_server* s, Request& r) {
+    poro_status st = setup_request(s, r);
+    if (st != PORO_OK) return st;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(64, r.total / 8 + 1));
+    while (r.done < r.total) {
+        {
+            std::lock_guard<std::mutex> l(s->mu);
+            if (r.cancel) {
+                poro_destroy(r.ctx);
+                r.ctx = nullptr;
+                return PORO_ETIMEOUT;  // marker: cancelled
+            }
+        }
+        const int64_t n = std::min(chunk, r.total - r.done);
+        if ((st = poro_advance(r.ctx, (double)(r.done + n) * r.dt_cycle * (1.0 + 1e-12))) != PORO_OK) {
+            r.err = poro_last_error(r.ctx);
+            poro_destroy(r.ctx);
+            r.ctx = nullptr;
+            return st;
+        }
+        r.done += n;
+        double t = 0.0;
+        poro_get_time(r.ctx, &t, nullptr);
+        std::lock_guard<std::mutex> l(s->mu);
+        r.sim_t = t;
+    }
+    collect_request(r);
     return PORO_OK;
 }
 
-void worker_main(poro_server* s, uint64_t ticket) {
-    Request* r;
-    {
-        std::lock_guard<std::mutex> l(s->mu);
-        r = s->reqs[ticket].get();
-    }
-    poro_status st = run_request(s, *r);
+// End state of a request; releases its slot and budget.
+void finalize(poro_server* s, Request* r, poro_status st) {
     std::lock_guard<std::mutex> l(s->mu);
     r->t_done = clk::now();
     if (st == PORO_OK) r->state = PORO_REQ_DONE;
@@ -167,6 +212,166 @@ void worker_main(poro_server* s, uint64_t ticket) {
     s->running -= 1;
     s->cv.notify_all();
     s->done_cv.notify_all();
+}
+
+void worker_main(poro_server* s, uint64_t ticket) {
+    Request* r;
+    {
+        std::lock_guard<std::mutex> l(s->mu);
+        r = s->reqs[ticket].get();
+    }
+    finalize(s, r, run_request(s, *r));
+}
+
+// Batched mode, set-up half: build the context, then hand the request to the
+// executor.
+void setup_main(poro_server* s, uint64_t ticket) {
+    Request* r;
+    {
+        std::lock_guard<std::mutex> l(s->mu);
+        r = s->reqs[ticket].get();
+    }
+    poro_status st = setup_request(s, *r);
+    if (st != PORO_OK) {
+        finalize(s, r, st);
+        return;
+    }
+    std::lock_guard<std::mutex> l(s->mu);
+    s->ready.push_back(ticket);
+    s->exec_cv.notify_all();
+}
+
+// requests that can share predictor launches (the server's contexts all keep
+// the default CTA variant)
+struct GroupKey {
+    int N, prec, refine, C;
+    bool operator<(const GroupKey& o) const {
+        return std::tie(N, prec, refine, C) < std::tie(o.N, o.prec, o.refine, o.C);
+    }
+};
+
+// cycles of one chunk: about 32 ticks, at least one cycle
+int64_t chunk_cycles(int C) { return std::max<int64_t>(1, 32 >> (C - 1)); }
+
+void executor_main(poro_server* s) {
+    std::vector<Request*> active;
+    std::map<std::vector<uint64_t>, poro::RunGroup*> groups;  // by the sorted tickets of their runs
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> l(s->mu);
+            s->exec_cv.wait(l, [&] { return s->exec_stop || !s->ready.empty() || !active.empty(); });
+            if (s->exec_stop && s->ready.empty() && active.empty()) break;
+            while (!s->ready.empty()) {
+                active.push_back(s->reqs[s->ready.front()].get());
+                s->ready.pop_front();
+            }
+        }
+        // cancellations (between chunks)
+        std::vector<Request*> keep;
+        for (Request* r : active) {
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> l(s->mu);
+                cancel = r->cancel;
+            }
+            if (!cancel) {
+                keep.push_back(r);
+                continue;
+            }
+            for (auto& kv : groups) poro::group_destroy(kv.second);
+            groups.clear();
+            poro_destroy(r->ctx);
+            r->ctx = nullptr;
+            finalize(s, r, PORO_ETIMEOUT);
+        }
+        active.swap(keep);
+        if (active.empty()) continue;
+        // groups of the running requests; a changed composition is rebuilt
+        std::map<GroupKey, std::vector<Request*>> by;
+        for (Request* r : active) by[GroupKey{r->N, r->prec, r->prec == PORO_FP64 ? 0 : r->refine, r->C}].push_back(r);
+        std::map<std::vector<uint64_t>, poro::RunGroup*> next;
+        std::vector<std::pair<poro::RunGroup*, std::vector<Request*>>> work;
+        std::vector<Request*> failed;
+        for (auto& kv : by) {
+            std::vector<Request*>& rs = kv.second;
+            std::sort(rs.begin(), rs.end(), [](const Request* a, const Request* b) { return a->ticket < b->ticket; });
+            std::vector<uint64_t> key;
+            std::vector<poro_ctx*> ctxs;
+            for (Request* r : rs) {
+                key.push_back(r->ticket);
+                ctxs.push_back(r->ctx);
+            }
+            poro::RunGroup* g = nullptr;
+            auto it = groups.find(key);
+            if (it != groups.end()) {
+                g = it->second;
+                groups.erase(it);
+            } else {
+                std::string err;
+                g = poro::group_create(ctxs.data(), (int)ctxs.size(), err);
+                if (!g) {
+                    for (Request* r : rs) {
+                        r->err = err;
+                        failed.push_back(r);
+                    }
+                    continue;
+                }
+            }
+            next[key] = g;
+            work.emplace_back(g, rs);
+        }
+        for (auto& kv : groups) poro::group_destroy(kv.second);
+        groups.swap(next);
+        // one chunk per group: all groups are enqueued before any is awaited
+        std::vector<int64_t> chunk(work.size(), 0);
+        std::vector<std::string> errs(work.size());
+        std::vector<bool> ok(work.size(), true);
+        for (size_t i = 0; i < work.size(); ++i) {
+            int64_t n = chunk_cycles(work[i].second[0]->C);
+            for (Request* r : work[i].second) n = std::min(n, r->total - r->done);
+            chunk[i] = n;
+            if (n > 0 && poro::group_enqueue(work[i].first, n, errs[i]) != 0) ok[i] = false;
+        }
+        for (size_t i = 0; i < work.size(); ++i) {
+            if (ok[i] && chunk[i] > 0 && poro::group_finish(work[i].first, errs[i]) != PORO_OK) ok[i] = false;
+            if (!ok[i]) {
+                for (Request* r : work[i].second) {
+                    r->err = errs[i];
+                    failed.push_back(r);
+                }
+                continue;
+            }
+            for (Request* r : work[i].second) {
+                r->done += chunk[i];
+                double t = 0.0;
+                poro_get_time(r->ctx, &t, nullptr);
+                std::lock_guard<std::mutex> l(s->mu);
+                r->sim_t = t;
+            }
+        }
+        // finished and failed requests leave (their groups first)
+        std::vector<Request*> still;
+        std::vector<Request*> finished;
+        for (Request* r : active) {
+            if (std::find(failed.begin(), failed.end(), r) != failed.end()) continue;
+            (r->done >= r->total ? finished : still).push_back(r);
+        }
+        if (!finished.empty() || !failed.empty()) {
+            for (auto& kv : groups) poro::group_destroy(kv.second);
+            groups.clear();
+        }
+        for (Request* r : finished) {
+            collect_request(*r);
+            finalize(s, r, PORO_OK);
+        }
+        for (Request* r : failed) {
+            poro_destroy(r->ctx);
+            r->ctx = nullptr;
+            finalize(s, r, PORO_ECUDA);
+        }
+        active.swap(still);
+    }
+    for (auto& kv : groups) poro::group_destroy(kv.second);
 }
 
 void scheduler_main(poro_server* s) {
@@ -196,7 +401,10 @@ void scheduler_main(poro_server* s) {
             s->running += 1;
             r->state = PORO_REQ_RUNNING;
             r->t_start = clk::now();
-            s->workers.emplace_back(worker_main, s, r->ticket);
+            if (s->batched)
+                s->workers.emplace_back(setup_main, s, r->ticket);
+            else
+                s->workers.emplace_back(worker_main, s, r->ticket);
             admitted = true;
         }
         if (!admitted) s->cv.wait(l);
@@ -213,7 +421,15 @@ poro_status poro_server_create(int device, size_t hbm_budget, int32_t max_slots,
     s->budget = hbm_budget;
     s->max_slots = max_slots;
     s->scheduler = std::thread(scheduler_main, s);
+    s->executor = std::thread(executor_main, s);
     *out = s;
+    return PORO_OK;
+}
+
+poro_status poro_server_set_batching(poro_server* s, int32_t on) {
+    if (!s) return sfail(nullptr, PORO_EINVAL, "poro_server_set_batching: NULL server");
+    std::lock_guard<std::mutex> l(s->mu);
+    s->batched = on != 0;
     return PORO_OK;
 }
 
@@ -229,6 +445,13 @@ poro_status poro_server_destroy(poro_server* s) {
     s->scheduler.join();
     for (auto& w : s->workers)
         if (w.joinable()) w.join();
+    {
+        std::lock_guard<std::mutex> l(s->mu);
+        for (uint64_t t : s->ready) s->reqs[t]->cancel = true;
+        s->exec_stop = true;
+        s->exec_cv.notify_all();
+    }
+    s->executor.join();
     delete s;
     return PORO_OK;
 }

@@ -386,4 +386,55 @@ bool element_constants(const ReferenceData& ref, const double* v12, const poro_m
     return true;
 }
 
+// Damped Maxwell (Section "Other applications"): the Jacobians of
+// q_t + A q_x + B q_y + C q_z = E q with q = (E_x, E_y, E_z, H_x, H_y, H_z),
+// eps E_t = curl H - sigma E and mu H_t = -curl E.  M[d][p][q] is the
+// coefficient of d_d q_q in the equation of q_p moved to the left side.
+static void maxwell_jacobians(double eps, double mu, double M[3][6][6]) {
+    std::memset(M, 0, sizeof(double) * 3 * 36);
+    const double ie = 1.0 / eps, im = 1.0 / mu;
+    // E_x: -(1/eps)(d_y H_z - d_z H_y), E_y: -(1/eps)(d_z H_x - d_x H_z), E_z: -(1/eps)(d_x H_y - d_y H_x)
+    M[1][0][5] = -ie; M[2][0][4] = ie;
+    M[2][1][3] = -ie; M[0][1][5] = ie;
+    M[0][2][4] = -ie; M[1][2][3] = ie;
+    // H: +(1/mu) curl E
+    M[1][3][2] = im; M[2][3][1] = -im;
+    M[2][4][0] = im; M[0][4][2] = -im;
+    M[0][5][1] = im; M[1][5][0] = -im;
+}
+
+bool maxwell_element_constants(const ReferenceData& ref, const double* v12, const double mat[3], double dt,
+                               double* out, std::string& err) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) { err = "element: time step must be positive"; return false; }
+    const double eps = mat[0], mu = mat[1], sigma = mat[2];
+    if (!(eps > 0.0) || !(mu > 0.0) || !(sigma >= 0.0) || !std::isfinite(eps) || !std::isfinite(mu) ||
+        !std::isfinite(sigma)) {
+        err = "element: need eps > 0, mu > 0, sigma >= 0";
+        return false;
+    }
+    double jinv[3][3], vol, dins;
+    if (!tet_geometry(v12, jinv, vol, dins, err)) return false;
+    double M[3][6][6];
+    maxwell_jacobians(eps, mu, M);
+    const int T = ref.T;
+    std::memset(out, 0, sizeof(double) * maxwell::elem_const_stride(ref.N));
+    for (int j = 0; j < 3; ++j)
+        for (int n = 0; n < maxwell::STAR_NNZ; ++n) {
+            const int p = maxwell::star_row(n), q = maxwell::star_col(n);
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) s += jinv[j][d] * M[d][p][q];
+            out[j * maxwell::STAR_NNZ + n] = dt * s;
+        }
+    const double e = -dt * sigma / eps;
+    std::vector<double> zm(ref.z);
+    for (int u = 0; u < T; ++u) zm[u * T + u] -= e;
+    double* zi = out + 3 * maxwell::STAR_NNZ;
+    if (!invert_small(T, zm.data(), zi)) { err = "element: singular time block"; return false; }
+    double* sc = zi + T * T;
+    sc[0] = e;
+    sc[1] = 0.0;
+    sc[2] = dt;
+    return true;
+}
+
 }  // namespace poro

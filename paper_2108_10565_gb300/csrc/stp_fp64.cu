@@ -36,6 +36,8 @@ struct K1Params {
     int stride;
     KhatBlocks<double> khat;
     const double* zinv;
+    const RunPtrs* runs;       // items of several runs (nullptr: the pointers above)
+    const int32_t* item_run;
 };
 
 // CTA sizes the autotuner chooses from (index 0 is the default)
@@ -45,23 +47,24 @@ struct K1Sizes {
     static constexpr int NT1 = N >= 5 ? 128 : (N == 4 ? 256 : 128);
 };
 
-template <int N, int NT_>
-struct K1Shape : Alg3Shape<N> {
-    using A = Alg3Shape<N>;
+template <int N, int NT_, class Sys = BiotSystem>
+struct K1Shape : Alg3Shape<N, Sys::NQ> {
+    using A = Alg3Shape<N, Sys::NQ>;
     static constexpr int NT = NT_;
     static constexpr int T_ = N + 1;
-    // shared layout (doubles): bq[13*QS] | X[13*XSMAX] | star[162] | zuf[T*T] | sc[4] | zin[T*T]
+    // shared layout (doubles): bq[NQ*QS] | X[NQ*XSMAX] | star[3*NNZ] | zuf[T*T] | sc[4] | zin[T*T]
     static constexpr int OFF_X = A::SQ;
-    static constexpr int OFF_STAR = OFF_X + NQ * A::XSMAX;
-    static constexpr int OFF_ZUF = OFF_STAR + 3 * STAR_NNZ;
+    static constexpr int OFF_STAR = OFF_X + Sys::NQ * A::XSMAX;
+    static constexpr int OFF_ZUF = OFF_STAR + 3 * Sys::NNZ;
     static constexpr int OFF_SC = OFF_ZUF + T_ * T_;
     static constexpr int OFF_ZIN = OFF_SC + 4;
     static constexpr int SMEM_DOUBLES = OFF_ZIN + T_ * T_;
 };
 
-template <int N, int NT_>
+template <int N, int NT_, class Sys = BiotSystem>
 __global__ void __launch_bounds__(NT_) stp_fp64_kernel(const K1Params P) {
-    using S = K1Shape<N, NT_>;
+    using S = K1Shape<N, NT_, Sys>;
+    constexpr int NQ = Sys::NQ, STAR_NNZ = Sys::NNZ;
     constexpr int B = S::B, T = S::T, NT = S::NT, QS = S::QS;
     extern __shared__ double sm[];
     double* bq = sm;
@@ -74,32 +77,35 @@ __global__ void __launch_bounds__(NT_) stp_fp64_kernel(const K1Params P) {
 
     for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
-        const double* q0 = P.q0 + e * (int64_t)(NQ * B);
-        const double* ec = P.econst + e * (int64_t)P.stride;
+        RunPtrs R{P.q0, P.econst, P.qt, P.iout};
+        if (P.runs) R = P.runs[P.item_run[it]];
+        const double* q0 = R.q0 + e * (int64_t)(NQ * B);
+        const double* ec = R.econst + e * (int64_t)P.stride;
         // element constants: star[162], zinv_uf[T*T], e, g, dt, pad are contiguous
         for (int i = tid; i < 3 * STAR_NNZ + T * T + 4; i += NT) star[i] = ec[i];
         for (int i = tid; i < T * T; i += NT) zin[i] = P.zinv[i];
-        init_rhs<N, NT>(bq, q0);
+        init_rhs<N, NT, double, double, NQ>(bq, q0);
         __syncthreads();
-        alg3_sweep<N, NT, double, 1>(bq, X, star, zuf, zin, sc[1], P.khat);
+        alg3_sweep<N, NT, double, 1, Sys>(bq, X, star, zuf, zin, sc[1], P.khat);
         // time integration and outputs (global layout [p][l][u], dense)
         const double dt = sc[2];
-        if (P.iout) {
-            double* io = P.iout + e * (int64_t)(NQ * B);
+        if (R.iout) {
+            double* io = R.iout + e * (int64_t)(NQ * B);
             for (int i = tid; i < NQ * B; i += NT) io[i] = dt * bq[(i / B) * QS + (i % B) * T];
         }
-        if (P.qt) {
-            double* qo = P.qt + e * (int64_t)S::QBT;
+        if (R.qt) {
+            double* qo = R.qt + e * (int64_t)S::QBT;
             for (int i = tid; i < S::QBT; i += NT) qo[i] = bq[(i / (B * T)) * QS + i % (B * T)];
         }
         __syncthreads();
     }
 }
 
-template <int N, int NT_>
+template <int N, int NT_, class Sys = BiotSystem>
 int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-              const double* econst, double* qt, double* iout, void* stream) {
-    using S = K1Shape<N, NT_>;
+              const double* econst, double* qt, double* iout, void* stream, const RunPtrs* runs,
+              const int32_t* item_run) {
+    using S = K1Shape<N, NT_, Sys>;
     K1Params P;
     P.elems = elems;
     P.q0 = q0;
@@ -107,7 +113,7 @@ int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, c
     P.qt = qt;
     P.iout = iout;
     P.count = count;
-    P.stride = elem_const_stride(N);
+    P.stride = Sys::NQ == NQ ? elem_const_stride(N) : maxwell::elem_const_stride(N);
     P.khat.val = ref.khat_val;
     P.khat.col = ref.khat_col;
     P.khat.row = ref.khat_row;
@@ -119,35 +125,56 @@ int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, c
     for (int g = 0; g <= MAX_N; ++g)
         for (int j = 0; j < 3; ++j) P.khat.list_base[g][j] = ref.list_base[W][g][j];
     P.zinv = ref.zinv;
+    P.runs = runs;
+    P.item_run = item_run;
     const size_t smem = sizeof(double) * S::SMEM_DOUBLES;
-    cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N, NT_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(stp_fp64_kernel<N, NT_, Sys>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    stp_fp64_kernel<N, NT_><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
+    stp_fp64_kernel<N, NT_, Sys><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
     return (int)cudaGetLastError();
 }
 
 template <int N>
 int launch_n(const DeviceReference& ref, int variant, const int32_t* elems, int64_t count, const double* q0,
-             const double* econst, double* qt, double* iout, void* stream) {
+             const double* econst, double* qt, double* iout, void* stream, const RunPtrs* runs,
+             const int32_t* item_run) {
     if (variant == 1)
-        return launch_nt<N, K1Sizes<N>::NT1>(ref, elems, count, q0, econst, qt, iout, stream);
-    return launch_nt<N, K1Sizes<N>::NT0>(ref, elems, count, q0, econst, qt, iout, stream);
+        return launch_nt<N, K1Sizes<N>::NT1>(ref, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+    return launch_nt<N, K1Sizes<N>::NT0>(ref, elems, count, q0, econst, qt, iout, stream, runs, item_run);
 }
 
 }  // namespace
 
-int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
-                    const double* econst, double* qt, double* iout, void* stream, int variant) {
+int launch_stp_fp64_maxwell(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                            const double* econst, double* qt, double* iout, void* stream) {
+    // 6 quantities: 2 warps cover the 6 T (p, u) pairs of a mode at every N
     switch (ref.N) {
-        case 1: return launch_n<1>(ref, variant, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, variant, elems, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, variant, elems, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, variant, elems, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, variant, elems, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, variant, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_nt<1, 64, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 2: return launch_nt<2, 64, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 3: return launch_nt<3, 64, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 4: return launch_nt<4, 128, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr,
+                                                        nullptr);
+        case 5: return launch_nt<5, 128, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr,
+                                                        nullptr);
+        case 6: return launch_nt<6, 128, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr,
+                                                        nullptr);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                    const double* econst, double* qt, double* iout, void* stream, int variant, const RunPtrs* runs,
+                    const int32_t* item_run) {
+    switch (ref.N) {
+        case 1: return launch_n<1>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 2: return launch_n<2>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 3: return launch_n<3>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 4: return launch_n<4>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 5: return launch_n<5>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 6: return launch_n<6>(ref, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
         default: return (int)cudaErrorInvalidValue;
     }
 }

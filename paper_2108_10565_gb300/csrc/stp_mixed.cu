@@ -66,6 +66,9 @@ struct K2Params {
     int32_t tc_off[MAX_N + 1][3];
     int32_t* status;          // set to 1 if a bounded wait gave up
     long long wait_limit;     // SM clocks after which a wait of the sweeps gives up
+    const RunPtrs* runs;      // items of several runs (nullptr: q0, econst, qt, iout above)
+    const int32_t* item_run;
+    int cap_a, cap_b;         // at most this many A buffers / Khat image slots per block (1..3)
 };
 
 // Residual CSR of every degree in constant memory: the table depends only on
@@ -184,6 +187,7 @@ struct TcState {
     uint32_t mph, lph;  // phase parity of each barrier (bit b for MMA barrier b, bit 2 + s for slot s)
     uint32_t pend;      // thread 0: barriers (same bits) with an operation in flight
     bool gave_up;       // thread 0: one of its waits gave up, it issues nothing more
+    int cap_a, cap_b;   // operand-layout caps (the autotuner's tile choice)
     long long limit;    // SM clocks a wait of the sweeps may take
     volatile int* abort;
 };
@@ -226,7 +230,7 @@ struct TcLayout {
     uint32_t sbo, half;  // bytes: 8-row group stride; one Khat image (hi or lo)
 };
 template <int PT, int BF>
-__device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats) {
+__device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats, int cap_a, int cap_b) {
     constexpr int ES = BF ? 2 : 4;
     TcLayout L;
     L.KP = tc_kp(g, BF != 0);
@@ -238,10 +242,12 @@ __device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats) {
     const int over = 16 * (int)(L.sbo / 4) - L.ahf;
     auto fits = [&](int na, int nb) { return 2 * na * L.ahf + nb * L.bif <= xy_floats && (2 * na - 1) * L.ahf + 16 * (int)(L.sbo / 4) <= xy_floats && over >= 0; };
     L.nB = fits(1, 3) ? 3 : (fits(1, 2) ? 2 : 1);
+    L.nB = L.nB < cap_b ? L.nB : cap_b;
     // direction j >= nB loads once the MMAs of j - nB are done, known at step
     // j - nB + nA: that is no later than step j only if nA <= nB.  With three
     // A buffers (and three slots) the block runs all directions in one pass.
     L.nA = (L.nB == 3 && fits(3, 3)) ? 3 : ((L.nB >= 2 && fits(2, L.nB)) ? 2 : 1);
+    L.nA = L.nA < cap_a ? L.nA : cap_a;
     return L;
 }
 
@@ -305,7 +311,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the first block's Khat images load while its time solves run
     if (tid == 0 && N >= 1) {
-        const TcLayout L0 = tc_layout<PT, BF>(N, S.xy_floats);
+        const TcLayout L0 = tc_layout<PT, BF>(N, S.xy_floats, S.cap_a, S.cap_b);
         for (int j = 0; j < L0.nB; ++j) tc_load_khat<PT, BF>(S, L0, P, N, j);
     }
 #pragma unroll 1
@@ -331,7 +337,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         __syncthreads();
         if (g == 0) break;
         constexpr int KSTEP = BF ? 16 : 8;
-        const TcLayout L = tc_layout<PT, BF>(g, S.xy_floats);
+        const TcLayout L = tc_layout<PT, BF>(g, S.xy_floats, S.cap_a, S.cap_b);
         const int KP = L.KP, NP = L.NP;
         const uint32_t sbo = L.sbo, half = L.half;
         if (L.nA == 3) {
@@ -446,7 +452,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         // the region is free: the next block's Khat images load during this
         // block's epilogue and the next time solves
         if (tid == 0 && g > 1) {
-            const TcLayout Ln = tc_layout<PT, BF>(g - 1, S.xy_floats);
+            const TcLayout Ln = tc_layout<PT, BF>(g - 1, S.xy_floats, S.cap_a, S.cap_b);
             for (int j = 0; j < Ln.nB; ++j) tc_load_khat<PT, BF>(S, Ln, P, g - 1, j);
         }
         tc::fence_after_sync();
@@ -701,6 +707,8 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     tcs.pend = 0;
     tcs.gave_up = false;
     tcs.limit = P.wait_limit > 0 ? P.wait_limit : tc::WAIT_LIMIT_CYCLES;
+    tcs.cap_a = P.cap_a;
+    tcs.cap_b = P.cap_b;
     tcs.abort = abort;
 
     // operand region starts finite (K padding of A meets zeros of B)
@@ -726,8 +734,10 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
 
     for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
-        const double* q0 = P.q0 + e * (int64_t)(NQ * B);
-        const double* ec = P.econst + e * (int64_t)P.stride;
+        RunPtrs R{P.q0, P.econst, P.qt, P.iout};
+        if (P.runs) R = P.runs[P.item_run[it]];
+        const double* q0 = R.q0 + e * (int64_t)(NQ * B);
+        const double* ec = R.econst + e * (int64_t)P.stride;
         // a wait of another CTA of this context gave up: skip the remaining
         // elements (the launch's results are reported as failed anyway)
         const int failed = (tid == 0 && P.status) ? *reinterpret_cast<volatile const int32_t*>(P.status) : 0;
@@ -783,9 +793,9 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         }
         if (!ok) break;
         // Q = Q1 (+ d1) (+ d2) in binary64; time integration
-        if (P.qt || P.iout) {
-            double* qo = P.qt ? P.qt + e * (int64_t)QBT : nullptr;
-            double* io = P.iout ? P.iout + e * (int64_t)(NQ * B) : nullptr;
+        if (R.qt || R.iout) {
+            double* qo = R.qt ? R.qt + e * (int64_t)QBT : nullptr;
+            double* io = R.iout ? R.iout + e * (int64_t)(NQ * B) : nullptr;
             // one (p, l) row of T time modes per thread
             bool bad = false;
             for (int i = tid; i < NQ * B; i += NT) {
@@ -839,7 +849,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
 
 template <int N, int REF, int NT_, int BF>
 int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, const double* q0, const double* econst,
-              double* qt, double* iout, void* stream) {
+              double* qt, double* iout, void* stream, const RunPtrs* runs, const int32_t* item_run) {
     using S = K2Shape<N, REF, NT_, BF>;
     K2Params P;
     P.elems = elems;
@@ -857,6 +867,10 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
         for (int j = 0; j < 3; ++j) P.tc_off[g][j] = ref.tc_off[g][j];
     P.status = ref.status;
     P.wait_limit = ref.wait_limit;
+    P.runs = runs;
+    P.item_run = item_run;
+    P.cap_a = ref.cap_a;
+    P.cap_b = ref.cap_b;
     // one CTA per element; every resident CTA holds TMEM_COLS columns of the
     // SM's 512, so the shared-memory request is raised where needed to keep
     // at most 512 / TMEM_COLS CTAs of this kernel resident on an SM (so no
@@ -884,23 +898,28 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
 
 template <int N, int NT_, int BF>
 int launch_nv(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
-              const double* econst, double* qt, double* iout, void* stream) {
+              const double* econst, double* qt, double* iout, void* stream, const RunPtrs* runs,
+              const int32_t* item_run) {
     switch (refine) {
-        case 0: return launch_nr<N, 0, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 1: return launch_nr<N, 1, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_nr<N, 2, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream);
+        case 0: return launch_nr<N, 0, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 1: return launch_nr<N, 1, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 2: return launch_nr<N, 2, NT_, BF>(ref, elems, count, q0, econst, qt, iout, stream, runs, item_run);
         default: return (int)cudaErrorInvalidValue;
     }
 }
 
 template <int N>
 int launch_n(const MixedReference& ref, int refine, int variant, const int32_t* elems, int64_t count,
-             const double* q0, const double* econst, double* qt, double* iout, void* stream) {
+             const double* q0, const double* econst, double* qt, double* iout, void* stream, const RunPtrs* runs,
+             const int32_t* item_run) {
     // the bf16 form is built for the default CTA size only
-    if (ref.bf16) return launch_nv<N, K2Sizes<N>::NT0, 1>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+    if (ref.bf16)
+        return launch_nv<N, K2Sizes<N>::NT0, 1>(ref, refine, elems, count, q0, econst, qt, iout, stream, runs,
+                                                 item_run);
     if (variant == 1)
-        return launch_nv<N, K2Sizes<N>::NT1, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
-    return launch_nv<N, K2Sizes<N>::NT0, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream);
+        return launch_nv<N, K2Sizes<N>::NT1, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream, runs,
+                                                 item_run);
+    return launch_nv<N, K2Sizes<N>::NT0, 0>(ref, refine, elems, count, q0, econst, qt, iout, stream, runs, item_run);
 }
 
 }  // namespace
@@ -925,14 +944,15 @@ int upload_residual_table(int N, const int32_t* rows, const int32_t* entries, in
 }
 
 int launch_stp_mixed(const MixedReference& ref, int refine, const int32_t* elems, int64_t count, const double* q0,
-                     const double* econst, double* qt, double* iout, void* stream, int variant) {
+                     const double* econst, double* qt, double* iout, void* stream, int variant, const RunPtrs* runs,
+                     const int32_t* item_run) {
     switch (ref.base->N) {
-        case 1: return launch_n<1>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
-        case 2: return launch_n<2>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
-        case 3: return launch_n<3>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
-        case 4: return launch_n<4>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
-        case 5: return launch_n<5>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
-        case 6: return launch_n<6>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream);
+        case 1: return launch_n<1>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 2: return launch_n<2>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 3: return launch_n<3>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 4: return launch_n<4>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 5: return launch_n<5>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
+        case 6: return launch_n<6>(ref, refine, variant, elems, count, q0, econst, qt, iout, stream, runs, item_run);
         default: return (int)cudaErrorInvalidValue;
     }
 }

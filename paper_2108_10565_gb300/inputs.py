@@ -153,19 +153,20 @@ def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, Tru
     assert all(len(coords[a]) == n[a] + 1 for a in range(3))
     vert = np.stack(np.broadcast_arrays(coords[0][gi], coords[1][gj], coords[2][gk]), -1).reshape(-1, 3)
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    tets = []
-    for i in range(nx):
-        for j in range(ny):
-            for k in range(nz):
-                for pm in perms:
-                    c = [i, j, k]
-                    ids = [vid(*c)]
-                    for ax in pm:
-                        c[ax] += 1
-                        ids.append(vid(*c))
-                    tets.append(ids)
-    tets = np.array(tets, dtype=np.int64)
-    # face matching on wrapped vertex keys
+    # tets in box order (i, j, k), then the 6 vertex paths of the Kuhn split
+    bi, bj, bk = [a.reshape(-1) for a in np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")]
+    steps = np.zeros((6, 4, 3), dtype=np.int64)
+    for p_, pm in enumerate(perms):
+        c = np.zeros(3, dtype=np.int64)
+        for v, ax in enumerate(pm):
+            c[ax] += 1
+            steps[p_, v + 1] = c
+    ci = bi[:, None, None] + steps[None, :, :, 0]
+    cj = bj[:, None, None] + steps[None, :, :, 1]
+    ck = bk[:, None, None] + steps[None, :, :, 2]
+    tets = vid(ci, cj, ck).reshape(-1, 4).astype(np.int64)
+    # face matching on wrapped vertex keys: the 3 sorted keys of every face,
+    # sorted; an interior face's key occurs twice
     ijk = np.stack(np.unravel_index(np.arange(vert.shape[0]), (nx + 1, ny + 1, nz + 1)), -1)
     wrapped = ijk.copy()
     for ax, m in enumerate(n):
@@ -173,27 +174,25 @@ def kuhn_box_mesh(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), periodic=(True, Tru
             wrapped[:, ax] %= m
     wkey = (wrapped[:, 0] * (ny + 1) + wrapped[:, 1]) * (nz + 1) + wrapped[:, 2]
     ne = tets.shape[0]
-    nb = -np.ones((ne, 4), dtype=np.int64)
-    seen = {}
-    for e in range(ne):
-        for f in range(4):
-            key = tuple(sorted(wkey[tets[e, [v for v in range(4) if v != f]]]))
-            if key in seen:
-                e2, f2 = seen.pop(key)
-                nb[e, f], nb[e2, f2] = e2, e
-            else:
-                seen[key] = (e, f)
+    opp = np.array([[v for v in range(4) if v != f] for f in range(4)])
+    fk = np.sort(wkey[tets[:, opp]], axis=2).reshape(-1, 3)  # [ne*4][3]
+    order = np.lexsort((fk[:, 2], fk[:, 1], fk[:, 0]))
+    sk = fk[order]
+    same = np.all(sk[1:] == sk[:-1], axis=1)
+    nb = -np.ones(ne * 4, dtype=np.int64)
+    a, b = order[:-1][same], order[1:][same]
+    nb[a], nb[b] = b // 4, a // 4
+    nb = nb.reshape(ne, 4)
     tag = np.zeros((ne, 4), dtype=np.int32)
     tags = tags or {}
-    for (e, f) in seen.values():
-        fv = ijk[tets[e, [v for v in range(4) if v != f]]]
-        side = None
+    be, bf = np.nonzero(nb < 0)
+    if be.size:
+        fv = ijk[tets[be[:, None], opp[bf]]]   # [nb][3][3]
+        side = np.full(be.size, "", dtype=object)
         for ax, name in enumerate("xyz"):
-            if np.all(fv[:, ax] == 0):
-                side = name + "-"
-            elif np.all(fv[:, ax] == n[ax]):
-                side = name + "+"
-        tag[e, f] = tags.get(side, 2)
+            side[np.all(fv[:, :, ax] == 0, axis=1)] = name + "-"
+            side[np.all(fv[:, :, ax] == n[ax], axis=1)] = name + "+"
+        tag[be, bf] = [tags.get(sd, 2) if sd else 2 for sd in side]
     return dict(vertices=vert, tets=tets, neighbors=nb, face_tag=tag)
 
 
@@ -276,3 +275,25 @@ def cfg3_mini_scenario(nz=8):
                 source=dict(x=np.array([0.0, 0.0, -1010.0]), w=EXPLOSIVE_WEIGHTS.copy(), f0=5.0, t0=0.25,
                             amplitude=1e9),
                 receivers=LOH_RECEIVERS.copy())
+
+
+# damped Maxwell (Section "Other applications"): per-element (eps, mu, sigma)
+SEED_MAXWELL = 2108105655
+
+
+def maxwell_isolated_elements(n, N, seed=SEED_MAXWELL, sigma_scale=1.0):
+    """Isolated tetrahedra (the geometry of `isolated_elements`) with
+    material rows (eps, mu, sigma): eps ~ U[1, 4], mu ~ U[1, 2], sigma =
+    sigma_scale * U[0.5, 1.5]; Q0 [n][6][B] ~ N(0, 1)."""
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    ss = np.random.SeedSequence(seed)
+    g_geo, g_mat, g_dof = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    vert = _blockwise(lambda r, k: random_tetrahedra(r, k), g_geo, n, (4, 3))
+    mat = _blockwise(lambda r, k: np.stack([r.uniform(1.0, 4.0, k), r.uniform(1.0, 2.0, k),
+                                            sigma_scale * r.uniform(0.5, 1.5, k)], axis=1), g_mat, n, (3,))
+    q0 = _blockwise(lambda r, k: r.standard_normal((k, 6, B)), g_dof, n, (6, B))
+    return dict(vertices=vert, materials=mat, Q0=q0, N=N)
+
+
+def maxwell_dict(row):
+    return {"eps": float(row[0]), "mu": float(row[1]), "sigma": float(row[2])}

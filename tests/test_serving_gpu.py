@@ -41,6 +41,13 @@ def _scenarios():
                               f0=3000.0, t0=3e-4, amplitude=1e6)],
                     rec=[np.array([0.4, 0.5, -0.1])], cycles=10))
     out.append(dict(out[0], prec=1, cycles=8))
+    # partners that share a batched group with the runs above (same degree,
+    # precision, refinement and clusters; other sources, receivers, lengths)
+    out.append(dict(out[0], src=[dict(sc0["source"], x=np.array([0.3, 0.6, 0.45]))], rec=sc0["receivers"][:2],
+                    cycles=9))
+    out.append(dict(out[1], src=[dict(out[1]["src"][0], x=np.array([0.5, 0.7, 2.0]))], cycles=3))
+    out.append(dict(out[2], prec=2, cycles=6))
+    out.append(dict(out[2], prec=2, cycles=11, rec=[np.array([1.1, 0.4, -0.7])]))
     return out
 
 
@@ -80,12 +87,18 @@ def _submit(L, srv, sc, t_end):
     return L.poro_submit(srv, s)
 
 
-def test_alone_equals_in_the_mix(L):
+@pytest.mark.parametrize("batched", [True, False])
+def test_alone_equals_in_the_mix(L, batched):
+    """Every request's seismograms are bitwise those of the same simulation
+    advanced alone: in batched mode (groups of equal degree, precision and
+    clusters share every predictor launch; here groups of 2 in FP64 GTS, FP64
+    3-cluster LTS and bf16 GTS, and single runs) and in stream mode."""
     scs = _scenarios()
     ends = [_t_end(L, sc) for sc in scs]
     alone = [_alone(L, sc, te) for sc, te in zip(scs, ends)]
-    srv = L.poro_server_create(0, 64 << 30, 3)
+    srv = L.poro_server_create(0, 64 << 30, 8)
     try:
+        L.poro_server_set_batching(srv, batched)
         tickets = [_submit(L, srv, sc, te) for sc, te in zip(scs, ends)]
         for t in tickets:
             assert L.poro_wait(srv, t, 300_000) == L.PORO_REQ_DONE, L.poro_request_error(srv, t)
