@@ -94,3 +94,35 @@ def dg_error(vertices, N, Q, Qref):
     err = np.einsum("e,l,epl->", dj, M, (np.asarray(Q) - Qref) ** 2)
     ref = np.einsum("e,l,epl->", dj, M, np.asarray(Qref) ** 2)
     return float(np.sqrt(err)), float(np.sqrt(ref))
+
+
+def error_norms(vertices, N, Q, field, t=None, qn=None, chunk=4096):
+    """L1, L2 and L-infinity norms of the DG field Q minus the exact field,
+    over all 13 quantities: at the points of the collapsed Gauss rule of
+    every element, e(x) = sum_l Q_pl phi_l(xi) - q_p(x);
+      L1 = sum_e |J_e| sum_q w_q sum_p |e_p|,
+      L2 = (sum_e |J_e| sum_q w_q sum_p e_p^2)^(1/2),
+      Linf = max over points and p of |e_p|.
+    Returns dict(err=(L1, L2, Linf), ref=(the same norms of q))."""
+    qn = qn or N + 4
+    pts, wts = tet_quadrature(qn)
+    phi = basis_values(N, pts)                                   # [nq][B]
+    vertices = np.asarray(vertices, float)
+    e1 = e2 = einf = r1 = r2 = rinf = 0.0
+    for c0 in range(0, len(vertices), chunk):
+        v = vertices[c0:c0 + chunk]
+        x0 = v[:, 0, :]
+        J = np.stack([v[:, 1] - x0, v[:, 2] - x0, v[:, 3] - x0], axis=2)
+        dj = np.abs(np.linalg.det(J))
+        x = x0[:, None, :] + np.einsum("qj,edj->eqd", pts, J)
+        q = field(x.reshape(-1, 3)).reshape(len(v), len(pts), 13)
+        qh = np.einsum("epl,ql->eqp", np.asarray(Q[c0:c0 + chunk]), phi)
+        d = qh - q
+        w = dj[:, None] * wts[None, :]
+        e1 += float(np.einsum("eq,eqp->", w, np.abs(d)))
+        e2 += float(np.einsum("eq,eqp->", w, d * d))
+        einf = max(einf, float(np.abs(d).max()))
+        r1 += float(np.einsum("eq,eqp->", w, np.abs(q)))
+        r2 += float(np.einsum("eq,eqp->", w, q * q))
+        rinf = max(rinf, float(np.abs(q).max()))
+    return {"err": (e1, float(np.sqrt(e2)), einf), "ref": (r1, float(np.sqrt(r2)), rinf)}

@@ -101,3 +101,34 @@ def test_oracle_converges_at_order_n_plus_1(N):
     rate = np.log2(errs[0] / errs[1])
     assert errs[1] < 0.01
     assert abs(rate - (N + 1)) < 0.25, (errs, rate)
+
+
+def test_error_norms_of_a_known_offset():
+    """error_norms against a closed form: the exact projection of a degree-N
+    polynomial field, compared with that field plus a constant c in one
+    quantity, differs by exactly c everywhere: L1 = |c| vol, L2 = |c|
+    sqrt(vol), Linf = |c|; and a field compared with its own projection
+    (degree <= N) has zero error."""
+    N = 2
+    mesh = inputs.kuhn_box_mesh(3, lo=(0, 0, 0), hi=(1.5, 1.5, 1.5))
+    v = mesh["vertices"][mesh["tets"]]
+    vol = 1.5 ** 3
+
+    def poly(x):
+        q = np.zeros((len(x), 13))
+        q[:, 0] = 1 + x[:, 0] * x[:, 1] - 2 * x[:, 2] ** 2
+        q[:, 9] = x[:, 0] - 3 * x[:, 1] * x[:, 2]
+        return q
+
+    c = 0.25
+    Q = planewave.project(v, N, poly)
+    r = planewave.error_norms(v, N, Q, poly)
+    assert max(r["err"]) < 1e-12
+
+    def shifted(x):
+        q = poly(x)
+        q[:, 4] += c
+        return q
+
+    r = planewave.error_norms(v, N, Q, shifted)
+    np.testing.assert_allclose(r["err"], (c * vol, c * np.sqrt(vol), c), rtol=1e-12)
