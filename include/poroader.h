@@ -413,7 +413,8 @@ poro_status poro_set_variant(poro_ctx* ctx, int32_t variant);
  * buffers take shared memory the block may not have, so the kernel still
  * uses only what fits.  Every choice gives bitwise the same predictor.
  * Available: FP64 contexts layouts 0 only (choices 0 and 6), the bf16 form
- * cta 0 only (choices 0..5), the tf32 form all 12. */
+ * cta 0 only (choices 0..5), the tf32 form all 12; layouts 1..5 with one
+ * refinement sweep (the default) only. */
 #define PORO_TILE_CHOICES 12
 
 /* Autotuner over the available tile choices: times each on the first

@@ -1822,6 +1822,7 @@ static bool tile_choice_valid(const poro_ctx* c, int choice) {
     if (choice < 0 || choice >= PORO_TILE_CHOICES) return false;
     const int cta = choice / 6, lay = choice % 6;
     if (c->prec == PORO_FP64) return lay == 0;       // the FP64 kernel has no tensor-core tiles
+    if (lay != 0 && c->refine != 1) return false;    // capped layouts: one refinement sweep only
     if (c->prec == PORO_BF16X3_REFINE) return cta == 0;  // bf16 sweeps: default CTA size only
     return true;
 }

@@ -65,7 +65,7 @@ struct K2Params {
     const float* khat_tc;     // tensor-core images of the Khat^j blocks (hi then lo)
     int32_t tc_off[MAX_N + 1][3];
     int32_t* status;          // set to 1 if a bounded wait gave up
-    long long wait_limit;     // SM clocks after which a wait of the sweeps gives up
+    long long wait_limit;     // SM clocks after which a wait of the sweeps gives up (> 0)
     const RunPtrs* runs;      // items of several runs (nullptr: q0, econst, qt, iout above)
     const int32_t* item_run;
     int cap_a, cap_b;         // at most this many A buffers / Khat image slots per block (1..3)
@@ -142,8 +142,8 @@ struct K2Shape : Alg3Shape<N> {
     static constexpr int OFF_TAB = OFF_ZI + R4(T_ * T_);   // ints: row_ptr[14], col[54]
     static constexpr int OFF_STAB = OFF_TAB + R4(NQ + 1 + STAR_NNZ);  // float4 [13][STAR_SLOTS]
     static constexpr int OFF_SC = OFF_STAB + 4 * NQ * STAR_SLOTS;  // ints: Q1 exponents [16], D1 exponents [16]
-    static constexpr int OFF_BAR = OFF_SC + 32;  // 5 mbarriers, TMEM slot, abort, non-finite and dirty flags
-    static constexpr int SMEM_FLOATS = OFF_BAR + 14;
+    static constexpr int OFF_BAR = OFF_SC + 32;  // 5 mbarriers, wait limit, TMEM slot, abort, non-finite, dirty, drain mask
+    static constexpr int SMEM_FLOATS = OFF_BAR + 18;
     static constexpr int TMEM_COLS = tc_np(N) <= 32 ? 32 : (tc_np(N) <= 64 ? 64 : 128);
     static_assert(A::PT <= 32 * (NW < 4 ? NW : 4), "every accumulator row (p, u) needs a reading warp");
     static_assert(NW == 2 || NW == 4 || NW == 8, "2, 4 or 8 warps");
@@ -174,10 +174,19 @@ __device__ __forceinline__ void solve_row8(float* row, const float* Zi) {
 }
 
 // Tensor-core state of one CTA (shared addresses, barrier phases).  Thread 0
-// issues every bulk copy and every MMA commit, and only while all of its own
-// waits have succeeded: then no barrier ever gets a second operation while
-// an earlier one may still be in flight, and `pend` (thread 0's record of the
-// barriers with an operation it has not seen complete) is exact.
+// issues every MMA commit and the Khat copies needed inside a block; thread
+// 96 (a warp with no epilogue rows) issues the next block's copies once the
+// block's MMAs are done.  An issuing thread issues only while all of its own
+// waits have succeeded.  Thread 0 waits for every copy before the MMAs that
+// read it, and thread 96's copies follow MMAs that thread 0 issued only after
+// such waits, so no barrier ever gets a second operation while an earlier one
+// may still be in flight.
+// Each thread keeps in `pend` the barriers it gave work that it has not seen
+// complete: bits 0, 1 MMA commits (cleared by the successful wait), bits 2-4
+// Khat copies into slots 0-2 (cleared by thread 0's wait on the copy, and by
+// every thread once the block's last MMAs are done, which implies that every
+// copy of the block was consumed); bit 31 records that one of the thread's
+// waits gave up.  The abort path merges the masks of threads 0 and 96.
 struct TcState {
     float* xy;      // operand region: A tiles (tf32 words, or bf16 values in the same bytes), then Khat images
     uint32_t xy_s;  // its shared address
@@ -185,18 +194,17 @@ struct TcState {
     uint32_t bar_s;     // mbarriers: MMAs done reading A buffer 0, 1; Khat image in slot 0, 1, 2
     uint32_t tmem;
     uint32_t mph, lph;  // phase parity of each barrier (bit b for MMA barrier b, bit 2 + s for slot s)
-    uint32_t pend;      // thread 0: barriers (same bits) with an operation in flight
-    bool gave_up;       // thread 0: one of its waits gave up, it issues nothing more
-    int cap_a, cap_b;   // operand-layout caps (the autotuner's tile choice)
-    long long limit;    // SM clocks a wait of the sweeps may take
+    uint32_t pend;      // barriers given work not seen complete; bit 31: a wait gave up
     volatile int* abort;
 };
+constexpr uint32_t GAVE_UP = 1u << 31;
 
 // A wait that gives up keeps its phase, so that the abort path can still
 // wait (with the full limit) for the operation it was waiting for
 __device__ __forceinline__ void tc_wait(TcState& S, uint32_t bit) {
     const uint32_t par = ((bit < 2 ? S.mph : S.lph) >> bit) & 1u;
-    if (tc::mbar_wait(S.bar_s + 8u * bit, par, S.limit)) {
+    // the wait limit is the 64-bit word after the five mbarriers
+    if (tc::mbar_wait_s(S.bar_s + 8u * bit, par, S.bar_s + 40u)) {
         if (bit < 2)
             S.mph ^= 1u << bit;
         else
@@ -204,18 +212,21 @@ __device__ __forceinline__ void tc_wait(TcState& S, uint32_t bit) {
         S.pend &= ~(1u << bit);
     } else {
         *S.abort = 1;
-        S.gave_up = true;
+        S.pend |= GAVE_UP;
     }
 }
 
-// abort path (thread 0): a wait with the full limit on every barrier that
-// still has a bulk copy or MMA in flight, so that they have landed before
-// the CTA frees its TMEM and exits.  Barriers with nothing in flight are
-// skipped.
-__device__ __forceinline__ void tc_drain(TcState& S) {
+// abort path (thread 0, after a CTA barrier, with `mask` the union of the
+// issuing threads' records): a wait with the full limit on every barrier
+// given work not seen complete, so that copies and MMAs still in flight have
+// landed before the CTA frees its TMEM and exits.  Barriers with nothing in
+// flight are skipped.  (A copy of thread 96 that thread 0 consumed before an
+// MMA wait gave up stays in thread 96's record; its barrier then has no
+// pending phase and the wait runs out its limit: bounded, and only on this
+// path.)
+__device__ __forceinline__ void tc_drain(TcState& S, uint32_t mask) {
     for (uint32_t bit = 0; bit < 5; ++bit)
-        if ((S.pend >> bit) & 1u)
-            tc::mbar_wait(S.bar_s + 8u * bit, ((bit < 2 ? S.mph : S.lph) >> bit) & 1u);
+        if ((mask >> bit) & 1u) tc::mbar_wait(S.bar_s + 8u * bit, ((bit < 2 ? S.mph : S.lph) >> bit) & 1u);
 }
 
 // Operand layout of degree block g in the region (floats): nA A buffers (hi
@@ -229,7 +240,7 @@ struct TcLayout {
     int KP, NP, ahf, bif, nA, nB;
     uint32_t sbo, half;  // bytes: 8-row group stride; one Khat image (hi or lo)
 };
-template <int PT, int BF>
+template <int PT, int BF, bool CAPS>
 __device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats, int cap_a, int cap_b) {
     constexpr int ES = BF ? 2 : 4;
     TcLayout L;
@@ -242,22 +253,22 @@ __device__ __forceinline__ TcLayout tc_layout(int g, int xy_floats, int cap_a, i
     const int over = 16 * (int)(L.sbo / 4) - L.ahf;
     auto fits = [&](int na, int nb) { return 2 * na * L.ahf + nb * L.bif <= xy_floats && (2 * na - 1) * L.ahf + 16 * (int)(L.sbo / 4) <= xy_floats && over >= 0; };
     L.nB = fits(1, 3) ? 3 : (fits(1, 2) ? 2 : 1);
-    L.nB = L.nB < cap_b ? L.nB : cap_b;
+    if (CAPS) L.nB = L.nB < cap_b ? L.nB : cap_b;
     // direction j >= nB loads once the MMAs of j - nB are done, known at step
     // j - nB + nA: that is no later than step j only if nA <= nB.  With three
     // A buffers (and three slots) the block runs all directions in one pass.
     L.nA = (L.nB == 3 && fits(3, 3)) ? 3 : ((L.nB >= 2 && fits(2, L.nB)) ? 2 : 1);
-    L.nA = L.nA < cap_a ? L.nA : cap_a;
+    if (CAPS) L.nA = L.nA < cap_a ? L.nA : cap_a;
     return L;
 }
 
-// bulk copy of direction j's Khat image of block g into its slot (thread 0,
-// unless one of its waits gave up)
+// bulk copy of direction j's Khat image of block g into its slot (one
+// thread, unless one of its waits gave up)
 template <int PT, int BF>
 __device__ __forceinline__ void tc_load_khat(TcState& S, const TcLayout& L, const K2Params& P, int g, int j) {
-    if (S.gave_up) return;
+    if (S.pend & GAVE_UP) return;
     const int slot = j % L.nB;
-    S.pend |= 1u << (2 + slot);
+    S.pend |= 4u << slot;
     const uint32_t bar = S.bar_s + 16u + 8u * (uint32_t)slot;
     const uint32_t dst = S.xy_s + 4u * (uint32_t)(2 * L.nA * L.ahf + slot * L.bif);
     tc::fence_async_smem();
@@ -303,7 +314,7 @@ __device__ __forceinline__ void store_item(float* ah, float* al, int it, int KP,
 // One binary32 sweep of Algorithm 3 with the Khat products on the tensor
 // cores.  On entry bq holds b, on exit Q.  Returns false (uniformly across the
 // CTA) if a bounded wait gave up.
-template <int N, int NT, int BF>
+template <int N, int NT, int BF, bool CAPS>
 __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, const float* zin, const float gcoup,
                               const K2Params& P, TcState& S) {
     using A = Alg3Shape<N>;
@@ -311,7 +322,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the first block's Khat images load while its time solves run
     if (tid == 0 && N >= 1) {
-        const TcLayout L0 = tc_layout<PT, BF>(N, S.xy_floats, S.cap_a, S.cap_b);
+        const TcLayout L0 = tc_layout<PT, BF, CAPS>(N, S.xy_floats, P.cap_a, P.cap_b);
         for (int j = 0; j < L0.nB; ++j) tc_load_khat<PT, BF>(S, L0, P, N, j);
     }
 #pragma unroll 1
@@ -337,7 +348,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         __syncthreads();
         if (g == 0) break;
         constexpr int KSTEP = BF ? 16 : 8;
-        const TcLayout L = tc_layout<PT, BF>(g, S.xy_floats, S.cap_a, S.cap_b);
+        const TcLayout L = tc_layout<PT, BF, CAPS>(g, S.xy_floats, P.cap_a, P.cap_b);
         const int KP = L.KP, NP = L.NP;
         const uint32_t sbo = L.sbo, half = L.half;
         if (L.nA == 3) {
@@ -355,7 +366,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             if (tid == 0) {
                 for (int j = 0; j < 3; ++j) tc_wait(S, 2u + (uint32_t)j);
             }
-            if (tid == 0 && !S.gave_up) {
+            if (tid == 0 && !(S.pend & GAVE_UP)) {
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 const int nk = KP / KSTEP;
@@ -385,6 +396,8 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
                 S.pend |= 1u;
             }
             tc_wait(S, 0u);
+            // the block's MMAs are done: every copy of the block was consumed
+            if (!(S.pend & GAVE_UP)) S.pend &= ~0x1Cu;
         } else {
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
@@ -413,7 +426,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             __syncthreads();
             if (*S.abort) return false;
             if (tid == 0) tc_wait(S, 2u + (uint32_t)slot);
-            if (tid == 0 && !S.gave_up) {
+            if (tid == 0 && !(S.pend & GAVE_UP)) {
                 tc::fence_after_sync();
                 const uint32_t id = BF ? tc::idesc_bf16(128, NP) : tc::idesc_tf32(128, NP);
                 // one K step = two core matrices along K, 256 B further: 16
@@ -448,11 +461,14 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
         for (int j = 3 - L.nA; j < 3; ++j) {
             tc_wait(S, (uint32_t)(j % L.nA));
         }
+        // the block's MMAs are done: every copy of the block was consumed
+        if (!(S.pend & GAVE_UP)) S.pend &= ~0x1Cu;
         }
         // the region is free: the next block's Khat images load during this
-        // block's epilogue and the next time solves
-        if (tid == 0 && g > 1) {
-            const TcLayout Ln = tc_layout<PT, BF>(g - 1, S.xy_floats, S.cap_a, S.cap_b);
+        // block's epilogue and the next time solves (issued by lane 0 of warp
+        // 3, whose TMEM lane quarter holds no rows: 13 T <= 96)
+        if (tid == (NW >= 4 ? 96 : 0) && g > 1) {
+            const TcLayout Ln = tc_layout<PT, BF, CAPS>(g - 1, S.xy_floats, P.cap_a, P.cap_b);
             for (int j = 0; j < Ln.nB; ++j) tc_load_khat<PT, BF>(S, Ln, P, g - 1, j);
         }
         tc::fence_after_sync();
@@ -464,7 +480,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
             const int c_begin = NW == 8 ? (warp >> 2) * ncol : 0;
             // a warp with a lane whose wait gave up reads no TMEM (the MMAs
             // may still be writing it); the CTA leaves the sweep below
-            const bool skip = __any_sync(0xffffffffu, S.gave_up);
+            const bool skip = __any_sync(0xffffffffu, (S.pend & GAVE_UP) != 0u);
             if (sp * 32 < PT && !skip) {
                 const int r = sp * 32 + lane;
                 const int p = r / T, u = r - (r / T) * T;
@@ -673,7 +689,7 @@ __device__ void stash_sweep(int* dst, int* sc, int* nonfinite, float* W, const d
     }
 }
 
-template <int N, int REF, int NT_, int BF>
+template <int N, int REF, int NT_, int BF, bool CAPS>
 __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixed_kernel(const K2Params P) {
     using S = K2Shape<N, REF, NT_, BF>;
     constexpr int B = S::B, T = S::T, NT = S::NT, QBT = S::QBT, QS = S::QS;
@@ -692,10 +708,12 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     int* tab = reinterpret_cast<int*>(smf + S::OFF_TAB);
     float4* stab = reinterpret_cast<float4*>(smf + S::OFF_STAB);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smf + S::OFF_BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 10);
-    volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 11);
-    int* nonfinite = reinterpret_cast<int*>(smf + S::OFF_BAR + 12);
-    int* dirty = reinterpret_cast<int*>(smf + S::OFF_BAR + 13);  // a result was not finite
+    long long* wlimit = reinterpret_cast<long long*>(smf + S::OFF_BAR + 10);  // wait limit (SM clocks)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 12);
+    volatile int* abort = reinterpret_cast<volatile int*>(smf + S::OFF_BAR + 13);
+    int* nonfinite = reinterpret_cast<int*>(smf + S::OFF_BAR + 14);
+    int* dirty = reinterpret_cast<int*>(smf + S::OFF_BAR + 15);  // a result was not finite
+    uint32_t* drain_mask = reinterpret_cast<uint32_t*>(smf + S::OFF_BAR + 16);  // thread 96's record, at exit
     const int tid = threadIdx.x;
 
     TcState tcs;
@@ -705,10 +723,6 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     tcs.bar_s = tc::smem_addr(bars);
     tcs.mph = tcs.lph = 0;
     tcs.pend = 0;
-    tcs.gave_up = false;
-    tcs.limit = P.wait_limit > 0 ? P.wait_limit : tc::WAIT_LIMIT_CYCLES;
-    tcs.cap_a = P.cap_a;
-    tcs.cap_b = P.cap_b;
     tcs.abort = abort;
 
     // operand region starts finite (K padding of A meets zeros of B)
@@ -720,6 +734,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
     }
     for (int i = tid; i < NQ + 1 + STAR_NNZ; i += NT) tab[i] = c_star_tab[i];
     if (tid == 0) {
+        *wlimit = P.wait_limit;
         *abort = 0;
         *dirty = 0;
         for (int b = 0; b < 5; ++b) tc::mbar_init(tcs.bar_s + 8u * (uint32_t)b, 1);
@@ -734,10 +749,8 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
 
     for (int64_t it = blockIdx.x; it < P.count; it += gridDim.x) {
         const int64_t e = P.elems ? (int64_t)P.elems[it] : it;
-        RunPtrs R{P.q0, P.econst, P.qt, P.iout};
-        if (P.runs) R = P.runs[P.item_run[it]];
-        const double* q0 = R.q0 + e * (int64_t)(NQ * B);
-        const double* ec = R.econst + e * (int64_t)P.stride;
+        const double* q0 = (P.runs ? P.runs[P.item_run[it]].q0 : P.q0) + e * (int64_t)(NQ * B);
+        const double* ec = (P.runs ? P.runs[P.item_run[it]].econst : P.econst) + e * (int64_t)P.stride;
         // a wait of another CTA of this context gave up: skip the remaining
         // elements (the launch's results are reported as failed anyway)
         const int failed = (tid == 0 && P.status) ? *reinterpret_cast<volatile const int32_t*>(P.status) : 0;
@@ -771,7 +784,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         if (failed) *abort = 1;
         __syncthreads();
         if (*abort) break;
-        if (!alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
+        if (!alg3_sweep_tc<N, NT, BF, CAPS>(W, sh, zuf, zin, g_dw.x, P, tcs)) break;
         if (REF >= 1) {
             stash_sweep<N, REF, NT_>(Q1, sq, nonfinite, W, q0);
             if (REF == 2) {
@@ -785,7 +798,7 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         for (int sweep = 1; sweep <= REF && ok; ++sweep) {
             residual<N, REF, NT_>(W, Q1, D1, sq, sd, stab, zneg, e_dw, g_dw, Yall, P);
             __syncthreads();
-            ok = alg3_sweep_tc<N, NT, BF>(W, sh, zuf, zin, g_dw.x, P, tcs);
+            ok = alg3_sweep_tc<N, NT, BF, CAPS>(W, sh, zuf, zin, g_dw.x, P, tcs);
             if (ok && REF == 2 && sweep == 1) {
                 stash_sweep<N, REF, NT_>(D1, sd, nonfinite, W, q0);
                 __syncthreads();
@@ -793,9 +806,11 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
         }
         if (!ok) break;
         // Q = Q1 (+ d1) (+ d2) in binary64; time integration
-        if (R.qt || R.iout) {
-            double* qo = R.qt ? R.qt + e * (int64_t)QBT : nullptr;
-            double* io = R.iout ? R.iout + e * (int64_t)(NQ * B) : nullptr;
+        double* qtb = P.runs ? P.runs[P.item_run[it]].qt : P.qt;
+        double* iob = P.runs ? P.runs[P.item_run[it]].iout : P.iout;
+        if (qtb || iob) {
+            double* qo = qtb ? qtb + e * (int64_t)QBT : nullptr;
+            double* io = iob ? iob + e * (int64_t)(NQ * B) : nullptr;
             // one (p, l) row of T time modes per thread
             bool bad = false;
             for (int i = tid; i < NQ * B; i += NT) {
@@ -840,7 +855,14 @@ __global__ void __launch_bounds__(NT_, (REF == 2 || NT_ > 256) ? 1 : 2) stp_mixe
             if (tid == 0) *dirty = 0;
         }
     }
-    if (tid == 0 && tcs.pend) tc_drain(tcs);
+    // the issuing threads' records of work not seen complete (empty unless a
+    // wait gave up: every copy and commit is waited for otherwise)
+    if (tid == (S::NW >= 4 ? 96 : 0)) *drain_mask = tcs.pend & 0x1Fu;
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t mask = (tcs.pend | *drain_mask) & 0x1Fu;
+        if (mask) tc_drain(tcs, mask);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && *abort && P.status) atomicExch(P.status, 1);
@@ -866,7 +888,7 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     for (int g = 0; g <= MAX_N; ++g)
         for (int j = 0; j < 3; ++j) P.tc_off[g][j] = ref.tc_off[g][j];
     P.status = ref.status;
-    P.wait_limit = ref.wait_limit;
+    P.wait_limit = ref.wait_limit > 0 ? ref.wait_limit : tc::WAIT_LIMIT_CYCLES;
     P.runs = runs;
     P.item_run = item_run;
     P.cap_a = ref.cap_a;
@@ -888,11 +910,16 @@ int launch_nr(const MixedReference& ref, const int32_t* elems, int64_t count, co
     size_t smem = sizeof(float) * S::SMEM_FLOATS;
     const size_t floor_smem = (size_t)sm_smem / (512 / S::TMEM_COLS + 1) + 64;
     if (smem + (size_t)reserved < floor_smem) smem = floor_smem - (size_t)reserved;
-    err = cudaFuncSetAttribute(stp_mixed_kernel<N, REF, NT_, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the default layout (as many buffers as fit) runs the kernel without caps;
+    // the autotuner's capped layouts run a second instantiation, built for one
+    // refinement sweep (the default) only
+    const bool caps = REF == 1 && (P.cap_a < 3 || P.cap_b < 3);
+    auto* kern = caps ? stp_mixed_kernel<N, REF, NT_, BF, REF == 1> : stp_mixed_kernel<N, REF, NT_, BF, false>;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     if (count <= 0) return 0;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    stp_mixed_kernel<N, REF, NT_, BF><<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
+    kern<<<(unsigned)grid, S::NT, smem, (cudaStream_t)stream>>>(P);
     return (int)cudaGetLastError();
 }
 

@@ -100,14 +100,11 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait for the phase with the given parity to complete: a
-// non-blocking probe, then blocking probes until `limit` SM clocks have
-// passed.  A limit of 1 gives up on any phase not complete at the first probe.
+// bounded wait for the phase with the given parity to complete: blocking
+// probes until `limit` SM clocks have passed.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = WAIT_LIMIT_CYCLES) {
     const long long t0 = clock64();
     for (;;) {
-        if (mbar_test(bar, parity)) return true;
-        if (clock64() - t0 > limit) return false;
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -117,6 +114,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// the same wait with a limit kept in shared memory (one 64-bit word at
+// limit_s): a limit below 4096 clocks probes without blocking (a blocking
+// probe may itself wait longer than such a limit), so a limit of 1 gives up
+// on any phase not complete at the first probe
+__device__ __forceinline__ bool mbar_wait_s(uint32_t bar, uint32_t parity, uint32_t limit_s) {
+    long long limit;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(limit) : "r"(limit_s));
+    if (limit >= 4096) return mbar_wait(bar, parity, limit);
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
