@@ -49,9 +49,17 @@ def parse():
     ap.add_argument("--no-steps", action="store_true", help="skip the time-stepping / LTS sections")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--lts-nz", type=int, default=12,
-                    help="layered graded mesh of the LTS section: 2nz x 2nz x nz Kuhn boxes, 24 nz^3 tets "
-                         "(12: 41,472; 44: 2,044,416)")
-    ap.add_argument("--serving-requests", type=int, default=12)
+                    help="layered graded mesh of the LTS vs GTS section: 2nz x 2nz x nz Kuhn boxes, 24 nz^3 tets "
+                         "(12: 41,472)")
+    ap.add_argument("--lts-full-nz", type=int, default=44,
+                    help="configured-size LTS run (44: 2,044,416 tets; 0: skip)")
+    ap.add_argument("--lts-full-fp64", action="store_true", help="also run the configured-size LTS in FP64")
+    ap.add_argument("--planewave-study", action="store_true",
+                    help="run the plane-wave convergence study instead of the benchmark")
+    ap.add_argument("--planewave-degrees", type=int, nargs="*", default=[1, 2, 3, 4, 5, 6])
+    ap.add_argument("--serving-requests", type=int, default=16)
+    ap.add_argument("--serving-cycles", type=int, default=4, help="steps of the largest cluster per served request")
+    ap.add_argument("--serving-no-fp64", action="store_true", help="skip the one-at-a-time FP64 baseline trace")
     return ap.parse_args()
 
 
@@ -389,81 +397,164 @@ def time_stepping_sections(L, local, args):
         L.poro_destroy(ctx)
         r[name] = {"seconds": el, "steps": nsteps, "element_updates_per_s": ne * nsteps / el}
     out[f"periodic_{ne}_N5_gts"] = r
-    # clustered LTS vs GTS on the layered graded mesh, same simulated time
-    mesh, mats = inputs.layered_graded_mesh(args.lts_nz, grading=512.0)
-    ne = mesh["tets"].shape[0]
-    r = {"n_elem": ne, "degree": 5}
-    for name, prec in (("fp64", 0), ("mixed", 1)):
-        res = {}
-        for C in (6, 1):
-            ctx, dt, cl = _setup_mesh_ctx(L, 5, prec, mesh, mats, C, local)
-            L.poro_add_point_source(ctx, np.array([0.0, 0.0, -1010.0]),
-                                    -np.r_[np.ones(3), np.zeros(6), -1, np.zeros(3)], 5.0, 0.25, 1e12)
-            L.poro_add_receiver(ctx, np.array([0.0, 0.0, -1.0]))
-            t_sim = 32 * dt * 2.0 ** 0  # one step of the largest cluster of the LTS run
-            L.poro_advance(ctx, t_sim * 1.0000001)  # warm-up cycle
+    # clustered LTS vs GTS on the layered graded mesh, same simulated time:
+    # the configured 32x grading (3 populated clusters) and a 512x grading
+    # that populates all 6; per-cluster GPU time of one cycle
+    for grading in (32.0, 512.0):
+        mesh, mats = inputs.layered_graded_mesh(args.lts_nz, grading=grading)
+        ne = mesh["tets"].shape[0]
+        r = {"n_elem": ne, "degree": 5, "grading": grading}
+        for name, prec in (("fp64", 0), ("mixed", 1)):
+            res = {}
+            for C in (6, 1):
+                ctx, dt, cl = _setup_mesh_ctx(L, 5, prec, mesh, mats, C, local)
+                L.poro_add_point_source(ctx, np.array([0.0, 0.0, -1010.0]), inputs.EXPLOSIVE_WEIGHTS, 5.0, 0.25,
+                                        1e12)
+                L.poro_add_receiver(ctx, np.array([0.0, 0.0, -1.0]))
+                t_sim = 32 * dt  # one step of the largest cluster of the LTS run
+                L.poro_advance(ctx, t_sim * 1.0000001)  # warm-up cycle
+                t0 = time.perf_counter()
+                L.poro_advance(ctx, 2 * t_sim * 1.0000001)
+                el = time.perf_counter() - t0
+                hist = np.bincount(cl, minlength=C).tolist()
+                upd = sum(n * 32 / 2 ** c for c, n in enumerate(hist))
+                res["lts" if C > 1 else "gts"] = {"seconds": el, "element_updates": upd,
+                                                  "element_updates_per_s": upd / el, "clusters": hist}
+                if C > 1:
+                    ms = L.poro_cluster_times(ctx, 3 * t_sim * 1.0000001, C)
+                    res["lts"]["cluster_gpu_ms_per_cycle"] = ms.tolist()
+                    res["lts"]["cluster_element_updates_per_cycle"] = [n * 32 / 2 ** c for c, n in enumerate(hist)]
+                L.poro_destroy(ctx)
+            res["lts_speedup_time_to_solution"] = res["gts"]["seconds"] / res["lts"]["seconds"]
+            res["lts_work_fraction_of_gts"] = res["lts"]["element_updates"] / res["gts"]["element_updates"]
+            r[name] = res
+        out[f"layered_graded_{int(grading)}x_lts_vs_gts"] = r
+    # the configured size: 88 x 88 x 44 boxes (2,044,416 tets), 32x grading,
+    # clustered LTS, one warm-up and one timed cycle, per-cluster times
+    if args.lts_full_nz > 0:
+        mesh, mats = inputs.layered_graded_mesh(args.lts_full_nz, grading=32.0)
+        ne = mesh["tets"].shape[0]
+        r = {"n_elem": ne, "degree": 5, "grading": 32.0}
+        for name, prec in (("mixed", 1), ("fp64", 0)):
+            if name == "fp64" and not args.lts_full_fp64:
+                continue
+            t0 = time.perf_counter()
+            ctx, dt, cl = _setup_mesh_ctx(L, 5, prec, mesh, mats, 6, local)
+            setup_s = time.perf_counter() - t0
+            L.poro_add_point_source(ctx, np.array([0.0, 0.0, -1010.0]), inputs.EXPLOSIVE_WEIGHTS, 5.0, 0.25, 1e12)
+            for x in inputs.LOH_RECEIVERS:
+                L.poro_add_receiver(ctx, x)
+            t_sim = 32 * dt
+            L.poro_advance(ctx, t_sim * 1.0000001)
             t0 = time.perf_counter()
             L.poro_advance(ctx, 2 * t_sim * 1.0000001)
             el = time.perf_counter() - t0
+            ms = L.poro_cluster_times(ctx, 3 * t_sim * 1.0000001, 6)
             L.poro_destroy(ctx)
-            hist = np.bincount(cl, minlength=C).tolist()
+            hist = np.bincount(cl, minlength=6).tolist()
             upd = sum(n * 32 / 2 ** c for c, n in enumerate(hist))
-            res["lts" if C > 1 else "gts"] = {"seconds": el, "element_updates": upd,
-                                              "element_updates_per_s": upd / el, "clusters": hist}
-        res["lts_speedup_time_to_solution"] = res["gts"]["seconds"] / res["lts"]["seconds"]
-        r[name] = res
-    out["layered_graded_lts_vs_gts"] = r
+            r[name] = {"seconds_per_cycle": el, "element_updates_per_cycle": upd, "element_updates_per_s": upd / el,
+                       "clusters": hist, "cluster_gpu_ms_per_cycle": ms.tolist(), "host_setup_s": setup_s,
+                       "gts_element_updates_same_time": ne * 32,
+                       "lts_work_fraction_of_gts": upd / (ne * 32.0)}
+        out["layered_graded_32x_full_size"] = r
     return out
 
 
-def serving_section(L, local, args):
-    """Served ensemble (scaled): a Poisson trace (mean 2 requests/s) of
-    independent simulations with uniform meshes of 3k-30k tets, N in {2,3,4},
-    seeded sources and material perturbations, a fixed number of steps of
-    their largest cluster each; continuous batching in mixed precision vs
-    the same trace one at a time in FP64."""
+def _serving_trace(L, args):
+    """The served-ensemble requests: mesh sizes uniform in 10k-500k tets (Kuhn
+    boxes of a 20 x 20 x 10 km domain, n_x = n_y = 2 n_z, free surface on
+    top), degree uniform in {3, 4, 5, 6}, a 500 m layer over a half-space
+    with each request's materials perturbed by +-20 % per parameter, one
+    explosive source at 1-5 km depth, 4 surface receivers, rate-2 clusters
+    (at most 2), --serving-cycles steps of the largest cluster each (the
+    configured 1 s of simulated time is cut)."""
     from paper_2108_10565_gb300 import inputs
 
     rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING))
-    n_req = args.serving_requests
-    arrivals = np.cumsum(rng.exponential(0.5, n_req))
+    meshes = {}
     reqs = []
-    for i in range(n_req):
-        mesh = inputs.uniform_box_mesh_for(int(rng.uniform(3000, 30000)))
+    for i in range(args.serving_requests):
+        n_target = int(rng.uniform(10_000, 500_000))
+        key = max(1, int(round((n_target / 24.0) ** (1.0 / 3.0))))  # the mesh's n_z
+        if key not in meshes:
+            meshes[key] = inputs.uniform_box_mesh_for(n_target)
+        mesh = meshes[key]
         ne = mesh["tets"].shape[0]
-        N = int(rng.integers(2, 5))
-        mats = inputs.perturbed_materials(rng, ne, base=inputs.HALFSPACE_MATERIAL)
+        N = int(rng.integers(3, 7))
+        # the request's material: the layer over the half-space, each scaled by
+        # one U[0.8, 1.2] draw per parameter for the whole request
+        layer = inputs.perturbed_materials(rng, 1, base=inputs.LAYER_MATERIAL)[0]
+        half = inputs.perturbed_materials(rng, 1, base=inputs.HALFSPACE_MATERIAL)[0]
+        depth = -mesh["vertices"][mesh["tets"]].mean(axis=1)[:, 2]
+        mats = np.ascontiguousarray(np.where((depth < 500.0)[:, None], layer[None, :], half[None, :]))
         src = dict(x=np.array([rng.uniform(5e3, 15e3), rng.uniform(5e3, 15e3), -rng.uniform(1e3, 5e3)]),
-                   w=-np.r_[np.ones(3), np.zeros(6), -1, np.zeros(3)], f0=2.0, t0=0.6, amplitude=1e12)
+                   w=inputs.EXPLOSIVE_WEIGHTS.copy(), f0=2.0, t0=0.6, amplitude=1e12)
         rec = [np.array([x, y, -1.0]) for x, y in rng.uniform(2e3, 18e3, (4, 2))]
-        reqs.append(dict(N=N, mesh=mesh, mats=mats, src=[src], rec=rec, ne=ne))
-    # simulated time: 10 steps of each request's own step
+        reqs.append(dict(N=N, mesh=mesh, mats=mats, src=[src], rec=rec, ne=ne, C=2))
     for rq in reqs:
-        dt = L.poro_cfl_dt(rq["N"], rq["mesh"]["vertices"][rq["mesh"]["tets"]], rq["mats"]).min()
-        rq["t_end"] = 10.0 * dt * 1.0000001
-    out = {"requests": n_req, "arrival_rate_per_s": 2.0,
-           "mesh_elements": [int(r["ne"]) for r in reqs], "degrees": [int(r["N"]) for r in reqs]}
-    for mode, prec, slots in (("served_mixed", 1, 4), ("one_at_a_time_fp64", 0, 1)):
-        srv = L.poro_server_create(local, 200 << 30, slots)
-        tickets, keep = [], []
-        t0 = time.perf_counter()
-        for rq, ta in zip(reqs, arrivals):
-            now = time.perf_counter() - t0
-            if ta > now:
-                time.sleep(ta - now)
-            sc, k = L.make_scenario(rq["N"], rq["mesh"], rq["mats"], rq["t_end"], precision=prec,
-                                    sources=rq["src"], receivers=rq["rec"])
-            keep.append(k)
-            tickets.append(L.poro_submit(srv, sc))
-        states = [L.poro_wait(srv, t, 600_000) for t in tickets]
-        wall = time.perf_counter() - t0
-        lat = np.array([L.poro_request_times(srv, t)[2] for t in tickets])
-        L.poro_server_destroy(srv)
-        upd = sum(r["ne"] * 10 for r in reqs)
-        out[mode] = {"wall_s": wall, "done": int(sum(s == L.PORO_REQ_DONE for s in states)),
-                     "requests_per_s": n_req / wall, "element_updates_per_s": upd / wall,
-                     "p50_time_to_seismogram_s": float(np.percentile(lat, 50)),
-                     "p99_time_to_seismogram_s": float(np.percentile(lat, 99))}
+        dt = L.poro_cfl_dt(rq["N"], rq["mesh"]["vertices"][rq["mesh"]["tets"]], rq["mats"])
+        dt_min = dt.min()
+        cl = np.minimum(rq["C"] - 1, np.floor(np.log2(dt / dt_min) + 1e-12)).astype(int)
+        rq["hist"] = np.bincount(cl, minlength=rq["C"])
+        rq["t_end"] = args.serving_cycles * dt_min * 2 ** (rq["C"] - 1) * 1.0000001
+        rq["updates"] = args.serving_cycles * sum(int(h) * 2 ** (rq["C"] - 1 - c) for c, h in enumerate(rq["hist"]))
+    return reqs
+
+
+def _serve(L, local, reqs, arrivals, prec, slots, batched):
+    srv = L.poro_server_create(local, 200 << 30, slots)
+    L.poro_server_set_batching(srv, batched)
+    tickets, keep = [], []
+    t0 = time.perf_counter()
+    for rq, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        sc, k = L.make_scenario(rq["N"], rq["mesh"], rq["mats"], rq["t_end"], precision=prec,
+                                max_clusters=rq["C"], sources=rq["src"], receivers=rq["rec"])
+        keep.append(k)
+        tickets.append(L.poro_submit(srv, sc))
+    states = [L.poro_wait(srv, t, 1_800_000) for t in tickets]
+    wall = time.perf_counter() - t0
+    lat = np.array([L.poro_request_times(srv, t)[2] for t in tickets])
+    L.poro_server_destroy(srv)
+    upd = sum(r["updates"] for r in reqs)
+    return {"wall_s": wall, "done": int(sum(s == L.PORO_REQ_DONE for s in states)),
+            "requests_per_s": len(reqs) / wall, "element_updates_per_s": upd / wall,
+            "p50_time_to_seismogram_s": float(np.percentile(lat, 50)),
+            "p99_time_to_seismogram_s": float(np.percentile(lat, 99))}
+
+
+def serving_section(L, local, args):
+    """Served ensemble: the configured request distribution (see
+    _serving_trace) under continuous batching in the mixed bf16 form:
+      - capacity: all requests submitted at once, batched and stream mode;
+      - the Poisson trace (mean 2 requests/s), batched;
+      - a Poisson trace at 0.8 x the measured batched capacity;
+      - the baseline: the Poisson trace one request at a time in FP64."""
+    from paper_2108_10565_gb300 import inputs
+
+    reqs = _serving_trace(L, args)
+    n_req = len(reqs)
+    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING + 1))
+    gaps = rng.exponential(1.0, n_req)
+    at_once = np.zeros(n_req)
+    out = {"requests": n_req, "own_cycles_per_request": args.serving_cycles, "max_clusters": 2,
+           "mesh_elements": [int(r["ne"]) for r in reqs], "degrees": [int(r["N"]) for r in reqs],
+           "element_updates_total": int(sum(r["updates"] for r in reqs))}
+    bf = L.PORO_BF16X3_REFINE
+    out["capacity_batched_mixed"] = _serve(L, local, reqs, at_once, bf, 16, True)
+    out["capacity_streams_mixed"] = _serve(L, local, reqs, at_once, bf, 16, False)
+    out["batched_over_streams"] = (out["capacity_batched_mixed"]["element_updates_per_s"]
+                                   / out["capacity_streams_mixed"]["element_updates_per_s"])
+    out["poisson_2_per_s_batched_mixed"] = _serve(L, local, reqs, np.cumsum(gaps / 2.0), bf, 16, True)
+    lam = 0.8 * out["capacity_batched_mixed"]["requests_per_s"]
+    out["arrival_rate_0p8_capacity_per_s"] = lam
+    out["poisson_0p8_capacity_batched_mixed"] = _serve(L, local, reqs, np.cumsum(gaps / lam), bf, 16, True)
+    if not args.serving_no_fp64:
+        out["poisson_2_per_s_one_at_a_time_fp64"] = _serve(L, local, reqs, np.cumsum(gaps / 2.0), L.PORO_FP64, 1,
+                                                           False)
     return out
 
 
@@ -699,9 +790,66 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_planewave_study(args):
+    """The paper's plane-wave convergence experiment (Section "Convergence")
+    at scale on the GPU: fast P + two S waves of the Biot system (k = (pi, pi,
+    pi)) on the periodic cube [-1, 1]^3 cut into 6 n^3 Kuhn tetrahedra, global
+    time stepping to t ~ 1e-4 s, L1 / L2 / L-infinity errors against the
+    exact solution and their rates between successive meshes, N = 1..6.
+    Prints one JSON line (not the benchmark's headline)."""
+    import torch
+
+    from oracle import planewave
+    from paper_2108_10565_gb300 import _lib as L
+    from paper_2108_10565_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    K = np.array([np.pi, np.pi, np.pi])
+    md = inputs.material_dict(inputs.REFERENCE_MATERIAL)
+    modes = planewave.plane_wave_modes(md, K, 3)
+    meshes = {1: (4, 8, 16, 32, 64), 2: (4, 8, 16, 32, 64), 3: (4, 8, 16, 32), 4: (4, 8, 16, 32), 5: (4, 8, 16),
+              6: (4, 8, 16)}
+    out = {"experiment": "plane-wave convergence, periodic cube [-1,1]^3, 6 n^3 tets, t_end ~ 1e-4 s, FP64",
+           "degrees": {}}
+    for N in sorted(meshes):
+        if N not in args.planewave_degrees:
+            continue
+        rows = []
+        for n in meshes[N]:
+            mesh = inputs.kuhn_box_mesh(n, lo=(-1, -1, -1), hi=(1, 1, 1))
+            ne = len(mesh["tets"])
+            v = mesh["vertices"][mesh["tets"]]
+            t0 = time.perf_counter()
+            ctx = L.poro_create(0, N, L.PORO_FP64)
+            try:
+                L.poro_set_mesh(ctx, mesh["vertices"], mesh["tets"], mesh["neighbors"], mesh["face_tag"])
+                L.poro_set_materials(ctx, np.tile(inputs.REFERENCE_MATERIAL, (ne, 1)))
+                dt, _ = L.poro_set_clusters(ctx, 0.5, 1)
+                L.poro_set_dofs(ctx, planewave.project(v, N, lambda x: planewave.plane_wave(x, 0.0, K, modes)))
+                t1 = time.perf_counter()
+                L.poro_advance(ctx, 1e-4)
+                t_run = time.perf_counter() - t1
+                Q = L.poro_get_dofs(ctx)
+                t, _ = L.poro_get_time(ctx)
+            finally:
+                L.poro_destroy(ctx)
+            nr = planewave.error_norms(v, N, Q, lambda x: planewave.plane_wave(x, t, K, modes))
+            rel = [a / b for a, b in zip(nr["err"], nr["ref"])]
+            rows.append({"n": n, "elements": ne, "steps": int(round(t / dt)), "t": t, "rel_L1": rel[0],
+                         "rel_L2": rel[1], "rel_Linf": rel[2], "gpu_advance_s": t_run,
+                         "total_s": time.perf_counter() - t0})
+        for a, b in zip(rows[:-1], rows[1:]):
+            b["rates"] = {k: float(np.log2(a[f"rel_{k}"] / b[f"rel_{k}"])) for k in ("L1", "L2", "Linf")}
+        out["degrees"][str(N)] = rows
+        print(json.dumps({"N": N, "rows": rows}), file=sys.stderr, flush=True)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.planewave_study:
+        run_planewave_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

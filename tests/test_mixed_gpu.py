@@ -303,3 +303,36 @@ def test_bounded_wait_gives_up_and_context_recovers(L, precision):
         L.poro_destroy(ctx)
     errs = [rel_l2(qt[i], oracle_predictor(d, i)) for i in range(n)]
     assert max(errs) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+def test_tile_choices_agree_and_autotune(L, N, precision):
+    """Every tile choice of the autotuner (CTA size x operand-buffer layout
+    of the tensor-core sweeps: fewer A buffers or Khat slots serialise the
+    directions differently) gives bitwise the predictor of the default
+    choice; the autotuner times the available ones and keeps one of them."""
+    d = population(23, N, seed=4100 + N)
+    ctx = L.poro_create(0, N, precision)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"])
+        L.poro_predict(ctx)
+        ref = L.poro_get_predictor(ctx, 0, 23)
+        avail = [c for c in range(L.PORO_TILE_CHOICES) if precision == 1 or c < 6]
+        for c in avail:
+            L.poro_set_tiles(ctx, c)
+            L.poro_predict(ctx)
+            np.testing.assert_array_equal(L.poro_get_predictor(ctx, 0, 23), ref, err_msg=f"choice {c}")
+        with pytest.raises(L.PoroError):
+            if precision == 2:
+                L.poro_set_tiles(ctx, 6)
+            else:
+                L.poro_set_tiles(ctx, 12)
+        best, ms = L.poro_autotune_tiles(ctx, 0)
+        assert best in avail and ms[best] > 0
+        assert all((ms[c] > 0) == (c in avail) for c in range(L.PORO_TILE_CHOICES))
+        L.poro_predict(ctx)
+        np.testing.assert_array_equal(L.poro_get_predictor(ctx, 0, 23), ref)
+    finally:
+        L.poro_destroy(ctx)
