@@ -269,7 +269,7 @@ DW_OPS_PER_MAC = 12.0
 # one ncu capture each of the 20,000-element case (dram__bytes_read.sum +
 # dram__bytes_write.sum divided by the elements); the traffic grows in
 # proportion to the elements, so a launch of n elements moves n times this
-TRAFFIC_BYTES_PER_ELEMENT = {("mixed", 6, 1): 77336.0, ("mixed_bf16", 6, 1): 77169.0}
+TRAFFIC_BYTES_PER_ELEMENT = {("mixed", 6, 1): 77336.0, ("mixed_bf16", 6, 1): 77169.0, ("fp64", 6, None): 77491.0}
 # nominal tf32 : bf16 dense tensor ratio (1.1 : 2.25 PFLOP/s)
 TF32_PER_BF16 = 1.1 / 2.25
 
