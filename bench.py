@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--lu-n3", type=int, default=1024, help="elements factored at N=3 for the LU comparator")
     ap.add_argument("--no-steps", action="store_true", help="skip the time-stepping / LTS sections")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the degree and refinement sweeps")
+    ap.add_argument("--sweep-degrees", type=int, nargs="*", default=[3, 4, 5])
     ap.add_argument("--lts-nz", type=int, default=12,
                     help="layered graded mesh of the LTS vs GTS section: 2nz x 2nz x nz Kuhn boxes, 24 nz^3 tets "
                          "(12: 41,472)")
@@ -346,6 +348,74 @@ def lu_comparator(L, torch, dev, local, args, hbm_gbs):
             }
         finally:
             L.poro_destroy(ctx)
+    return out
+
+
+def predictor_sweeps(L, torch, dev, local, args, head_pop):
+    """The isolated population (200k elements) at the other configured
+    degrees in the three forms, and refinement sweeps K = 0 and 2 of both
+    mixed forms at the headline degree (K = 1 is the headline), with their
+    error against the FP64 kernel: element-updates/s (CUDA events, mean of 5
+    launches after 2 warm-ups)."""
+    from paper_2108_10565_gb300 import inputs
+
+    n = args.n_elem
+    out = {"degrees": {}, "refinement_N6": {}}
+    st = torch.cuda.Stream(device=local)
+
+    def timed(ctx, q0, qt, io):
+        for _ in range(2):
+            L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                               st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(5):
+                L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                                   st.cuda_stream)
+            e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    for N in sorted(set(args.sweep_degrees) | {args.degree}):
+        d = head_pop if N == args.degree else inputs.isolated_elements(n, N)
+        dt = L.poro_cfl_dt(N, d["vertices"], d["materials"])
+        q0 = torch.from_numpy(d["Q0"]).to(dev)
+        B, T = d["Q0"].shape[2], N + 1
+        qt = torch.empty((n, 13, B, T), dtype=torch.float64, device=dev)
+        io = torch.empty((n, 13, B), dtype=torch.float64, device=dev)
+        ref = None
+        row = {}
+        settings = [("fp64", L.PORO_FP64, None)]
+        if N == args.degree:
+            settings += [(f"{nm}_K{k}", pr, k) for nm, pr in (("mixed_tf32", L.PORO_FP32_REFINE),
+                                                            ("mixed_bf16x3", L.PORO_BF16X3_REFINE)) for k in (0, 2)]
+        else:
+            settings += [("mixed_tf32", L.PORO_FP32_REFINE, 1), ("mixed_bf16x3", L.PORO_BF16X3_REFINE, 1)]
+        for name, prec, k in settings:
+            ctx = L.poro_create(local, N, prec)
+            try:
+                if k is not None:
+                    L.poro_set_refinement(ctx, k)
+                L.poro_set_isolated(ctx, d["vertices"], d["materials"], dt)
+                ms = timed(ctx, q0, qt, io)
+            finally:
+                L.poro_destroy(ctx)
+            r = {"ms_per_launch": ms, "element_updates_per_s": n / (ms * 1e-3)}
+            if prec == L.PORO_FP64:
+                ref = qt.clone()
+            elif ref is not None:
+                e = (torch.linalg.vector_norm((qt - ref).reshape(n, -1), dim=1)
+                     / torch.linalg.vector_norm(ref.reshape(n, -1), dim=1)).cpu().numpy()
+                r["error_vs_fp64"] = {"median": float(np.median(e)), "max": float(e.max())}
+            if N == args.degree:
+                out["refinement_N6"][name] = r
+            else:
+                row[name] = r
+        if N != args.degree:
+            out["degrees"][str(N)] = row
+        del q0, qt, io, ref
+        torch.cuda.empty_cache()
     return out
 
 
@@ -758,6 +828,12 @@ def run_ours(args):
     lu = None
     if not args.no_lu and world == 1:
         lu = lu_comparator(L, torch, dev, local, args, float(peaks["hbm_gbs"]))
+    sweeps = None
+    if not args.no_sweeps and world == 1:
+        try:
+            sweeps = predictor_sweeps(L, torch, dev, local, args, d)
+        except Exception as ex:
+            sweeps = {"error": repr(ex)}
 
     if rank != 0:
         if world > 1:
@@ -782,7 +858,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"mixed": "tf32x3+f32+f64", "mixed_bf16x3": "bf16x3+f32+f64"}.get(head, "f64"), "data": "synthetic",
         "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": errs.get(head),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
-        "lu_comparator": lu, "time_stepping": steps, "serving": serving,
+        "lu_comparator": lu, "predictor_sweeps": sweeps, "time_stepping": steps, "serving": serving,
     }
     print(json.dumps(out))
     if world > 1:

@@ -239,7 +239,8 @@ poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const 
 
 /* End-to-end predictor from host buffers: Q0 of every element in, I out, with
  * the host<->device copies overlapped with the kernels.  The population is
- * cut into chunks of `chunk_elems` elements (0: automatic, about 8 chunks);
+ * cut into chunks of `chunk_elems` elements (0: automatic, about 16 chunks
+ * of at least 4096 elements);
  * chunk i's Q0 copy, predictor (solver as in poro_predict) and I copy run on
  * three streams, so one chunk's copies run under another chunk's kernel.
  * q0_host[n_elem][13][B] is read and becomes the context's DOFs;
