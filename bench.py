@@ -531,21 +531,23 @@ def time_stepping_sections(L, local, args):
     return out
 
 
-def _serving_trace(L, args):
+def _serving_trace(L, args, n_req=None, size=(10_000, 500_000), cycles=None):
     """The served-ensemble requests: mesh sizes uniform in 10k-500k tets (Kuhn
     boxes of a 20 x 20 x 10 km domain, n_x = n_y = 2 n_z, free surface on
     top), degree uniform in {3, 4, 5, 6}, a 500 m layer over a half-space
-    with each request's materials perturbed by +-20 % per parameter, one
+    with each request's materials perturbed by +-20 % per parameter (the
+    three skeleton moduli by one common factor), one
     explosive source at 1-5 km depth, 4 surface receivers, rate-2 clusters
     (at most 2), --serving-cycles steps of the largest cluster each (the
     configured 1 s of simulated time is cut)."""
     from paper_2108_10565_gb300 import inputs
 
-    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING))
+    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING + (0 if n_req is None else 2)))
     meshes = {}
     reqs = []
-    for i in range(args.serving_requests):
-        n_target = int(rng.uniform(10_000, 500_000))
+    cycles = args.serving_cycles if cycles is None else cycles
+    for i in range(args.serving_requests if n_req is None else n_req):
+        n_target = int(rng.uniform(*size))
         key = max(1, int(round((n_target / 24.0) ** (1.0 / 3.0))))  # the mesh's n_z
         if key not in meshes:
             meshes[key] = inputs.uniform_box_mesh_for(n_target)
@@ -554,8 +556,8 @@ def _serving_trace(L, args):
         N = int(rng.integers(3, 7))
         # the request's material: the layer over the half-space, each scaled by
         # one U[0.8, 1.2] draw per parameter for the whole request
-        layer = inputs.perturbed_materials(rng, 1, base=inputs.LAYER_MATERIAL)[0]
-        half = inputs.perturbed_materials(rng, 1, base=inputs.HALFSPACE_MATERIAL)[0]
+        layer = inputs.perturbed_materials(rng, 1, base=inputs.LAYER_MATERIAL, tie_skeleton=True)[0]
+        half = inputs.perturbed_materials(rng, 1, base=inputs.HALFSPACE_MATERIAL, tie_skeleton=True)[0]
         depth = -mesh["vertices"][mesh["tets"]].mean(axis=1)[:, 2]
         mats = np.ascontiguousarray(np.where((depth < 500.0)[:, None], layer[None, :], half[None, :]))
         src = dict(x=np.array([rng.uniform(5e3, 15e3), rng.uniform(5e3, 15e3), -rng.uniform(1e3, 5e3)]),
@@ -567,8 +569,8 @@ def _serving_trace(L, args):
         dt_min = dt.min()
         cl = np.minimum(rq["C"] - 1, np.floor(np.log2(dt / dt_min) + 1e-12)).astype(int)
         rq["hist"] = np.bincount(cl, minlength=rq["C"])
-        rq["t_end"] = args.serving_cycles * dt_min * 2 ** (rq["C"] - 1) * 1.0000001
-        rq["updates"] = args.serving_cycles * sum(int(h) * 2 ** (rq["C"] - 1 - c) for c, h in enumerate(rq["hist"]))
+        rq["t_end"] = cycles * dt_min * 2 ** (rq["C"] - 1) * 1.0000001
+        rq["updates"] = cycles * sum(int(h) * 2 ** (rq["C"] - 1 - c) for c, h in enumerate(rq["hist"]))
     return reqs
 
 
@@ -625,6 +627,18 @@ def serving_section(L, local, args):
     if not args.serving_no_fp64:
         out["poisson_2_per_s_one_at_a_time_fp64"] = _serve(L, local, reqs, np.cumsum(gaps / 2.0), L.PORO_FP64, 1,
                                                            False)
+    # many small requests (2k-20k tets, 16 steps each), all at once: the case
+    # where runs sharing launches matters
+    small = _serving_trace(L, args, n_req=48, size=(2_000, 20_000), cycles=16)
+    z = np.zeros(len(small))
+    out["small_requests"] = {"requests": len(small), "mesh_elements": [int(r["ne"]) for r in small],
+                             "degrees": [int(r["N"]) for r in small],
+                             "element_updates_total": int(sum(r["updates"] for r in small)),
+                             "capacity_batched_mixed": _serve(L, local, small, z, bf, 48, True),
+                             "capacity_streams_mixed": _serve(L, local, small, z, bf, 48, False)}
+    sm = out["small_requests"]
+    sm["batched_over_streams"] = (sm["capacity_batched_mixed"]["element_updates_per_s"]
+                                  / sm["capacity_streams_mixed"]["element_updates_per_s"])
     return out
 
 

@@ -1308,9 +1308,10 @@ poro_status poro_add_receiver(poro_ctx* c, const double xyz[3], int32_t* id_out)
 // modulo 2^c matter); the absolute tick for the sources is read from
 // d_tick, which the cycle advances at its end.
 // One tick k of the cycle for context c on stream st: predictors of the
-// clusters that start a step at k (skipped when a batched launch over
-// several runs already did them: predict = false), LTS buffers, correctors of
-// the clusters whose step ends at k + 1, point sources and receivers.
+// clusters that start a step at k, LTS buffers, correctors of the clusters
+// whose step ends at k + 1, point sources and receivers.  `what` selects the
+// parts (TICK_*): a batched group runs the predictors and correctors of all
+// its runs as single launches and the rest per run.
 // (prof, nullable: an event pair recorded around each cluster's launches,
 // for poro_cluster_times)
 struct ClusterEvent {
@@ -1330,8 +1331,11 @@ static int mark(std::vector<ClusterEvent>* prof, int cl, bool begin, cudaStream_
     return (int)cudaEventRecord(prof->back().b, st);
 }
 
-static int enqueue_tick(poro_ctx* c, int64_t k, bool predict, const double* d_rp, double* d_seis, int64_t cap,
+enum : unsigned { TICK_PREDICT = 1, TICK_BUFFERS = 2, TICK_CORRECT = 4, TICK_SOURCES = 8, TICK_ALL = 15 };
+
+static int enqueue_tick(poro_ctx* c, int64_t k, unsigned what, const double* d_rp, double* d_seis, int64_t cap,
                         int32_t* d_cnt, cudaStream_t st, std::vector<ClusterEvent>* prof = nullptr) {
+    const bool predict = (what & TICK_PREDICT) != 0;
     const int C = c->C;
     const int nrec = (int)c->rec_elem.size();
     const bool want_qt = C > 1;
@@ -1347,7 +1351,7 @@ static int enqueue_tick(poro_ctx* c, int64_t k, bool predict, const double* d_rp
         else if (predict)
             rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
                                         want_qt ? c->d_qt : nullptr, c->d_iout, st, c->variant);
-        if (rc == 0 && C > 1)
+        if (rc == 0 && C > 1 && (what & TICK_BUFFERS))
             rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, st);
         if (rc == 0) rc = mark(prof, cl, false, st);
     }
@@ -1358,7 +1362,13 @@ static int enqueue_tick(poro_ctx* c, int64_t k, bool predict, const double* d_rp
             rc = mark(prof, cl, true, st);
             poro::CorrectorData d = c->cd;
             d.tick = k;
-            rc = poro::launch_corrector(d, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(), st);
+            if (what & TICK_CORRECT)
+                rc = poro::launch_corrector(d, C > 1 ? c->d_cl_elems[cl] : nullptr, (int64_t)c->cl_elems[cl].size(),
+                                            st);
+            if (!(what & TICK_SOURCES)) {
+                if (rc == 0) rc = mark(prof, cl, false, st);
+                continue;
+            }
             for (auto& src : c->sources)
                 if (rc == 0 && c->h_cl[src.elem] == cl)
                     rc = poro::launch_point_source_tick(c->N, c->d_q0, src.elem, src.d_coef, src.f0, src.t0, c->dt, len,
@@ -1376,7 +1386,7 @@ static int enqueue_tick(poro_ctx* c, int64_t k, bool predict, const double* d_rp
 static int enqueue_cycle(poro_ctx* c, const double* d_rp, double* d_seis, int64_t cap, int32_t* d_cnt) {
     const int64_t cycle = (int64_t)1 << (c->C - 1);
     int rc = 0;
-    for (int64_t k = 0; k < cycle && rc == 0; ++k) rc = enqueue_tick(c, k, true, d_rp, d_seis, cap, d_cnt, c->stream);
+    for (int64_t k = 0; k < cycle && rc == 0; ++k) rc = enqueue_tick(c, k, TICK_ALL, d_rp, d_seis, cap, d_cnt, c->stream);
     if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
     return rc;
 }
@@ -1508,6 +1518,13 @@ struct RunGroup {
     int32_t* d_items = nullptr;      // elements of all runs' due clusters, tick residue by tick residue
     int32_t* d_item_run = nullptr;
     std::vector<int64_t> k_off, k_cnt;
+    // correctors: per tick residue k the elements of all runs' clusters whose
+    // step ends at k + 1, and each run's corrector data with tick k
+    // ([cycle][runs] tables)
+    CorrectorData* d_cdata = nullptr;
+    int32_t* d_citems = nullptr;
+    int32_t* d_citem_run = nullptr;
+    std::vector<int64_t> ck_off, ck_cnt;
     int64_t pending = 0;             // ticks enqueued since the last group_finish
     // captured cycle, valid while every run's receiver buffers stay the same
     cudaGraphExec_t exec = nullptr;
@@ -1530,7 +1547,13 @@ static int enqueue_group_cycle(RunGroup* g) {
                                       lead->variant, g->d_runs, ir);
         }
         for (poro_ctx* c : g->runs)
-            if (rc == 0) rc = enqueue_tick(c, k, false, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, g->stream);
+            if (rc == 0) rc = enqueue_tick(c, k, TICK_BUFFERS, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, g->stream);
+        const int64_t cc = g->ck_cnt[k];
+        if (rc == 0 && cc > 0)
+            rc = launch_corrector(lead->cd, g->d_citems + g->ck_off[k], cc, g->stream,
+                                  g->d_cdata + k * (int64_t)g->runs.size(), g->d_citem_run + g->ck_off[k]);
+        for (poro_ctx* c : g->runs)
+            if (rc == 0) rc = enqueue_tick(c, k, TICK_SOURCES, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, g->stream);
     }
     for (poro_ctx* c : g->runs)
         if (rc == 0) rc = launch_tick_advance(c->d_tick, g->cycle, g->stream);
@@ -1545,6 +1568,9 @@ void group_destroy(RunGroup* g) {
     dfree(g->d_runs);
     dfree(g->d_items);
     dfree(g->d_item_run);
+    dfree(g->d_cdata);
+    dfree(g->d_citems);
+    dfree(g->d_citem_run);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1594,10 +1620,30 @@ RunGroup* group_create(poro_ctx* const* runs, int n, std::string& err) {
             }
         g->k_cnt.push_back((int64_t)items.size() - g->k_off.back());
     }
+    std::vector<int32_t> citems, citem_run;
+    std::vector<CorrectorData> cdata;
+    for (int64_t k = 0; k < g->cycle; ++k) {
+        g->ck_off.push_back((int64_t)citems.size());
+        for (int i = 0; i < n; ++i) {
+            CorrectorData d = runs[i]->cd;
+            d.tick = k;
+            cdata.push_back(d);
+            for (int cl = 0; cl < g->C; ++cl) {
+                if ((k + 1) % ((int64_t)1 << cl)) continue;
+                const std::vector<int32_t>& el = runs[i]->cl_elems[cl];
+                citems.insert(citems.end(), el.begin(), el.end());
+                citem_run.insert(citem_run.end(), el.size(), (int32_t)i);
+            }
+        }
+        g->ck_cnt.push_back((int64_t)citems.size() - g->ck_off.back());
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = upload((void**)&g->d_runs, rp.data(), rp.size() * sizeof(RunPtrs));
     if (e == cudaSuccess) e = upload((void**)&g->d_items, items.data(), items.size() * sizeof(int32_t));
     if (e == cudaSuccess) e = upload((void**)&g->d_item_run, item_run.data(), item_run.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = upload((void**)&g->d_cdata, cdata.data(), cdata.size() * sizeof(CorrectorData));
+    if (e == cudaSuccess) e = upload((void**)&g->d_citems, citems.data(), citems.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = upload((void**)&g->d_citem_run, citem_run.data(), citem_run.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
         err = std::string("group_create: ") + cudaGetErrorString(e);
         group_destroy(g);
@@ -1697,7 +1743,7 @@ poro_status poro_cluster_times(poro_ctx* c, double t_end, double* ms_out) {
     int rc = 0;
     for (int64_t n = 0; n < n_cycles && rc == 0; ++n) {
         for (int64_t k = 0; k < cycle && rc == 0; ++k)
-            rc = enqueue_tick(c, k, true, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, c->stream, &prof);
+            rc = enqueue_tick(c, k, TICK_ALL, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, c->stream, &prof);
         if (rc == 0) rc = poro::launch_tick_advance(c->d_tick, cycle, c->stream);
     }
     cudaError_t er = cudaSuccess;

@@ -72,8 +72,9 @@ __device__ void neighbour_integral(const CorrectorData& D, int64_t e, int64_t nb
 // the reference triangle), so per face
 //   u_f = c_f (F^- (I Pf^T) + F^+ (I^nb Pnb^T))          [13 x df]
 //   dQ -= M^{-1} sum_f Pf^T u_f                          (one pass over all faces)
-template <int N>
-__global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, const int32_t* elems, int64_t count) {
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D1, const int32_t* elems, int64_t count,
+                                                        const CorrectorData* runs, const int32_t* item_run) {
     constexpr int B = n_modes(N), QB = NQ * B, DF = (N + 1) * (N + 2) / 2, FQ = NQ * DF;
     constexpr int stride = elem_const_stride(N);
     extern __shared__ double sm[];
@@ -88,6 +89,9 @@ __global__ void __launch_bounds__(CNT) corrector_kernel(const CorrectorData D, c
     __shared__ double wts[MAX_N + 1];
     const int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        // one run's data (D1), or item it's run of a batched launch over
+        // several runs (their tables in global memory)
+        const CorrectorData& D = BATCH ? runs[item_run[it]] : D1;
         const int64_t e = elems ? elems[it] : it;
         const double* ec = D.econst + e * stride;
         const double dt = ec[ec_scalars(N) + 2];
@@ -251,28 +255,31 @@ __global__ void receiver_kernel(int B, const double* q, int32_t nrec, const int6
 }
 
 template <int N>
-int launch_corr_n(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+int launch_corr_n(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream, const CorrectorData* runs,
+                  const int32_t* item_run) {
     constexpr int B = n_modes(N), DF = (N + 1) * (N + 2) / 2;
     const size_t smem = sizeof(double) * (4 * NQ * B + 9 * NQ * DF);
-    cudaError_t err = cudaFuncSetAttribute(corrector_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto* kern = runs ? corrector_kernel<N, true> : corrector_kernel<N, false>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    corrector_kernel<N><<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count);
+    kern<<<(unsigned)grid, CNT, smem, (cudaStream_t)stream>>>(d, elems, count, runs, item_run);
     return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream,
+                     const CorrectorData* runs, const int32_t* item_run) {
     if (count <= 0) return 0;
-    if (d.dw) return launch_corrector_dw(d, elems, count, stream);
+    if (d.dw) return launch_corrector_dw(d, elems, count, stream, runs, item_run);
     switch (d.N) {
-        case 1: return launch_corr_n<1>(d, elems, count, stream);
-        case 2: return launch_corr_n<2>(d, elems, count, stream);
-        case 3: return launch_corr_n<3>(d, elems, count, stream);
-        case 4: return launch_corr_n<4>(d, elems, count, stream);
-        case 5: return launch_corr_n<5>(d, elems, count, stream);
-        case 6: return launch_corr_n<6>(d, elems, count, stream);
+        case 1: return launch_corr_n<1>(d, elems, count, stream, runs, item_run);
+        case 2: return launch_corr_n<2>(d, elems, count, stream, runs, item_run);
+        case 3: return launch_corr_n<3>(d, elems, count, stream, runs, item_run);
+        case 4: return launch_corr_n<4>(d, elems, count, stream, runs, item_run);
+        case 5: return launch_corr_n<5>(d, elems, count, stream, runs, item_run);
+        case 6: return launch_corr_n<6>(d, elems, count, stream, runs, item_run);
         default: return (int)cudaErrorInvalidValue;
     }
 }

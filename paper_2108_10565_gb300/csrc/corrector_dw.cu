@@ -24,9 +24,10 @@ namespace {
 
 constexpr int DNT = 128;
 
-template <int N>
-__global__ void __launch_bounds__(DNT, 4) corrector_dw_kernel(const CorrectorData D, const int32_t* elems,
-                                                             int64_t count) {
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(DNT, 4) corrector_dw_kernel(const CorrectorData D1, const int32_t* elems,
+                                                             int64_t count, const CorrectorData* runs,
+                                                             const int32_t* item_run) {
     constexpr int B = n_modes(N), QB = NQ * B;
     constexpr int stride = elem_const_stride(N);
     constexpr int DF = (N + 1) * (N + 2) / 2, FQ = NQ * DF;
@@ -43,6 +44,9 @@ __global__ void __launch_bounds__(DNT, 4) corrector_dw_kernel(const CorrectorDat
     __shared__ double wts[MAX_N + 1];
     const int tid = threadIdx.x;
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        // one run's data (D1), or item it's run of a batched launch over
+        // several runs (their tables in global memory)
+        const CorrectorData& D = BATCH ? runs[item_run[it]] : D1;
         const int64_t e = elems ? elems[it] : it;
         const double* ec = D.econst + e * stride;
         const double dt = ec[ec_scalars(N) + 2];
@@ -246,29 +250,32 @@ __global__ void __launch_bounds__(DNT, 4) corrector_dw_kernel(const CorrectorDat
 }
 
 template <int N>
-int launch_n(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+int launch_n(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream, const CorrectorData* runs,
+             const int32_t* item_run) {
+    auto* kern = runs ? corrector_dw_kernel<N, true> : corrector_dw_kernel<N, false>;
     constexpr int B = n_modes(N);
     constexpr int DF = (N + 1) * (N + 2) / 2;
     const size_t smem = sizeof(float2) * (4 * NQ * B + 9 * NQ * DF);
     cudaError_t err =
-        cudaFuncSetAttribute(corrector_dw_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     const int64_t grid = count < (int64_t)(1u << 30) ? count : (int64_t)(1u << 30);
-    corrector_dw_kernel<N><<<(unsigned)grid, DNT, smem, (cudaStream_t)stream>>>(d, elems, count);
+    kern<<<(unsigned)grid, DNT, smem, (cudaStream_t)stream>>>(d, elems, count, runs, item_run);
     return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream) {
+int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream,
+                        const CorrectorData* runs, const int32_t* item_run) {
     if (count <= 0) return 0;
     switch (d.N) {
-        case 1: return launch_n<1>(d, elems, count, stream);
-        case 2: return launch_n<2>(d, elems, count, stream);
-        case 3: return launch_n<3>(d, elems, count, stream);
-        case 4: return launch_n<4>(d, elems, count, stream);
-        case 5: return launch_n<5>(d, elems, count, stream);
-        case 6: return launch_n<6>(d, elems, count, stream);
+        case 1: return launch_n<1>(d, elems, count, stream, runs, item_run);
+        case 2: return launch_n<2>(d, elems, count, stream, runs, item_run);
+        case 3: return launch_n<3>(d, elems, count, stream, runs, item_run);
+        case 4: return launch_n<4>(d, elems, count, stream, runs, item_run);
+        case 5: return launch_n<5>(d, elems, count, stream, runs, item_run);
+        case 6: return launch_n<6>(d, elems, count, stream, runs, item_run);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -272,8 +272,13 @@ struct CorrectorData {
 };
 int launch_lts_buffers(int N, int C, const int32_t* elems, int64_t count, const int32_t* slot, const double* iout,
                        double* buf, int64_t tick, void* stream);
-int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
-int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream);
+// `runs` (device array, nullable) / `item_run`: a launch over several runs;
+// item i is element elems[i] of the run whose data is runs[item_run[i]] (d
+// then only selects the precision and degree)
+int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream,
+                     const CorrectorData* runs = nullptr, const int32_t* item_run = nullptr);
+int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream,
+                        const CorrectorData* runs = nullptr, const int32_t* item_run = nullptr);
 int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
 int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef, double f0, double tc, double dt,
                              int64_t len, int64_t k_rel, const int64_t* tick, void* stream);

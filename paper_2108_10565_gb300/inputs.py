@@ -74,11 +74,21 @@ def random_tetrahedra(rng, n, h_range=(50.0, 200.0), max_aspect=4.0):
     return np.ascontiguousarray(out[:n])
 
 
-def perturbed_materials(rng, n, spread=0.2, base=REFERENCE_MATERIAL):
+def perturbed_materials(rng, n, spread=0.2, base=REFERENCE_MATERIAL, tie_skeleton=False):
     """Each of the 10 parameters scaled by an independent U[1-spread, 1+spread].
     For spread <= 0.2 around the reference material every draw is physical
-    (porosity in (0,1), positive coupling modulus and Biot mass determinant)."""
-    return np.ascontiguousarray(base[None, :] * rng.uniform(1.0 - spread, 1.0 + spread, (n, 10)))
+    (porosity in (0,1), positive coupling modulus and Biot mass determinant).
+
+    tie_skeleton: K_S, lambda_M and mu_M share the first draw, so the ratio of
+    drained to grain bulk modulus stays the base material's.  Needed for soft
+    bases such as LAYER_MATERIAL, whose drained modulus is close to K_S: with
+    independent draws the drained modulus can exceed K_S and the coupling
+    modulus M turns negative.  The same random numbers are consumed either way."""
+    f = rng.uniform(1.0 - spread, 1.0 + spread, (n, 10))
+    if tie_skeleton:
+        f[:, 2] = f[:, 0]
+        f[:, 3] = f[:, 0]
+    return np.ascontiguousarray(base[None, :] * f)
 
 
 def isolated_elements(n, N, seed=SEED_ISOLATED, q0_scale=1.0):

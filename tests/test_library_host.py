@@ -123,3 +123,20 @@ def test_library_khat_rows_match_oracle_fractions(L, N):
     ko = basis.khat_matrices(N)
     for a in range(3):
         assert khat_row_fractions(k[a]) == khat_row_fractions(ko[a])
+
+
+def test_perturbed_layer_materials_stay_physical():
+    """The served-ensemble recipe (layer and half-space, +-20 %, skeleton
+    moduli tied): every draw is in the model's domain, while independent
+    draws of the soft layer's moduli are not (drained modulus above K_S)."""
+    rng = np.random.default_rng(11)
+    for base in (inputs.LAYER_MATERIAL, inputs.HALFSPACE_MATERIAL, inputs.REFERENCE_MATERIAL):
+        for row in inputs.perturbed_materials(rng, 2000, base=base, tie_skeleton=True):
+            material.check_physical(inputs.material_dict(row))
+    bad = 0
+    for row in inputs.perturbed_materials(rng, 2000, base=inputs.LAYER_MATERIAL):
+        try:
+            material.check_physical(inputs.material_dict(row))
+        except ValueError:
+            bad += 1
+    assert bad > 0
