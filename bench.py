@@ -413,6 +413,12 @@ def predictor_sweeps(L, torch, dev, local, args, head_pop):
             else:
                 row[name] = r
         if N != args.degree:
+            if not args.no_cpu:
+                # the oracle's plain-loop C Algorithm 3 at this degree, all
+                # host cores, on a bounded prefix of the population
+                rate, cores, k, passes, el = cpu_alg3_rate(N, args.cpu_budget_s / 4, 0, args.cpu_elems // 2)
+                row["cpu_alg3_oracle"] = {"element_updates_per_s": rate, "cores": cores,
+                                          "sample": f"first {k} elements, {passes} passes, {el:.1f} s"}
             out["degrees"][str(N)] = row
         del q0, qt, io, ref
         torch.cuda.empty_cache()
