@@ -307,3 +307,40 @@ def maxwell_isolated_elements(n, N, seed=SEED_MAXWELL, sigma_scale=1.0):
 
 def maxwell_dict(row):
     return {"eps": float(row[0]), "mu": float(row[1]), "sigma": float(row[2])}
+
+
+SEED_VISCO = 2108105656
+
+
+def viscoelastic_isolated_elements(n, N, seed=SEED_VISCO, omega_scale=1.0):
+    """Isolated tetrahedra (the geometry of `isolated_elements`) with
+    viscoelastic material rows of 12 values (rho, lam_u, mu_u, omega_1..3,
+    Ylam_1..3, Ymu_1..3): rho ~ U[2000, 3000] kg/m^3, S speed ~ U[1500, 3500]
+    m/s, P speed = S speed x U[1.7, 2.0]; relaxation frequencies 2 pi f_c
+    (0.1, 1, 10) with f_c = 1 Hz, times omega_scale; anelastic coefficients
+    U[0.005, 0.03] of the unrelaxed modulus each (quality factors of about
+    20 to 100 over the band).  Q0 [n][27][B] ~ N(0, 1)."""
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    ss = np.random.SeedSequence(seed)
+    g_geo, g_mat, g_dof = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    vert = _blockwise(lambda r, k: random_tetrahedra(r, k), g_geo, n, (4, 3))
+
+    def mats(r, k):
+        rho = r.uniform(2000.0, 3000.0, k)
+        cs = r.uniform(1500.0, 3500.0, k)
+        cp = cs * r.uniform(1.7, 2.0, k)
+        mu = rho * cs ** 2
+        lam = rho * cp ** 2 - 2 * mu
+        om = np.tile(omega_scale * 2 * np.pi * np.array([0.1, 1.0, 10.0]), (k, 1))
+        ylam = lam[:, None] * r.uniform(0.005, 0.03, (k, 3))
+        ymu = mu[:, None] * r.uniform(0.005, 0.03, (k, 3))
+        return np.concatenate([rho[:, None], lam[:, None], mu[:, None], om, ylam, ymu], axis=1)
+
+    mat = _blockwise(mats, g_mat, n, (12,))
+    q0 = _blockwise(lambda r, k: r.standard_normal((k, 27, B)), g_dof, n, (27, B))
+    return dict(vertices=vert, materials=mat, Q0=q0, N=N)
+
+
+def viscoelastic_dict(row):
+    return {"rho": float(row[0]), "lam": float(row[1]), "mu": float(row[2]), "omega": np.array(row[3:6], float),
+            "Ylam": np.array(row[6:9], float), "Ymu": np.array(row[9:12], float)}
