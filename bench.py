@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the degree and refinement sweeps")
     ap.add_argument("--sweep-degrees", type=int, nargs="*", default=[3, 4, 5])
+    ap.add_argument("--no-systems", action="store_true", help="skip the damped Maxwell and viscoelastic predictors")
     ap.add_argument("--lts-nz", type=int, default=12,
                     help="layered graded mesh of the LTS vs GTS section: 2nz x 2nz x nz Kuhn boxes, 24 nz^3 tets "
                          "(12: 41,472)")
@@ -421,6 +422,56 @@ def predictor_sweeps(L, torch, dev, local, args, head_pop):
                                           "sample": f"first {k} elements, {passes} passes, {el:.1f} s"}
             out["degrees"][str(N)] = row
         del q0, qt, io, ref
+        torch.cuda.empty_cache()
+    return out
+
+
+def other_systems(L, torch, dev, local, args):
+    """The binary64 Algorithm-3 kernel on the paper's other systems with an
+    upper-triangular source matrix (Section "Other applications"): damped
+    Maxwell (6 quantities, 200,000 elements) and viscoelastic attenuation
+    (27 quantities, 50,000 elements), isolated tetrahedra of the headline
+    geometry at the headline degree.  Element-updates/s (CUDA events, mean of
+    5 launches after 2 warm-ups) and the FP64 pipe fraction against the
+    nominal 1.25 TFLOP/s (flops from poro_flop_count)."""
+    from paper_2108_10565_gb300 import inputs
+
+    N = args.degree
+    out = {}
+    st = torch.cuda.Stream(device=local)
+    for name, system, n, gen, setter in (
+            ("damped_maxwell", L.PORO_SYSTEM_MAXWELL, 200_000, inputs.maxwell_isolated_elements,
+             L.poro_set_isolated_maxwell),
+            ("viscoelastic_3mech", L.PORO_SYSTEM_VISCOELASTIC, 50_000, inputs.viscoelastic_isolated_elements,
+             L.poro_set_isolated_viscoelastic)):
+        d = gen(n, N)
+        dt = L.poro_cfl_dt_system(system, N, d["vertices"], d["materials"])
+        nq = d["Q0"].shape[1]
+        q0 = torch.from_numpy(d["Q0"]).to(dev)
+        qt = torch.empty((n, nq, d["Q0"].shape[2], N + 1), dtype=torch.float64, device=dev)
+        io = torch.empty_like(q0)
+        ctx = L.poro_create(local, N, L.PORO_FP64, system=system)
+        try:
+            setter(ctx, d["vertices"], d["materials"], dt)
+            for _ in range(2):
+                L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                                   st.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(st):
+                e0.record(st)
+                for _ in range(5):
+                    L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                                       st.cuda_stream)
+                e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            f = L.poro_flop_count(ctx, 0)[0]
+        finally:
+            L.poro_destroy(ctx)
+        ach = f * n / (ms * 1e-3) / 1e12
+        out[name] = {"elements": n, "quantities": nq, "ms_per_launch": ms, "element_updates_per_s": n / (ms * 1e-3),
+                     "flops_per_element": f, "fp64_tflops": ach, "fp64_frac_nominal": ach / 1.25}
+        del q0, qt, io
         torch.cuda.empty_cache()
     return out
 
@@ -855,6 +906,13 @@ def run_ours(args):
         except Exception as ex:
             sweeps = {"error": repr(ex)}
 
+    systems = None
+    if not args.no_systems and world == 1:
+        try:
+            systems = other_systems(L, torch, dev, local, args)
+        except Exception as ex:
+            systems = {"error": repr(ex)}
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -878,7 +936,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": {"mixed": "tf32x3+f32+f64", "mixed_bf16x3": "bf16x3+f32+f64"}.get(head, "f64"), "data": "synthetic",
         "config": cfg, "roofline": roofline(head), "forms": forms_out, "mixed_error": errs.get(head),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": hr["clocks"], "gpu_launches": args.steps,
-        "lu_comparator": lu, "predictor_sweeps": sweeps, "time_stepping": steps, "serving": serving,
+        "lu_comparator": lu, "predictor_sweeps": sweeps, "other_systems": systems, "time_stepping": steps,
+        "serving": serving,
     }
     print(json.dumps(out))
     if world > 1:

@@ -76,13 +76,21 @@ typedef enum {
 
 /* The linear hyperbolic system of a context.  Section "Other applications":
  * the predictor and Algorithm 3 apply to any such system whose source matrix
- * E is upper triangular; besides Biot's equations the library builds the
- * damped Maxwell equations (eps E_t = curl H - sigma E, mu H_t = -curl E,
- * quantities (E_x, E_y, E_z, H_x, H_y, H_z), E = diag(-sigma/eps x 3, 0 x 3))
- * for the isolated-element predictor in binary64. */
+ * E is upper triangular; besides Biot's equations the library builds, for
+ * the isolated-element predictor in binary64:
+ *  - the damped Maxwell equations (eps E_t = curl H - sigma E, mu H_t =
+ *    -curl E, quantities (E_x, E_y, E_z, H_x, H_y, H_z), E = diag(-sigma/eps
+ *    x 3, 0 x 3));
+ *  - viscoelastic attenuation with 3 relaxation mechanisms (anelastic
+ *    functions th_l: sigma_t = lam_u tr(D) I + 2 mu_u D - sum_l (Ylam_l tr(th_l)
+ *    I + 2 Ymu_l th_l), rho v_t = div sigma, th_l,t = omega_l (D - th_l), D the
+ *    strain rate; 27 quantities: stresses xx yy zz xy yz xz, velocities u v w,
+ *    then th_1, th_2, th_3 in the stress order; E upper triangular with
+ *    -omega_l on th_l's diagonal). */
 typedef enum {
-    PORO_SYSTEM_BIOT = 0,     /* 13 quantities, the paper's poroelastic system */
-    PORO_SYSTEM_MAXWELL = 1   /* 6 quantities, damped Maxwell */
+    PORO_SYSTEM_BIOT = 0,         /* 13 quantities, the paper's poroelastic system */
+    PORO_SYSTEM_MAXWELL = 1,      /* 6 quantities, damped Maxwell */
+    PORO_SYSTEM_VISCOELASTIC = 2  /* 27 quantities, viscoelastic attenuation */
 } poro_system;
 
 typedef enum {
@@ -102,13 +110,15 @@ typedef enum {
  * of |numerators| below 2^22 (the exact integer residual needs that). */
 poro_status poro_create(int device, int degree_N, poro_precision precision, poro_ctx** out);
 
-/* poro_create for a given system.  PORO_SYSTEM_MAXWELL contexts support
- * PORO_FP64 and the isolated-element calls (poro_set_isolated_maxwell,
- * poro_set_dofs, poro_predict*, poro_get_predictor, poro_get_integrated,
- * poro_flop_count); DOF arrays then have 6 quantities ([n][6][B] and
- * [n][6][B][N+1]).  Meshes, the LU comparator and the autotuner return
- * PORO_EUNSUPPORTED on them.  Errors: as poro_create, PORO_EUNSUPPORTED
- * (unknown system, Maxwell with a mixed precision). */
+/* poro_create for a given system.  PORO_SYSTEM_MAXWELL and
+ * PORO_SYSTEM_VISCOELASTIC contexts support PORO_FP64 and the
+ * isolated-element calls (poro_set_isolated_maxwell or
+ * poro_set_isolated_viscoelastic, poro_set_dofs, poro_predict*,
+ * poro_get_predictor, poro_get_integrated, poro_flop_count); DOF arrays then
+ * have 6 or 27 quantities ([n][Q][B] and [n][Q][B][N+1]).  Meshes, the LU
+ * comparator and the autotuner return PORO_EUNSUPPORTED on them.  Errors: as
+ * poro_create, PORO_EUNSUPPORTED (unknown system, a mixed precision for a
+ * system other than Biot's). */
 poro_status poro_create_system(int device, int degree_N, poro_precision precision, poro_system system,
                                poro_ctx** out);
 
@@ -180,6 +190,14 @@ poro_status poro_max_wave_speed(const poro_material* mat, double* speed);
 poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_material* mat,
                         double cfl_c, double* dt);
 
+/* poro_cfl_dt for a system's material rows (host): mat[n][3] (eps, mu, sigma)
+ * for PORO_SYSTEM_MAXWELL with v = 1 / sqrt(eps mu), mat[n][12] (rho, lam_u,
+ * mu_u, ...) for PORO_SYSTEM_VISCOELASTIC with the unrelaxed P speed
+ * v = sqrt((lam_u + 2 mu_u) / rho), poro_material rows for PORO_SYSTEM_BIOT.
+ * Errors: PORO_EINVAL (degenerate element or material), PORO_EUNSUPPORTED. */
+poro_status poro_cfl_dt_system(poro_system system, int degree_N, int64_t n, const double* vert,
+                               const double* mat, double cfl_c, double* dt);
+
 /* ------------------------------------------------------ isolated elements */
 
 /* Load n_elem unconnected tetrahedra (the population of the paper's
@@ -201,6 +219,17 @@ poro_status poro_set_isolated(poro_ctx* ctx, int64_t n_elem, const double* vert,
  * context). */
 poro_status poro_set_isolated_maxwell(poro_ctx* ctx, int64_t n, const double* vert, const double* mat,
                                       const double* dt);
+
+/* Isolated viscoelastic elements (Section "Other applications"): like
+ * poro_set_isolated with mat[n][12] = (rho, lam_u, mu_u, omega_1..3,
+ * Ylam_1..3, Ymu_1..3) per element (host, copied; rho > 0, mu_u > 0, unrelaxed
+ * bulk modulus > 0, omega_l >= 0).  Per element the library builds A^{j*} on
+ * the 51-entry union pattern of the system's Jacobians, e_l = -omega_l dt,
+ * the three (Z - e_l I)^{-1} and the couplings of E* into the stresses.
+ * Errors: PORO_EINVAL (degenerate element or material), PORO_EUNSUPPORTED
+ * (not a viscoelastic context). */
+poro_status poro_set_isolated_viscoelastic(poro_ctx* ctx, int64_t n, const double* vert, const double* mat,
+                                           const double* dt);
 
 /* Copy DOFs Q[n_elem][13][B] (host) into the context.  Errors: PORO_ESTATE
  * before poro_set_isolated. */

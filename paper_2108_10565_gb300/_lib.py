@@ -16,7 +16,7 @@ PORO_OK, PORO_EINVAL, PORO_ENOMEM, PORO_ECUDA, PORO_ETIMEOUT, PORO_ESTATE, PORO_
     0, -1, -2, -3, -4, -5, -6, -7)
 PORO_FP64, PORO_FP32_REFINE, PORO_BF16X3_REFINE = 0, 1, 2
 PORO_SOLVE_BLOCK, PORO_SOLVE_LU = 0, 1
-PORO_SYSTEM_BIOT, PORO_SYSTEM_MAXWELL = 0, 1
+PORO_SYSTEM_BIOT, PORO_SYSTEM_MAXWELL, PORO_SYSTEM_VISCOELASTIC = 0, 1, 2
 
 _c = ctypes
 _i32, _i64, _dbl, _vp = _c.c_int32, _c.c_int64, _c.c_double, _c.c_void_p
@@ -41,6 +41,8 @@ SIGNATURES = [
     ("poro_create_system", _i32, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_vp)]),
     ("poro_get_system", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32)]),
     ("poro_set_isolated_maxwell", _i32, [_vp, _i64, _vp, _vp, _vp]),
+    ("poro_set_isolated_viscoelastic", _i32, [_vp, _i64, _vp, _vp, _vp]),
+    ("poro_cfl_dt_system", _i32, [_i32, _i32, _i64, _vp, _vp, _dbl, _vp]),
     ("poro_destroy", _i32, [_vp]),
     ("poro_last_error", _c.c_char_p, [_vp]),
     ("poro_get_info", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32), _c.POINTER(_i64)]),
@@ -201,6 +203,14 @@ def poro_cfl_dt(N, vert, mat, cfl_c=0.5):
     return dt
 
 
+def poro_cfl_dt_system(system, N, vert, mat, cfl_c=0.5):
+    v, m = _f64(vert), _f64(mat)
+    n = v.shape[0]
+    dt = np.empty(n)
+    _check(lib().poro_cfl_dt_system(system, N, n, _ptr(v), _ptr(m), cfl_c, _ptr(dt)))
+    return dt
+
+
 def poro_set_isolated(ctx, vert, mat, dt):
     v, m, d = _f64(vert), _f64(mat), _f64(dt)
     return _check(lib().poro_set_isolated(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
@@ -210,6 +220,12 @@ def poro_set_isolated_maxwell(ctx, vert, mat, dt):
     """mat[n][3] = (eps, mu, sigma) per element."""
     v, m, d = _f64(vert), _f64(mat), _f64(dt)
     return _check(lib().poro_set_isolated_maxwell(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
+
+
+def poro_set_isolated_viscoelastic(ctx, vert, mat, dt):
+    """mat[n][12] = (rho, lam_u, mu_u, omega_1..3, Ylam_1..3, Ymu_1..3) per element."""
+    v, m, d = _f64(vert), _f64(mat), _f64(dt)
+    return _check(lib().poro_set_isolated_viscoelastic(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
 
 
 def poro_set_dofs(ctx, Q):

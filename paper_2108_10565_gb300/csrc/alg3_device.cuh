@@ -18,14 +18,22 @@ namespace poro {
 
 __host__ __device__ constexpr int bank_stride(int n, int T) { return n + ((T - n % 32) + 32) % 32; }
 
+template <int T, class Real>
+__device__ __forceinline__ void solve_row(Real* row, const Real* Zi);
+
 // The linear system of the predictor: its quantities, the union pattern of
 // its reference Jacobians and the structure of its source matrix E (upper
 // triangular, Section "Block-wise back-substitution"): per mode the time
 // solves are NPLAIN rows with Z^{-1} (E_pp = 0), NSHIFT rows with
 // (Z - e I)^{-1} and no coupling, and NPAIR pairs: src solved with
 // (Z - e I)^{-1}, then b_dst += g Q_src, then dst with Z^{-1}.
+// Per-element constants (in this order): star[3][NNZ], NSHM shifted time
+// matrices (Z - e I)^{-1}, NSC scalars with dt at DT_SC; TWO_PHASE systems
+// solve their blocks with solve_block (below) instead of the kinds above.
 struct BiotSystem {  // Biot's equations: G couples u_f -> u, v_f -> v, w_f -> w
     static constexpr int NQ = poro::NQ, NNZ = STAR_NNZ, NPLAIN = 7, NSHIFT = 0, NPAIR = 3;
+    static constexpr int NSHM = 1, NSC = 4, DT_SC = 2;
+    static constexpr bool TWO_PHASE = false;
     PORO_HD static constexpr int row(int n) { return star_row(n); }
     PORO_HD static constexpr int col(int n) { return star_col(n); }
     PORO_HD static constexpr int plain(int k) { return k < 6 ? k : QP; }
@@ -35,12 +43,65 @@ struct BiotSystem {  // Biot's equations: G couples u_f -> u, v_f -> v, w_f -> w
 };
 struct MaxwellSystem {  // damped Maxwell: E diagonal, -sigma/eps on the electric rows
     static constexpr int NQ = maxwell::NQ, NNZ = maxwell::STAR_NNZ, NPLAIN = 3, NSHIFT = 3, NPAIR = 0;
+    static constexpr int NSHM = 1, NSC = 4, DT_SC = 2;
+    static constexpr bool TWO_PHASE = false;
     PORO_HD static constexpr int row(int n) { return maxwell::star_row(n); }
     PORO_HD static constexpr int col(int n) { return maxwell::star_col(n); }
     PORO_HD static constexpr int plain(int k) { return 3 + k; }
     PORO_HD static constexpr int shifted(int k) { return k; }
     PORO_HD static constexpr int pair_src(int) { return 0; }
     PORO_HD static constexpr int pair_dst(int) { return 0; }
+};
+// Viscoelastic attenuation: per mode, phase 1 solves the velocities with
+// Z^{-1} and mechanism l's six anelastic functions with (Z - e_l I)^{-1};
+// after a barrier, phase 2 adds to each stress its couplings to the solved
+// functions (E* strictly upper part) and solves it with Z^{-1}.
+struct ViscoSystem {
+    static constexpr int NQ = visco::NQ, NNZ = visco::STAR_NNZ, NPLAIN = 0, NSHIFT = 0, NPAIR = 0;
+    static constexpr int NSHM = visco::NMECH, NSC = visco::NSC, DT_SC = visco::sc_dt();
+    static constexpr bool TWO_PHASE = true;
+    PORO_HD static constexpr int row(int n) { return visco::star_row(n); }
+    PORO_HD static constexpr int col(int n) { return visco::star_col(n); }
+    PORO_HD static constexpr int plain(int) { return 0; }
+    PORO_HD static constexpr int shifted(int) { return 0; }
+    PORO_HD static constexpr int pair_src(int) { return 0; }
+    PORO_HD static constexpr int pair_dst(int) { return 0; }
+    // modes [o, o + d) of one degree block; zsh: NMECH matrices (Z - e_l I)^{-1};
+    // cp: per mechanism the couplings (normal diagonal, normal off-diagonal,
+    // shear) of E*.  The caller's barrier follows.
+    template <int T, int NT, int QS, class Real>
+    __device__ static void solve_block(Real* bq, int o, int d, const Real* zin, const Real* zsh, const Real* cp) {
+        const int tid = threadIdx.x;
+        constexpr int NM = visco::NMECH;
+        for (int it = tid; it < (3 + 6 * NM) * d; it += NT) {
+            const int kind = it / d, m = o + it % d;
+            if (kind < 3) solve_row<T>(bq + (6 + kind) * QS + m * T, zin);
+            else solve_row<T>(bq + (9 + (kind - 3)) * QS + m * T, zsh + ((kind - 3) / 6) * T * T);
+        }
+        __syncthreads();
+        for (int it = tid; it < 6 * d; it += NT) {
+            const int c = it / d, m = o + it % d;
+            Real* row = bq + c * QS + m * T;
+#pragma unroll
+            for (int l = 0; l < NM; ++l) {
+                const Real* th = bq + (9 + 6 * l) * QS + m * T;
+                if (c < 3) {
+                    // normal stress c: (Ylam + 2 Ymu) on th_cc, Ylam on the other two
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const Real g = k == c ? cp[3 * l] : cp[3 * l + 1];
+#pragma unroll
+                        for (int u = 0; u < T; ++u) row[u] = fma(g, th[k * QS + u], row[u]);
+                    }
+                } else {
+                    const Real g = cp[3 * l + 2];
+#pragma unroll
+                    for (int u = 0; u < T; ++u) row[u] = fma(g, th[c * QS + u], row[u]);
+                }
+            }
+            solve_row<T>(row, zin);
+        }
+    }
 };
 
 template <int N, int NQ_ = NQ>
@@ -99,11 +160,13 @@ __device__ __forceinline__ void init_rhs(Real* bq, const In* q0) {
 // In-place sweep: on entry bq holds b, on exit the solution Q.  X is a
 // scratch area of JX * Sys::NQ * XSMAX values in shared memory; star[3][NNZ]
 // the element's reference Jacobians on the union pattern; zuf = (Z - e I)^{-1},
-// zin = Z^{-1}; gcoup = the coupling entry g of E* (Biot: E*_{u,uf}).  JX
+// zin = Z^{-1}; gcoup = the coupling entry g of E* (Biot: E*_{u,uf}); for
+// two-phase systems zuf holds their NSHM shifted matrices and cpl their
+// couplings.  JX
 // directions are handled per pass (1 or 3).  Ends with a barrier.
 template <int N, int NT, class Real, int JX, class Sys = BiotSystem>
 __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf, const Real* zin,
-                           const Real gcoup, const KhatBlocks<Real>& K) {
+                           const Real gcoup, const KhatBlocks<Real>& K, const Real* cpl = nullptr) {
     constexpr int NQ = Sys::NQ, STAR_NNZ = Sys::NNZ;
     using S = Alg3Shape<N, NQ>;
     constexpr int T = S::T, QS = S::QS, PT = S::PT, PUL = S::PUL, NW = NT / 32;
@@ -122,7 +185,10 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
         // and the coupled pairs (Biot: 6 stresses and p; u_f then u, v_f
         // then v, w_f then w)
         constexpr int NKIND = Sys::NPLAIN + Sys::NSHIFT + Sys::NPAIR;
-        for (int it = tid; it < NKIND * d; it += NT) {
+        if constexpr (Sys::TWO_PHASE) {
+            Sys::template solve_block<T, NT, QS, Real>(bq, o, d, zin, zuf, cpl);
+        } else {
+          for (int it = tid; it < NKIND * d; it += NT) {
             const int kind = it / d, m = o + it % d;
             if (kind < Sys::NPLAIN) {
                 solve_row<T>(bq + Sys::plain(kind) * QS + m * T, zin);
@@ -137,6 +203,7 @@ __device__ void alg3_sweep(Real* bq, Real* X, const Real* star, const Real* zuf,
                 for (int u = 0; u < T; ++u) rv[u] = fma(gcoup, rf[u], rv[u]);
                 solve_row<T>(rv, zin);
             }
+          }
         }
         __syncthreads();
         if (g == 0) break;

@@ -265,10 +265,10 @@ poro_status poro_create_system(int device, int degree_N, poro_precision precisio
                                poro_ctx** out) {
     if (!out) return fail(nullptr, PORO_EINVAL, "poro_create: out is NULL");
     *out = nullptr;
-    if (system != PORO_SYSTEM_BIOT && system != PORO_SYSTEM_MAXWELL)
+    if (system != PORO_SYSTEM_BIOT && system != PORO_SYSTEM_MAXWELL && system != PORO_SYSTEM_VISCOELASTIC)
         return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: unknown system");
-    if (system == PORO_SYSTEM_MAXWELL && precision != PORO_FP64)
-        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: the damped Maxwell system is built in FP64 only");
+    if (system != PORO_SYSTEM_BIOT && precision != PORO_FP64)
+        return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: systems other than Biot's are built in FP64 only");
     if (degree_N < 1 || degree_N > poro::MAX_N)
         return fail(nullptr, PORO_EUNSUPPORTED, "poro_create: degree N must be in 1..6");
     if (precision != PORO_FP64 && precision != PORO_FP32_REFINE && precision != PORO_BF16X3_REFINE)
@@ -284,7 +284,7 @@ poro_status poro_create_system(int device, int degree_N, poro_precision precisio
     c->N = degree_N;
     c->prec = precision;
     c->system = system;
-    c->nq = system == PORO_SYSTEM_MAXWELL ? poro::maxwell::NQ : NQ;
+    c->nq = system == PORO_SYSTEM_MAXWELL ? poro::maxwell::NQ : system == PORO_SYSTEM_VISCOELASTIC ? poro::visco::NQ : NQ;
     c->refine = 1;  // one sweep reaches the 1e-10 goal in both mixed forms (measured)
     std::string err;
     if (!poro::reference_data(degree_N, c->ref, err)) {
@@ -293,8 +293,9 @@ poro_status poro_create_system(int device, int degree_N, poro_precision precisio
     }
     c->B = c->ref.B;
     c->T = c->ref.T;
-    c->stride = system == PORO_SYSTEM_MAXWELL ? poro::maxwell::elem_const_stride(degree_N)
-                                              : poro::elem_const_stride(degree_N);
+    c->stride = system == PORO_SYSTEM_MAXWELL        ? poro::maxwell::elem_const_stride(degree_N)
+                : system == PORO_SYSTEM_VISCOELASTIC ? poro::visco::elem_const_stride(degree_N)
+                                                     : poro::elem_const_stride(degree_N);
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
@@ -576,6 +577,32 @@ poro_status poro_cfl_dt(int degree_N, int64_t n, const double* vert, const poro_
     return PORO_OK;
 }
 
+poro_status poro_cfl_dt_system(poro_system system, int degree_N, int64_t n, const double* vert, const double* mat,
+                               double cfl_c, double* dt) {
+    if (system == PORO_SYSTEM_BIOT)
+        return poro_cfl_dt(degree_N, n, vert, reinterpret_cast<const poro_material*>(mat), cfl_c, dt);
+    if (system != PORO_SYSTEM_MAXWELL && system != PORO_SYSTEM_VISCOELASTIC)
+        return fail(nullptr, PORO_EUNSUPPORTED, "poro_cfl_dt_system: unknown system");
+    if (degree_N < 1 || degree_N > poro::MAX_N) return fail(nullptr, PORO_EUNSUPPORTED, "poro_cfl_dt_system: degree");
+    if (n < 0 || (n > 0 && (!vert || !mat || !dt)) || !(cfl_c > 0.0))
+        return fail(nullptr, PORO_EINVAL, "poro_cfl_dt_system: bad argument");
+    const int nm = system == PORO_SYSTEM_MAXWELL ? 3 : 12;
+    for (int64_t i = 0; i < n; ++i) {
+        double jinv[3][3], vol, dins;
+        std::string err;
+        const double* m = mat + nm * i;
+        // fastest characteristic speed: 1 / sqrt(eps mu), or the unrelaxed P speed
+        const double v = system == PORO_SYSTEM_MAXWELL ? 1.0 / std::sqrt(m[0] * m[1])
+                                                       : std::sqrt((m[1] + 2.0 * m[2]) / m[0]);
+        if (!poro::tet_geometry(vert + 12 * i, jinv, vol, dins, err))
+            return fail(nullptr, PORO_EINVAL, "poro_cfl_dt_system: element " + std::to_string(i) + ": " + err);
+        if (!(v > 0.0) || !std::isfinite(v))
+            return fail(nullptr, PORO_EINVAL, "poro_cfl_dt_system: element " + std::to_string(i) + ": material");
+        dt[i] = cfl_c / (2 * degree_N + 1) * dins / v;
+    }
+    return PORO_OK;
+}
+
 static poro_status upload_population(poro_ctx* c, int64_t n, const std::vector<double>& ec) {
     const size_t nd = (size_t)n * c->nq * c->B;
     cudaError_t e;
@@ -631,6 +658,27 @@ poro_status poro_set_isolated_maxwell(poro_ctx* c, int64_t n, const double* vert
     return upload_population(c, n, ec);
 }
 
+poro_status poro_set_isolated_viscoelastic(poro_ctx* c, int64_t n, const double* vert, const double* mat,
+                                           const double* dt) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated_viscoelastic: ctx is NULL");
+    if (c->system != PORO_SYSTEM_VISCOELASTIC)
+        return fail(c, PORO_EUNSUPPORTED, "poro_set_isolated_viscoelastic: context is not a viscoelastic context");
+    if (n < 0 || (n > 0 && (!vert || !mat || !dt)))
+        return fail(c, PORO_EINVAL, "poro_set_isolated_viscoelastic: bad argument");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    c->mesh_mode = false;
+    std::vector<double> ec((size_t)n * c->stride);
+    for (int64_t i = 0; i < n; ++i) {
+        std::string err;
+        if (!poro::visco_element_constants(c->ref, vert + 12 * i, mat + 12 * i, dt[i], ec.data() + (size_t)i * c->stride,
+                                           err))
+            return fail(c, PORO_EINVAL, "poro_set_isolated_viscoelastic: element " + std::to_string(i) + ": " + err);
+    }
+    return upload_population(c, n, ec);
+}
+
 poro_status poro_get_system(const poro_ctx* c, int32_t* system, int32_t* n_quantities) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_system: ctx is NULL");
     if (system) *system = c->system;
@@ -668,6 +716,8 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
     if (c->system == PORO_SYSTEM_MAXWELL) {
         rc = poro::launch_stp_fp64_maxwell(c->dref, nullptr, count, q0, ec, qt, iout, st);
+    } else if (c->system == PORO_SYSTEM_VISCOELASTIC) {
+        rc = poro::launch_stp_fp64_visco(c->dref, nullptr, count, q0, ec, qt, iout, st);
     } else if (c->prec == PORO_FP64) {
         rc = poro::launch_stp_fp64(c->dref, nullptr, count, q0, ec, qt, iout, st, c->variant);
     } else {
@@ -880,11 +930,13 @@ poro_status poro_get_integrated(poro_ctx* c, int64_t first, int64_t count, doubl
 poro_status poro_flop_count(const poro_ctx* c, int32_t refine_sweeps, double* f) {
     if (!c || !f) return fail(nullptr, PORO_EINVAL, "poro_flop_count: NULL argument");
     const double B = c->B, T = c->T, nq = c->nq;
-    const bool mx = c->system == PORO_SYSTEM_MAXWELL;
-    const double nnz = mx ? poro::maxwell::STAR_NNZ : poro::STAR_NNZ, npair = mx ? 0 : 3;
-    // S3: nq B rows of T x T time solves + the G couplings per mode (Biot: 3)
+    const bool mx = c->system == PORO_SYSTEM_MAXWELL, ve = c->system == PORO_SYSTEM_VISCOELASTIC;
+    const double nnz = mx ? poro::maxwell::STAR_NNZ : ve ? poro::visco::STAR_NNZ : poro::STAR_NNZ;
+    // couplings of E*'s strictly upper part per mode (Biot 3, viscoelastic 3 x 12)
+    const double npair = mx ? 0 : ve ? 12 * poro::visco::NMECH : 3;
+    // S3: nq B rows of T x T time solves + the couplings per mode
     const double s3 = 2.0 * nq * B * T * T + 2.0 * npair * B * T;
-    // S4a: star products (Biot 54, Maxwell 12 entries) of all modes of degree >= 1, 3 directions
+    // S4a: star products (Biot 54, Maxwell 12, viscoelastic 51 entries) of all modes of degree >= 1, 3 directions
     const double s4a = 2.0 * 3 * nnz * (B - 1) * T;
     // S4b: structural non-zeros of the Khat blocks, each applied to nq T columns
     const double s4b = 2.0 * (double)c->ref.khat_block_nnz * nq * T;

@@ -76,6 +76,42 @@ PORO_HD constexpr int star_col(int n) {
 PORO_HD constexpr int elem_const_stride(int N) { return (3 * STAR_NNZ + (N + 1) * (N + 1) + 4 + 1) & ~1; }
 }  // namespace maxwell
 
+// Viscoelastic attenuation (Section "Other applications": upper-triangular
+// source matrix), anelastic-function form with NMECH relaxation mechanisms:
+// 27 quantities (6 stresses xx yy zz xy yz xz, velocities u v w, then six
+// anelastic functions per mechanism in the stress order).  E* holds
+// -omega_l dt on the diagonal of mechanism l's functions and the couplings
+// -(Ylam_l + 2 Ymu_l) dt, -Ylam_l dt (normal block) and -2 Ymu_l dt (shear)
+// from them into the stresses.  Union pattern of the reference Jacobians
+// (51 entries a direction): normal stresses <- u v w, shear stresses <- their
+// two velocities, velocities <- the three stresses of their row of sigma,
+// anelastic functions <- the velocities of their strain-rate component.
+namespace visco {
+constexpr int NMECH = 3;
+constexpr int NQ = 9 + 6 * NMECH;
+constexpr int STAR_NNZ = 15 + 9 + 9 * NMECH;
+// row-major pattern of the first 24 (stress and velocity rows) and of one
+// mechanism's 9 (functions xx yy zz xy yz xz), columns as quantity indices
+PORO_HD constexpr int star_row(int n) {
+    constexpr int r[24] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 4, 4, 5, 5, 6, 6, 6, 7, 7, 7, 8, 8, 8};
+    constexpr int m[9] = {0, 1, 2, 3, 3, 4, 4, 5, 5};
+    return n < 24 ? r[n] : 9 + 6 * ((n - 24) / 9) + m[(n - 24) % 9];
+}
+PORO_HD constexpr int star_col(int n) {
+    constexpr int c[24] = {6, 7, 8, 6, 7, 8, 6, 7, 8, 6, 7, 7, 8, 6, 8, 0, 3, 5, 3, 1, 4, 5, 4, 2};
+    constexpr int m[9] = {6, 7, 8, 6, 7, 7, 8, 6, 8};
+    return n < 24 ? c[n] : m[(n - 24) % 9];
+}
+// per-element constants: star[3][51], (Z - e_l I)^{-1} [NMECH][T][T], then
+// 14 scalars: per mechanism (-(Ylam+2Ymu) dt, -Ylam dt, -2 Ymu dt), e_l
+// (NMECH), dt, pad
+constexpr int NSC = 3 * NMECH + NMECH + 2;
+PORO_HD constexpr int sc_dt() { return 4 * NMECH; }
+PORO_HD constexpr int elem_const_stride(int N) {
+    return (3 * STAR_NNZ + NMECH * (N + 1) * (N + 1) + NSC + 1) & ~1;
+}
+}  // namespace visco
+
 // Per-element constants, in doubles, in this order:
 //   star[3][54]       A^{j*} = dt A^j on the union pattern
 //   zinv_uf[T][T]     (Z - e I)^{-1}, e = E*_{uf,uf} (row-major, [u][s])
@@ -122,6 +158,10 @@ bool element_constants(const ReferenceData& ref, const double* v12, const poro_m
 // (maxwell::elem_const_stride(N) doubles)
 bool maxwell_element_constants(const ReferenceData& ref, const double* v12, const double mat[3], double dt,
                                double* out, std::string& err);
+// One viscoelastic element: mat = rho, lam_u, mu_u, omega[3], Ylam[3],
+// Ymu[3]; out gets visco::elem_const_stride(N) doubles
+bool visco_element_constants(const ReferenceData& ref, const double* v12, const double mat[12], double dt,
+                             double* out, std::string& err);
 
 // ----- corrector set-up (mesh.cpp) -----
 // Godunov flux solver matrices of one face: A_n^L q* = Fm q_L + Fp q_R.
@@ -314,5 +354,9 @@ int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t co
 // [count][maxwell::elem_const_stride(N)], qt [count][6][B][T]).
 int launch_stp_fp64_maxwell(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
                             const double* econst, double* qt, double* iout, void* stream);
+// ... and for the viscoelastic system (q0 [count][27][B], econst
+// [count][visco::elem_const_stride(N)], qt [count][27][B][T]).
+int launch_stp_fp64_visco(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                          const double* econst, double* qt, double* iout, void* stream);
 
 }  // namespace poro

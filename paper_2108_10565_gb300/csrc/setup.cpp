@@ -437,4 +437,74 @@ bool maxwell_element_constants(const ReferenceData& ref, const double* v12, cons
     return true;
 }
 
+// Reference Jacobians of the viscoelastic system (the form of q_t + A q_x +
+// B q_y + C q_z = E q): sigma_ii,t = lam_u div v + 2 mu_u d_i v_i, sigma_ab,t =
+// mu_u (d_b v_a + d_a v_b), rho v_i,t = sum_d d_d sigma_id, th_ii,t = omega
+// d_i v_i, th_ab,t = omega (d_b v_a + d_a v_b) / 2 (plus the source terms).
+static void visco_jacobians(const double* mat, double M[3][visco::NQ][visco::NQ]) {
+    std::memset(M, 0, sizeof(double) * 3 * visco::NQ * visco::NQ);
+    const double rho = mat[0], lam = mat[1], mu = mat[2];
+    const int vel[3] = {6, 7, 8};
+    const int shear[3][3] = {{3, 0, 1}, {4, 1, 2}, {5, 0, 2}};  // component, a, b
+    const int sig[3][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}};
+    for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d) M[d][i][vel[d]] = -(d == i ? lam + 2.0 * mu : lam);
+    for (const auto& sh : shear) {
+        M[sh[2]][sh[0]][vel[sh[1]]] = -mu;
+        M[sh[1]][sh[0]][vel[sh[2]]] = -mu;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d) M[d][vel[i]][sig[i][d]] = -1.0 / rho;
+    for (int l = 0; l < visco::NMECH; ++l) {
+        const double w = mat[3 + l];
+        const int base = 9 + 6 * l;
+        for (int i = 0; i < 3; ++i) M[i][base + i][vel[i]] = -w;
+        for (const auto& sh : shear) {
+            M[sh[2]][base + sh[0]][vel[sh[1]]] = -0.5 * w;
+            M[sh[1]][base + sh[0]][vel[sh[2]]] = -0.5 * w;
+        }
+    }
+}
+
+bool visco_element_constants(const ReferenceData& ref, const double* v12, const double mat[12], double dt,
+                             double* out, std::string& err) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) { err = "element: time step must be positive"; return false; }
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(mat[i])) { err = "element: non-finite material parameter"; return false; }
+    if (!(mat[0] > 0.0) || !(mat[2] > 0.0) || !(mat[1] + 2.0 * mat[2] / 3.0 > 0.0)) {
+        err = "element: need rho > 0, mu_u > 0 and a positive unrelaxed bulk modulus";
+        return false;
+    }
+    for (int l = 0; l < visco::NMECH; ++l)
+        if (!(mat[3 + l] >= 0.0)) { err = "element: relaxation frequencies must be >= 0"; return false; }
+    double jinv[3][3], vol, dins;
+    if (!tet_geometry(v12, jinv, vol, dins, err)) return false;
+    static thread_local double M[3][visco::NQ][visco::NQ];
+    visco_jacobians(mat, M);
+    const int T = ref.T;
+    std::memset(out, 0, sizeof(double) * visco::elem_const_stride(ref.N));
+    for (int j = 0; j < 3; ++j)
+        for (int n = 0; n < visco::STAR_NNZ; ++n) {
+            const int p = visco::star_row(n), q = visco::star_col(n);
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) s += jinv[j][d] * M[d][p][q];
+            out[j * visco::STAR_NNZ + n] = dt * s;
+        }
+    double* zi = out + 3 * visco::STAR_NNZ;
+    double* sc = zi + visco::NMECH * T * T;
+    for (int l = 0; l < visco::NMECH; ++l) {
+        const double e = -dt * mat[3 + l];
+        std::vector<double> zm(ref.z);
+        for (int u = 0; u < T; ++u) zm[u * T + u] -= e;
+        if (!invert_small(T, zm.data(), zi + l * T * T)) { err = "element: singular time block"; return false; }
+        const double ylam = mat[6 + l], ymu = mat[9 + l];
+        sc[3 * l + 0] = -dt * (ylam + 2.0 * ymu);
+        sc[3 * l + 1] = -dt * ylam;
+        sc[3 * l + 2] = -dt * 2.0 * ymu;
+        sc[3 * visco::NMECH + l] = e;
+    }
+    sc[visco::sc_dt()] = dt;
+    return true;
+}
+
 }  // namespace poro

@@ -52,12 +52,15 @@ struct K1Shape : Alg3Shape<N, Sys::NQ> {
     using A = Alg3Shape<N, Sys::NQ>;
     static constexpr int NT = NT_;
     static constexpr int T_ = N + 1;
-    // shared layout (doubles): bq[NQ*QS] | X[NQ*XSMAX] | star[3*NNZ] | zuf[T*T] | sc[4] | zin[T*T]
+    // shared layout (doubles): bq[NQ*QS] | X[NQ*XSMAX] | star[3*NNZ] |
+    // zsh[NSHM*T*T] | sc[NSC] | zin[T*T]; star .. sc are the element's
+    // constants in their global order (EC words)
     static constexpr int OFF_X = A::SQ;
     static constexpr int OFF_STAR = OFF_X + Sys::NQ * A::XSMAX;
     static constexpr int OFF_ZUF = OFF_STAR + 3 * Sys::NNZ;
-    static constexpr int OFF_SC = OFF_ZUF + T_ * T_;
-    static constexpr int OFF_ZIN = OFF_SC + 4;
+    static constexpr int OFF_SC = OFF_ZUF + Sys::NSHM * T_ * T_;
+    static constexpr int OFF_ZIN = OFF_SC + Sys::NSC;
+    static constexpr int EC = OFF_ZIN - OFF_STAR;
     static constexpr int SMEM_DOUBLES = OFF_ZIN + T_ * T_;
 };
 
@@ -81,14 +84,14 @@ __global__ void __launch_bounds__(NT_) stp_fp64_kernel(const K1Params P) {
         if (P.runs) R = P.runs[P.item_run[it]];
         const double* q0 = R.q0 + e * (int64_t)(NQ * B);
         const double* ec = R.econst + e * (int64_t)P.stride;
-        // element constants: star[162], zinv_uf[T*T], e, g, dt, pad are contiguous
-        for (int i = tid; i < 3 * STAR_NNZ + T * T + 4; i += NT) star[i] = ec[i];
+        // element constants: stars, shifted time matrices and scalars are contiguous
+        for (int i = tid; i < S::EC; i += NT) star[i] = ec[i];
         for (int i = tid; i < T * T; i += NT) zin[i] = P.zinv[i];
         init_rhs<N, NT, double, double, NQ>(bq, q0);
         __syncthreads();
-        alg3_sweep<N, NT, double, 1, Sys>(bq, X, star, zuf, zin, sc[1], P.khat);
+        alg3_sweep<N, NT, double, 1, Sys>(bq, X, star, zuf, zin, sc[1], P.khat, sc);
         // time integration and outputs (global layout [p][l][u], dense)
-        const double dt = sc[2];
+        const double dt = sc[Sys::DT_SC];
         if (R.iout) {
             double* io = R.iout + e * (int64_t)(NQ * B);
             for (int i = tid; i < NQ * B; i += NT) io[i] = dt * bq[(i / B) * QS + (i % B) * T];
@@ -113,7 +116,8 @@ int launch_nt(const DeviceReference& ref, const int32_t* elems, int64_t count, c
     P.qt = qt;
     P.iout = iout;
     P.count = count;
-    P.stride = Sys::NQ == NQ ? elem_const_stride(N) : maxwell::elem_const_stride(N);
+    P.stride = Sys::NQ == NQ ? elem_const_stride(N)
+               : Sys::NQ == maxwell::NQ ? maxwell::elem_const_stride(N) : visco::elem_const_stride(N);
     P.khat.val = ref.khat_val;
     P.khat.col = ref.khat_col;
     P.khat.row = ref.khat_row;
@@ -161,6 +165,20 @@ int launch_stp_fp64_maxwell(const DeviceReference& ref, const int32_t* elems, in
                                                         nullptr);
         case 6: return launch_nt<6, 128, MaxwellSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr,
                                                         nullptr);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_stp_fp64_visco(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
+                          const double* econst, double* qt, double* iout, void* stream) {
+    // 27 quantities: the (p, u) pairs of a mode span 1 to 6 lanes per warp
+    switch (ref.N) {
+        case 1: return launch_nt<1, 64, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 2: return launch_nt<2, 64, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 3: return launch_nt<3, 128, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 4: return launch_nt<4, 128, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 5: return launch_nt<5, 256, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
+        case 6: return launch_nt<6, 256, ViscoSystem>(ref, elems, count, q0, econst, qt, iout, stream, nullptr, nullptr);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -140,3 +140,22 @@ def test_perturbed_layer_materials_stay_physical():
         except ValueError:
             bad += 1
     assert bad > 0
+
+
+def test_cfl_other_systems_match_oracle(L):
+    """poro_cfl_dt_system: the CFL step of the damped Maxwell and viscoelastic
+    material rows against the oracle's statement of each system."""
+    from oracle import maxwell, viscoelastic
+
+    for system, gen, mod, to_dict in ((L.PORO_SYSTEM_MAXWELL, inputs.maxwell_isolated_elements, maxwell,
+                                       inputs.maxwell_dict),
+                                      (L.PORO_SYSTEM_VISCOELASTIC, inputs.viscoelastic_isolated_elements,
+                                       viscoelastic, inputs.viscoelastic_dict)):
+        d = gen(40, 4)
+        dt = L.poro_cfl_dt_system(system, 4, d["vertices"], d["materials"])
+        ref = [mod.cfl_dt(d["vertices"][i], to_dict(d["materials"][i]), 4) for i in range(40)]
+        np.testing.assert_allclose(dt, ref, rtol=1e-13)
+    bad = inputs.maxwell_isolated_elements(2, 2)
+    bad["materials"][1, 0] = -1.0
+    with pytest.raises(L.PoroError):
+        L.poro_cfl_dt_system(L.PORO_SYSTEM_MAXWELL, 2, bad["vertices"], bad["materials"])
