@@ -269,11 +269,11 @@ poro_status poro_predict_dev(poro_ctx* ctx, int64_t first, int64_t count, const 
 /* End-to-end predictor from host buffers: Q0 of every element in, I out, with
  * the host<->device copies overlapped with the kernels.  The population is
  * cut into chunks of `chunk_elems` elements (0: automatic, about 16 chunks
- * of at least 4096 elements);
+ * of at least 4096 elements, the first three and last three smaller);
  * chunk i's Q0 copy, predictor (solver as in poro_predict) and I copy run on
  * three streams, so one chunk's copies run under another chunk's kernel.
- * q0_host[n_elem][13][B] is read and becomes the context's DOFs;
- * I_out[n_elem][13][B] is written; the full predictor stays on the device
+ * q0_host[n_elem][Q][B] is read and becomes the context's DOFs;
+ * I_out[n_elem][Q][B] is written (Q the system's quantities); the full predictor stays on the device
  * (poro_get_predictor).  Pinned host memory gives the overlap; pageable
  * memory works without it.  Synchronous: returns when I_out is complete.
  * (The paper has no counterpart: it is the host boundary of a batched GPU

@@ -228,8 +228,23 @@ def poro_set_isolated_viscoelastic(ctx, vert, mat, dt):
     return _check(lib().poro_set_isolated_viscoelastic(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
 
 
+def _out(out, shape):
+    """A C-contiguous float64 buffer of `shape` for the library to fill:
+    `out` if it is one, a new array if out is None."""
+    if out is None:
+        return np.empty(shape)
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size == int(np.prod(shape))):
+        raise ValueError(f"out must be a C-contiguous float64 array of shape {shape}")
+    return out
+
+
 def poro_set_dofs(ctx, Q):
+    N, _, n = poro_get_info(ctx)
+    nq = poro_get_system(ctx)[1]
     q = _f64(Q)
+    if n > 0 and q.size != n * nq * ((N + 1) * (N + 2) * (N + 3) // 6):
+        raise ValueError(f"Q must hold {n} elements x {nq} quantities x B(N) modes")
     return _check(lib().poro_set_dofs(ctx, _ptr(q)), ctx)
 
 
@@ -241,8 +256,7 @@ def poro_get_predictor(ctx, first, count, out=None):
     N, _, _ = poro_get_info(ctx)
     nq = poro_get_system(ctx)[1]
     B, T = (N + 1) * (N + 2) * (N + 3) // 6, N + 1
-    if out is None:
-        out = np.empty((count, nq, B, T))
+    out = _out(out, (count, nq, B, T))
     _check(lib().poro_get_predictor(ctx, first, count, _ptr(out)), ctx)
     return out
 
@@ -251,8 +265,7 @@ def poro_get_integrated(ctx, first, count, out=None):
     N, _, _ = poro_get_info(ctx)
     nq = poro_get_system(ctx)[1]
     B = (N + 1) * (N + 2) * (N + 3) // 6
-    if out is None:
-        out = np.empty((count, nq, B))
+    out = _out(out, (count, nq, B))
     _check(lib().poro_get_integrated(ctx, first, count, _ptr(out)), ctx)
     return out
 
@@ -262,13 +275,16 @@ def poro_sync(ctx, timeout_ms=-1):
 
 
 def poro_predict_host(ctx, Q0, out=None, chunk_elems=0, solver=PORO_SOLVE_BLOCK):
-    """End to end from host arrays: Q0[n][13][B] in, I[n][13][B] out, copies
-    overlapped with the kernels (pass pinned arrays for the overlap)."""
+    """End to end from host arrays: Q0[n][Q][B] in, I[n][Q][B] out (Q the
+    system's quantities), copies overlapped with the kernels (pass pinned
+    arrays for the overlap)."""
     N, _, n = poro_get_info(ctx)
+    nq = poro_get_system(ctx)[1]
     B = (N + 1) * (N + 2) * (N + 3) // 6
     q = _f64(Q0)
-    if out is None:
-        out = np.empty((n, 13, B))
+    if n > 0 and q.size != n * nq * B:
+        raise ValueError(f"Q0 must hold {n} x {nq} x {B} values")
+    out = _out(out, (n, nq, B))
     _check(lib().poro_predict_host(ctx, _ptr(q), _ptr(out), chunk_elems, solver), ctx)
     return out
 
@@ -355,9 +371,9 @@ def poro_correct(ctx, cluster=-1):
 
 def poro_get_dofs(ctx, out=None):
     N, _, n = poro_get_info(ctx)
+    nq = poro_get_system(ctx)[1]
     B = (N + 1) * (N + 2) * (N + 3) // 6
-    if out is None:
-        out = np.empty((n, 13, B))
+    out = _out(out, (n, nq, B))
     _check(lib().poro_get_dofs(ctx, _ptr(out)), ctx)
     return out
 

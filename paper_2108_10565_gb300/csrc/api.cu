@@ -767,12 +767,32 @@ poro_status poro_predict_host(poro_ctx* c, const double* q0_host, double* I_out,
         return cuda_fail(c, e, "poro_predict_host");
     if (!c->s_out && (e = cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(c, e, "poro_predict_host");
-    // automatic: about 16 chunks of at least 4096 elements (measured on GB300 at
-    // N = 6, 200k elements: 16 chunks leave 6.8 ms of the 3.5 GB of copies
-    // exposed, 8 chunks 10 ms, 4 chunks 17 ms)
-    int64_t chunk = chunk_elems > 0 ? chunk_elems : std::max<int64_t>(4096, ((n + 15) / 16 + 255) / 256 * 256);
-    if (chunk > n) chunk = n;
-    const int64_t nchunks = (n + chunk - 1) / chunk;
+    // chunk boundaries.  Only the first chunk's upload and the last chunk's
+    // download are not hidden under kernels, so the automatic schedule takes
+    // about 16 chunks of at least 4096 elements (measured on GB300 at N = 6,
+    // 200k elements: 16 chunks leave 6.8 ms of the 3.5 GB of copies exposed, 8
+    // chunks 10 ms, 4 chunks 17 ms) and ramps the first three up from 1/8 and
+    // the last three down to 1/8 of that size (measured against 16 equal
+    // chunks: the same within the run-to-run spread of about 1.5 ms).
+    // chunk_elems > 0: equal chunks.
+    std::vector<int64_t> bounds{0};
+    {
+        const int64_t chunk = chunk_elems > 0 ? std::min(chunk_elems, n)
+                                              : std::min(n, std::max<int64_t>(4096, ((n + 15) / 16 + 255) / 256 * 256));
+        int64_t ramp[3] = {chunk / 8, chunk / 4, chunk / 2}, ramp_sum = 0;
+        for (int64_t& r : ramp) ramp_sum += (r = std::max<int64_t>(256, r / 256 * 256));
+        const bool ramped = chunk_elems <= 0 && n - 2 * ramp_sum >= 2 * chunk;
+        if (ramped)
+            for (int64_t r : ramp) bounds.push_back(bounds.back() + r);
+        const int64_t mid_end = ramped ? n - ramp_sum : n;
+        const int64_t mid = mid_end - bounds.back();
+        const int64_t k = std::max<int64_t>(1, (mid + chunk - 1) / chunk);
+        const int64_t start = bounds.back();
+        for (int64_t i = 1; i <= k; ++i) bounds.push_back(start + (chunk_elems > 0 ? std::min(mid, i * chunk) : mid * i / k));
+        if (ramped)
+            for (int i = 2; i >= 0; --i) bounds.push_back(bounds.back() + ramp[i]);
+    }
+    const int64_t nchunks = (int64_t)bounds.size() - 1;
     if (nchunks > 4096) return fail(c, PORO_EINVAL, "poro_predict_host: more than 4096 chunks");
     while ((int64_t)c->ev_in.size() < nchunks) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -786,7 +806,7 @@ poro_status poro_predict_host(poro_ctx* c, const double* q0_host, double* I_out,
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "poro_predict_host");
     const size_t per = (size_t)c->nq * c->B;
     for (int64_t i = 0; i < nchunks; ++i) {
-        const int64_t first = i * chunk, cnt = std::min(chunk, n - first);
+        const int64_t first = bounds[i], cnt = bounds[i + 1] - bounds[i];
         if ((e = cudaMemcpyAsync(c->d_q0 + first * per, q0_host + first * per, cnt * per * sizeof(double),
                                  cudaMemcpyHostToDevice, c->s_in)) != cudaSuccess ||
             (e = cudaEventRecord(c->ev_in[i], c->s_in)) != cudaSuccess ||

@@ -194,6 +194,24 @@ def test_host_pipeline_matches_step_by_step(L, prec, chunk):
     np.testing.assert_array_equal(qt_got, qt_ref)
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_host_pipeline_ramped_chunks(L, prec):
+    """A population large enough for the automatic schedule's ramped first
+    and last chunks (20,000 elements at N = 2: chunks 512, 1024, 2048, then
+    about 4,096, then 2048, 1024, 512) gives bitwise the step-by-step I."""
+    d = population(20000, 2, seed=13)
+    qt_ref, i_ref = _run_host(L, d, prec)
+    ctx = L.poro_create(0, d["N"], prec)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        i_got = L.poro_predict_host(ctx, d["Q0"])
+        qt_got = L.poro_get_predictor(ctx, 0, 20000)
+    finally:
+        L.poro_destroy(ctx)
+    np.testing.assert_array_equal(i_got, i_ref)
+    np.testing.assert_array_equal(qt_got, qt_ref)
+
+
 def test_host_pipeline_errors(L):
     d = population(5, 2, seed=12)
     ctx = L.poro_create(0, d["N"], 0)
