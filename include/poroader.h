@@ -220,6 +220,40 @@ poro_status poro_set_isolated(poro_ctx* ctx, int64_t n_elem, const double* vert,
 poro_status poro_set_isolated_maxwell(poro_ctx* ctx, int64_t n, const double* vert, const double* mat,
                                       const double* dt);
 
+/* Isolated tetrahedra with sub-cell material variation (Section
+ * "Limitations": with material varying inside an element the stiffness
+ * matrices become 3-tensors).  mat[n][4] holds one material per vertex
+ * (vertex v of vert[i] carries mat[4 i + v]); the Jacobians A_d(x) and the
+ * source matrix E(x) are the linear interpolation of the four vertex
+ * materials' (a reading: the paper does not say how the material varies).
+ * The predictor system is then Y = Y_0 + sum_{r=1..3} Mh3_r (sum_j Khat^j
+ * A^{j*}_r - E*_r), Y_0 the constant-material operator of the mode-0 (mean)
+ * Jacobians and Mh3_r = M^{-1} int phi_k phi_r phi_l; a material of degree 1
+ * couples modes of equal degree, so Algorithm 3 does not solve Y directly.
+ * poro_predict then iterates Q <- Y_0^{-1} (b - (Y - Y_0) Q) per element
+ * (Richardson iteration preconditioned by Algorithm 3 on the mean
+ * material, binary64) until max |change| <= tol max |Q| (see
+ * poro_set_subcell_tolerance); the contraction factor is about the
+ * material's relative variation inside the element.  Biot FP64 contexts
+ * only; the LU comparator and the autotuners return PORO_EUNSUPPORTED on
+ * such a population.  dt[n] as in poro_set_isolated (the CFL step of the
+ * fastest vertex material is the safe choice).  Errors: PORO_EINVAL
+ * (degenerate element or vertex material), PORO_EUNSUPPORTED, PORO_ENOMEM. */
+poro_status poro_set_isolated_subcell(poro_ctx* ctx, int64_t n_elem, const double* vert,
+                                      const poro_material* mat, const double* dt);
+
+/* Stopping rule of the sub-cell iteration: relative change tol (>= 0,
+ * default 1e-13) and at most max_iter iterations (1..100000, default 100).
+ * Errors: PORO_EINVAL. */
+poro_status poro_set_subcell_tolerance(poro_ctx* ctx, double tol, int32_t max_iter);
+
+/* Iterations each element of [first, first + count) took in the last
+ * sub-cell predictor (synchronises the context stream): k > 0 converged
+ * after k iterations, -k stopped at max_iter = k without converging or on a
+ * non-finite iterate, 0 not run.  Errors: PORO_ESTATE (no sub-cell
+ * population), PORO_EINVAL, PORO_ECUDA. */
+poro_status poro_get_subcell_iterations(poro_ctx* ctx, int64_t first, int64_t count, int32_t* out);
+
 /* Isolated viscoelastic elements (Section "Other applications"): like
  * poro_set_isolated with mat[n][12] = (rho, lam_u, mu_u, omega_1..3,
  * Ylam_1..3, Ymu_1..3) per element (host, copied; rho > 0, mu_u > 0, unrelaxed

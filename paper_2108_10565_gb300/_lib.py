@@ -42,6 +42,9 @@ SIGNATURES = [
     ("poro_get_system", _i32, [_vp, _c.POINTER(_i32), _c.POINTER(_i32)]),
     ("poro_set_isolated_maxwell", _i32, [_vp, _i64, _vp, _vp, _vp]),
     ("poro_set_isolated_viscoelastic", _i32, [_vp, _i64, _vp, _vp, _vp]),
+    ("poro_set_isolated_subcell", _i32, [_vp, _i64, _vp, _vp, _vp]),
+    ("poro_set_subcell_tolerance", _i32, [_vp, _dbl, _i32]),
+    ("poro_get_subcell_iterations", _i32, [_vp, _i64, _i64, _vp]),
     ("poro_cfl_dt_system", _i32, [_i32, _i32, _i64, _vp, _vp, _dbl, _vp]),
     ("poro_destroy", _i32, [_vp]),
     ("poro_last_error", _c.c_char_p, [_vp]),
@@ -220,6 +223,24 @@ def poro_set_isolated_maxwell(ctx, vert, mat, dt):
     """mat[n][3] = (eps, mu, sigma) per element."""
     v, m, d = _f64(vert), _f64(mat), _f64(dt)
     return _check(lib().poro_set_isolated_maxwell(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
+
+
+def poro_set_isolated_subcell(ctx, vert, mat, dt):
+    """mat[n][4][10]: the material rows of each element's four vertices."""
+    v, m, d = _f64(vert), _f64(mat), _f64(dt)
+    if m.size != v.shape[0] * 4 * 10:
+        raise ValueError("mat must hold 4 material rows of 10 values per element")
+    return _check(lib().poro_set_isolated_subcell(ctx, v.shape[0], _ptr(v), _ptr(m), _ptr(d)), ctx)
+
+
+def poro_set_subcell_tolerance(ctx, tol, max_iter):
+    return _check(lib().poro_set_subcell_tolerance(ctx, tol, max_iter), ctx)
+
+
+def poro_get_subcell_iterations(ctx, first, count):
+    out = np.empty(count, dtype=np.int32)
+    _check(lib().poro_get_subcell_iterations(ctx, first, count, out.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return out
 
 
 def poro_set_isolated_viscoelastic(ctx, vert, mat, dt):

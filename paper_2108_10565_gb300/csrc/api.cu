@@ -43,6 +43,13 @@ struct poro_ctx {
     double* d_qt = nullptr;
     double* d_iout = nullptr;
     bool have_dofs = false, have_pred = false;
+    // ---- sub-cell material population (poro_set_isolated_subcell)
+    bool subcell = false;
+    double* d_evar = nullptr;                  // [n][subcell_var_stride()]
+    int32_t* d_iters = nullptr;                // [n] iterations of the last predictor
+    poro::SubcellReference sub;                // mass 3-tensors (built on first use)
+    double sub_tol = 1e-13;
+    int sub_max_iter = 100;
     std::string err;
     // ---- mesh mode (corrector, sources, receivers, time stepping)
     bool mesh_mode = false, have_mat = false, ready = false;
@@ -145,6 +152,9 @@ void free_mesh_device(poro_ctx* c) {
 void free_population(poro_ctx* c) {
     free_lu(c);
     free_mesh_device(c);
+    dfree(c->d_evar);
+    dfree(c->d_iters);
+    c->subcell = false;
     dfree(c->d_econst);
     dfree(c->d_q0);
     dfree(c->d_qt);
@@ -176,6 +186,9 @@ void free_reference(poro_ctx* c) {
     dfree(c->mref.khat_tc);
     dfree(c->mref.status);
     dfree(c->mref.zinv_f32);
+    dfree(c->sub.m3_row);
+    dfree(c->sub.m3_col);
+    dfree(c->sub.m3_val);
     dfree(c->dref.khat_val);
     dfree(c->dref.khat_col);
     dfree(c->dref.khat_row);
@@ -187,7 +200,7 @@ void free_reference(poro_ctx* c) {
 
 namespace poro {
 bool ctx_view(const poro_ctx* c, CtxView& v) {
-    if (!c || !c->d_econst || c->system != PORO_SYSTEM_BIOT) return false;
+    if (!c || !c->d_econst || c->system != PORO_SYSTEM_BIOT || c->subcell) return false;
     v.device = c->device;
     v.N = c->N;
     v.n_elem = c->n_elem;
@@ -679,6 +692,76 @@ poro_status poro_set_isolated_viscoelastic(poro_ctx* c, int64_t n, const double*
     return upload_population(c, n, ec);
 }
 
+poro_status poro_set_isolated_subcell(poro_ctx* c, int64_t n, const double* vert, const poro_material* mat,
+                                      const double* dt) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_isolated_subcell: ctx is NULL");
+    if (c->system != PORO_SYSTEM_BIOT || c->prec != PORO_FP64)
+        return fail(c, PORO_EUNSUPPORTED, "poro_set_isolated_subcell: built for Biot's system in FP64");
+    if (n < 0 || (n > 0 && (!vert || !mat || !dt)))
+        return fail(c, PORO_EINVAL, "poro_set_isolated_subcell: bad argument");
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_population(c);
+    c->mesh_mode = false;
+    std::string err;
+    if (!c->sub.m3_row) {
+        std::vector<int32_t> row, col;
+        std::vector<double> val;
+        if (!poro::subcell_mass_tensors(c->ref, row, col, val, err))
+            return fail(c, PORO_EINVAL, "poro_set_isolated_subcell: " + err);
+        cudaError_t e = upload((void**)&c->sub.m3_row, row.data(), row.size() * sizeof(int32_t));
+        if (e == cudaSuccess) e = upload((void**)&c->sub.m3_col, col.data(), col.size() * sizeof(int32_t));
+        if (e == cudaSuccess) e = upload((void**)&c->sub.m3_val, val.data(), val.size() * sizeof(double));
+        if (e != cudaSuccess) {
+            dfree(c->sub.m3_row);
+            dfree(c->sub.m3_col);
+            dfree(c->sub.m3_val);
+            return cuda_fail(c, e, "poro_set_isolated_subcell: tensors");
+        }
+    }
+    double P[4][4];
+    if (!poro::subcell_projection(P, err)) return fail(c, PORO_EINVAL, "poro_set_isolated_subcell: " + err);
+    const int vs = poro::subcell_var_stride();
+    std::vector<double> ec((size_t)n * c->stride), ev((size_t)n * vs);
+    for (int64_t i = 0; i < n; ++i)
+        if (!poro::subcell_element_constants(c->ref, P, vert + 12 * i, mat + 4 * i, dt[i], ec.data() + (size_t)i * c->stride,
+                                             ev.data() + (size_t)i * vs, err))
+            return fail(c, PORO_EINVAL, "poro_set_isolated_subcell: element " + std::to_string(i) + ": " + err);
+    poro_status st = upload_population(c, n, ec);
+    if (st != PORO_OK) return st;
+    cudaError_t e = upload((void**)&c->d_evar, ev.data(), ev.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_iters, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_iters, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        free_population(c);
+        return cuda_fail(c, e, "poro_set_isolated_subcell");
+    }
+    c->subcell = true;
+    return PORO_OK;
+}
+
+poro_status poro_set_subcell_tolerance(poro_ctx* c, double tol, int32_t max_iter) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_set_subcell_tolerance: ctx is NULL");
+    if (!(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1 || max_iter > 100000)
+        return fail(c, PORO_EINVAL, "poro_set_subcell_tolerance: need tol >= 0 and 1 <= max_iter <= 100000");
+    c->sub_tol = tol;
+    c->sub_max_iter = max_iter;
+    return PORO_OK;
+}
+
+poro_status poro_get_subcell_iterations(poro_ctx* c, int64_t first, int64_t count, int32_t* out) {
+    if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_subcell_iterations: ctx is NULL");
+    if (!c->subcell) return fail(c, PORO_ESTATE, "poro_get_subcell_iterations: no sub-cell population loaded");
+    if (first < 0 || count < 0 || first + count > c->n_elem || (count > 0 && !out))
+        return fail(c, PORO_EINVAL, "poro_get_subcell_iterations: bad range");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpyAsync(out, c->d_iters + first, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "poro_get_subcell_iterations");
+    return PORO_OK;
+}
+
 poro_status poro_get_system(const poro_ctx* c, int32_t* system, int32_t* n_quantities) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_get_system: ctx is NULL");
     if (system) *system = c->system;
@@ -705,8 +788,9 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
     const double* ec = c->d_econst + first * c->stride;
     int rc = 0;
     if (solver == PORO_SOLVE_LU) {
-        if (c->system != PORO_SYSTEM_BIOT)
-            return fail(c, PORO_EUNSUPPORTED, "predict (LU): the dense-LU comparator is built for Biot's system");
+        if (c->system != PORO_SYSTEM_BIOT || c->subcell)
+            return fail(c, PORO_EUNSUPPORTED,
+                        "predict (LU): the dense-LU comparator is built for Biot's system with constant material");
         if (count > 0 && (first < c->lu_first || first + count > c->lu_first + c->lu_count))
             return fail(c, PORO_ESTATE, "predict (LU): elements not factored; call poro_lu_factor first");
         rc = poro::launch_lu_solve(c->lref, count, c->lu, first - c->lu_first, q0, ec, qt, iout, st);
@@ -714,7 +798,10 @@ static poro_status dispatch_predict(poro_ctx* c, int64_t first, int64_t count, c
         return PORO_OK;
     }
     if (solver != PORO_SOLVE_BLOCK) return fail(c, PORO_EINVAL, "predict: unknown solver");
-    if (c->system == PORO_SYSTEM_MAXWELL) {
+    if (c->subcell) {
+        rc = poro::launch_stp_subcell(c->dref, c->sub, count, q0, ec, c->d_evar + first * poro::subcell_var_stride(),
+                                      qt, iout, c->d_iters + first, c->sub_tol, c->sub_max_iter, st);
+    } else if (c->system == PORO_SYSTEM_MAXWELL) {
         rc = poro::launch_stp_fp64_maxwell(c->dref, nullptr, count, q0, ec, qt, iout, st);
     } else if (c->system == PORO_SYSTEM_VISCOELASTIC) {
         rc = poro::launch_stp_fp64_visco(c->dref, nullptr, count, q0, ec, qt, iout, st);
@@ -842,7 +929,8 @@ poro_status poro_lu_bytes(int degree_N, int64_t count, size_t* bytes) {
 
 poro_status poro_lu_factor(poro_ctx* c, int64_t first, int64_t count) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_lu_factor: ctx is NULL");
-    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_lu_factor: the dense-LU comparator is built for Biot's system");
+    if (c->system != PORO_SYSTEM_BIOT || c->subcell)
+        return fail(c, PORO_EUNSUPPORTED, "poro_lu_factor: the dense-LU comparator is built for Biot's system with constant material");
     if (!c->d_econst) return fail(c, PORO_ESTATE, "poro_lu_factor: no element population loaded");
     if (first < 0 || count < 0 || first + count > c->n_elem || count > 65535)
         return fail(c, PORO_EINVAL, "poro_lu_factor: element range outside the population (or > 65535)");
@@ -1895,7 +1983,8 @@ poro_status poro_flux_matrices(const poro_material* mL, const poro_material* mR,
 
 poro_status poro_autotune(poro_ctx* c, int64_t sample, int32_t* variant_out, double* ms_out) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_autotune: ctx is NULL");
-    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_autotune: the autotuner is built for Biot's system");
+    if (c->system != PORO_SYSTEM_BIOT || c->subcell)
+        return fail(c, PORO_EUNSUPPORTED, "poro_autotune: the autotuner is built for Biot's constant-material predictor");
     if (!c->d_econst || c->n_elem <= 0) return fail(c, PORO_ESTATE, "poro_autotune: no element population loaded");
     cudaSetDevice(c->device);
     const int64_t n = std::max<int64_t>(1, std::min(sample > 0 ? sample : c->n_elem, c->n_elem));
@@ -1964,7 +2053,8 @@ poro_status poro_set_tiles(poro_ctx* c, int32_t choice) {
 
 poro_status poro_autotune_tiles(poro_ctx* c, int64_t sample, int32_t* choice_out, double* ms_out) {
     if (!c) return fail(nullptr, PORO_EINVAL, "poro_autotune_tiles: ctx is NULL");
-    if (c->system != PORO_SYSTEM_BIOT) return fail(c, PORO_EUNSUPPORTED, "poro_autotune_tiles: Biot contexts only");
+    if (c->system != PORO_SYSTEM_BIOT || c->subcell)
+        return fail(c, PORO_EUNSUPPORTED, "poro_autotune_tiles: Biot constant-material contexts only");
     if (!c->d_econst || c->n_elem <= 0) return fail(c, PORO_ESTATE, "poro_autotune_tiles: no element population loaded");
     cudaSetDevice(c->device);
     const int64_t n = std::max<int64_t>(1, std::min(sample > 0 ? sample : c->n_elem, c->n_elem));

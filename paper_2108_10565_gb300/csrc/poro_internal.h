@@ -163,6 +163,30 @@ bool maxwell_element_constants(const ReferenceData& ref, const double* v12, cons
 bool visco_element_constants(const ReferenceData& ref, const double* v12, const double mat[12], double dt,
                              double* out, std::string& err);
 
+// ----- sub-cell material (setup.cpp, subcell.cu) -----
+// Per element, besides the mean-material constants (elem_const_stride
+// layout, from the mode-0 Jacobians): star_r[3][54] for the variation modes
+// r = 1..3 of the linearly interpolated Jacobians, then (e_r, g_r) of E*_r.
+PORO_HD constexpr int subcell_var_stride() { return (3 * 3 * STAR_NNZ + 6 + 1) & ~1; }
+// Mh3_r = M^{-1} int phi_k phi_r phi_l, r = 1..3, as CSR over all rows k:
+// row pointers [3][B + 1] absolute into col / val (device)
+struct SubcellReference {
+    int32_t* m3_row = nullptr;
+    int32_t* m3_col = nullptr;
+    double* m3_val = nullptr;
+};
+// host: the three tensors by the collapsed Gauss rule of reference_data
+bool subcell_mass_tensors(const ReferenceData& R, std::vector<int32_t>& row, std::vector<int32_t>& col,
+                          std::vector<double>& val, std::string& err);
+// host: P[r][v], the modal coefficients f_r = sum_v P[r][v] f_v of the linear
+// field with values f_v at the reference vertices
+bool subcell_projection(double P[4][4], std::string& err);
+// host: one element with vertex materials mats[4] (vertex v of v12 carries
+// mats[v]); mean constants into mean_out, variation block into var_out
+bool subcell_element_constants(const ReferenceData& ref, const double P[4][4], const double* v12,
+                               const poro_material mats[4], double dt, double* mean_out, double* var_out,
+                               std::string& err);
+
 // ----- corrector set-up (mesh.cpp) -----
 // Godunov flux solver matrices of one face: A_n^L q* = Fm q_L + Fp q_R.
 // kind: PORO_FACE_INTERIOR (mR required), PORO_FACE_FREE_SURFACE, PORO_FACE_ABSORBING.
@@ -354,6 +378,11 @@ int launch_stp_fp64(const DeviceReference& ref, const int32_t* elems, int64_t co
 // [count][maxwell::elem_const_stride(N)], qt [count][6][B][T]).
 int launch_stp_fp64_maxwell(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,
                             const double* econst, double* qt, double* iout, void* stream);
+// Sub-cell material predictor (subcell.cu): evar [count][subcell_var_stride()],
+// iters [count] (iterations of each element, negative if not converged).
+int launch_stp_subcell(const DeviceReference& ref, const SubcellReference& sub, int64_t count, const double* q0,
+                       const double* econst, const double* evar, double* qt, double* iout, int32_t* iters,
+                       double tol, int max_iter, void* stream);
 // ... and for the viscoelastic system (q0 [count][27][B], econst
 // [count][visco::elem_const_stride(N)], qt [count][27][B][T]).
 int launch_stp_fp64_visco(const DeviceReference& ref, const int32_t* elems, int64_t count, const double* q0,

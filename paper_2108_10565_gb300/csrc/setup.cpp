@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <string>
 
 #include "poro_internal.h"
 
@@ -504,6 +505,121 @@ bool visco_element_constants(const ReferenceData& ref, const double* v12, const 
         sc[3 * visco::NMECH + l] = e;
     }
     sc[visco::sc_dt()] = dt;
+    return true;
+}
+
+// ------------------------------------------------------------ sub-cell material
+// Section "Limitations": with Jacobians and source matrix that vary linearly
+// inside the element, the stiffness becomes the 3-tensor
+// int phi_k phi_r d_j phi_l = (M3_r Khat^j)[k, l] (d_j phi_l lies in the
+// basis) with the mass 3-tensor M3_r[k, l] = int phi_k phi_r phi_l, r < 4.
+bool subcell_mass_tensors(const ReferenceData& R, std::vector<int32_t>& row, std::vector<int32_t>& col,
+                          std::vector<double>& val, std::string& err) {
+    const int N = R.N, B = R.B;
+    if (B < 4) { err = "sub-cell material needs N >= 1"; return false; }
+    std::vector<int> ti, tj, tk;
+    for (int g = 0; g <= N; ++g)
+        for (int k = 0; k <= g; ++k)
+            for (int j = 0; j <= g - k; ++j) {
+                ti.push_back(g - j - k);
+                tj.push_back(j);
+                tk.push_back(k);
+            }
+    // integrands of degree <= 2N + 1, times the collapsed weight: N + 3 points
+    std::vector<long double> xg, wg;
+    gauss_legendre(N + 3, xg, wg);
+    const int nq = N + 3;
+    std::vector<long double> T3(3 * (size_t)B * B, 0.0L), val_q(B), grad(3 * B);
+    for (int a = 0; a < nq; ++a)
+        for (int b = 0; b < nq; ++b)
+            for (int c = 0; c < nq; ++c) {
+                const long double r = xg[a], s = xg[b], t = xg[c];
+                const long double w = wg[a] * wg[b] * wg[c] * (1.0L - s) * (1.0L - t) * (1.0L - t) / 64.0L;
+                for (int l = 0; l < B; ++l) dubiner(ti[l], tj[l], tk[l], r, s, t, val_q[l], &grad[3 * l]);
+                for (int m = 1; m < 4; ++m)
+                    for (int k = 0; k < B; ++k) {
+                        const long double wk = w * val_q[k] * val_q[m];
+                        for (int l = 0; l < B; ++l) T3[((size_t)(m - 1) * B + k) * B + l] += wk * val_q[l];
+                    }
+            }
+    long double tmax = 0.0L;
+    for (long double v : T3) tmax = std::max(tmax, std::fabs(v));
+    row.assign(3 * (size_t)(B + 1), 0);
+    col.clear();
+    val.clear();
+    for (int m = 0; m < 3; ++m)
+        for (int k = 0; k < B; ++k) {
+            row[(size_t)m * (B + 1) + k] = (int32_t)col.size();
+            for (int l = 0; l < B; ++l) {
+                const long double v = T3[((size_t)m * B + k) * B + l];
+                // exact zeros of the orthogonal basis sit at the rounding level
+                if (std::fabs(v) <= 1e-13L * tmax) continue;
+                col.push_back(l);
+                val.push_back((double)(v / (long double)R.mass_diag[k]));
+            }
+            row[(size_t)m * (B + 1) + B] = (int32_t)col.size();
+        }
+    return true;
+}
+
+bool subcell_projection(double P[4][4], std::string& err) {
+    const double verts[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double V[16], Pi[16];
+    for (int v = 0; v < 4; ++v) basis_at(1, verts[v], V + 4 * v);  // V[v][r] = phi_r(vertex v)
+    if (!invert_small(4, V, Pi)) { err = "sub-cell projection singular"; return false; }
+    for (int r = 0; r < 4; ++r)
+        for (int v = 0; v < 4; ++v) P[r][v] = Pi[r * 4 + v];
+    return true;
+}
+
+bool subcell_element_constants(const ReferenceData& ref, const double P[4][4], const double* v12,
+                               const poro_material mats[4], double dt, double* mean_out, double* var_out,
+                               std::string& err) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) { err = "element: time step must be positive"; return false; }
+    double jinv[3][3], vol, dins;
+    if (!tet_geometry(v12, jinv, vol, dins, err)) return false;
+    static thread_local double abc[4][3][NQ][NQ], E[4][NQ][NQ];
+    for (int v = 0; v < 4; ++v)
+        if (!material_jacobians(mats[v], abc[v], E[v], err)) {
+            err = "vertex " + std::to_string(v) + ": " + err;
+            return false;
+        }
+    const int T = ref.T;
+    std::memset(mean_out, 0, sizeof(double) * elem_const_stride(ref.N));
+    std::memset(var_out, 0, sizeof(double) * subcell_var_stride());
+    double e[4], g[4];
+    for (int r = 0; r < 4; ++r) {
+        double* star = r == 0 ? mean_out : var_out + (r - 1) * 3 * STAR_NNZ;
+        for (int j = 0; j < 3; ++j)
+            for (int n = 0; n < STAR_NNZ; ++n) {
+                const int p = star_row(n), q = star_col(n);
+                double s = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double a = 0.0;
+                    for (int v = 0; v < 4; ++v) a += P[r][v] * abc[v][d][p][q];
+                    s += jinv[j][d] * a;
+                }
+                star[j * STAR_NNZ + n] = dt * s;
+            }
+        e[r] = g[r] = 0.0;
+        for (int v = 0; v < 4; ++v) {
+            e[r] += P[r][v] * E[v][QUF][QUF];
+            g[r] += P[r][v] * E[v][QU][QUF];
+        }
+        e[r] *= dt;
+        g[r] *= dt;
+    }
+    std::vector<double> zm(ref.z);
+    for (int u = 0; u < T; ++u) zm[u * T + u] -= e[0];
+    if (!invert_small(T, zm.data(), mean_out + ec_zinv(ref.N))) { err = "element: singular time block"; return false; }
+    double* sc = mean_out + ec_scalars(ref.N);
+    sc[0] = e[0];
+    sc[1] = g[0];
+    sc[2] = dt;
+    for (int r = 1; r < 4; ++r) {
+        var_out[3 * 3 * STAR_NNZ + 2 * (r - 1)] = e[r];
+        var_out[3 * 3 * STAR_NNZ + 2 * (r - 1) + 1] = g[r];
+    }
     return true;
 }
 

@@ -344,3 +344,30 @@ def viscoelastic_isolated_elements(n, N, seed=SEED_VISCO, omega_scale=1.0):
 def viscoelastic_dict(row):
     return {"rho": float(row[0]), "lam": float(row[1]), "mu": float(row[2]), "omega": np.array(row[3:6], float),
             "Ylam": np.array(row[6:9], float), "Ymu": np.array(row[9:12], float)}
+
+
+SEED_SUBCELL = 2108105657
+
+
+def subcell_isolated_elements(n, N, seed=SEED_SUBCELL, spread=0.1):
+    """Isolated tetrahedra (the geometry of `isolated_elements`) whose four
+    vertices carry their own material: each element's centre material is
+    scaled per parameter by U[0.8, 1.2] around REFERENCE_MATERIAL (skeleton
+    moduli tied), and each vertex material by a further U[1 - spread,
+    1 + spread] per parameter (skeleton moduli tied).  materials [n][4][10],
+    Q0 [n][13][B] ~ N(0, 1)."""
+    B = (N + 1) * (N + 2) * (N + 3) // 6
+    ss = np.random.SeedSequence(seed)
+    g_geo, g_mat, g_dof = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(3)]
+    vert = _blockwise(lambda r, k: random_tetrahedra(r, k), g_geo, n, (4, 3))
+
+    def mats(r, k):
+        centre = perturbed_materials(r, k, tie_skeleton=True)
+        f = r.uniform(1.0 - spread, 1.0 + spread, (k, 4, 10))
+        f[:, :, 2] = f[:, :, 0]
+        f[:, :, 3] = f[:, :, 0]
+        return centre[:, None, :] * f
+
+    mat = _blockwise(mats, g_mat, n, (4, 10))
+    q0 = _blockwise(lambda r, k: r.standard_normal((k, 13, B)), g_dof, n, (13, B))
+    return dict(vertices=vert, materials=mat, Q0=q0, N=N)
