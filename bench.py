@@ -433,7 +433,8 @@ def other_systems(L, torch, dev, local, args):
     (27 quantities, 50,000 elements), isolated tetrahedra of the headline
     geometry at the headline degree.  Element-updates/s (CUDA events, mean of
     5 launches after 2 warm-ups) and the FP64 pipe fraction against the
-    nominal 1.25 TFLOP/s (flops from poro_flop_count)."""
+    nominal 1.25 TFLOP/s (flops from poro_flop_count).  Then the sub-cell
+    material predictor (Section "Limitations") on 20,000 Biot elements."""
     from paper_2108_10565_gb300 import inputs
 
     N = args.degree
@@ -473,6 +474,40 @@ def other_systems(L, torch, dev, local, args):
                      "flops_per_element": f, "fp64_tflops": ach, "fp64_frac_nominal": ach / 1.25}
         del q0, qt, io
         torch.cuda.empty_cache()
+    # sub-cell material (Section "Limitations"): Biot with linearly varying
+    # Jacobians, 20,000 elements, vertex materials +-10 % around each element's
+    # material; the Richardson iteration stops at a relative change of 1e-13
+    n = 20_000
+    d = inputs.subcell_isolated_elements(n, N, spread=0.1)
+    dt = np.minimum.reduce([L.poro_cfl_dt(N, d["vertices"], np.ascontiguousarray(d["materials"][:, v, :]))
+                            for v in range(4)])
+    q0 = torch.from_numpy(d["Q0"]).to(dev)
+    qt = torch.empty((n, 13, d["Q0"].shape[2], N + 1), dtype=torch.float64, device=dev)
+    io = torch.empty_like(q0)
+    ctx = L.poro_create(local, N, L.PORO_FP64)
+    try:
+        L.poro_set_isolated_subcell(ctx, d["vertices"], d["materials"], dt)
+        for _ in range(2):
+            L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                               st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(3):
+                L.poro_predict_dev(ctx, 0, n, q0.data_ptr(), qt.data_ptr(), io.data_ptr(), L.PORO_SOLVE_BLOCK,
+                                   st.cuda_stream)
+            e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        it = L.poro_get_subcell_iterations(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+    out["biot_subcell_linear_10pct"] = {
+        "elements": n, "ms_per_launch": ms, "element_updates_per_s": n / (ms * 1e-3),
+        "iterations": {"median": float(np.median(np.abs(it))), "max": int(np.abs(it).max()),
+                       "unconverged": int((it <= 0).sum())}}
+    del q0, qt, io
+    torch.cuda.empty_cache()
     return out
 
 
