@@ -623,7 +623,7 @@ def time_stepping_sections(L, local, args):
     return out
 
 
-def _serving_trace(L, args, n_req=None, size=(10_000, 500_000), cycles=None):
+def _serving_trace(L, args, n_req=None, size=(10_000, 500_000), cycles=None, seed_offset=0):
     """The served-ensemble requests: mesh sizes uniform in 10k-500k tets (Kuhn
     boxes of a 20 x 20 x 10 km domain, n_x = n_y = 2 n_z, free surface on
     top), degree uniform in {3, 4, 5, 6}, a 500 m layer over a half-space
@@ -634,7 +634,7 @@ def _serving_trace(L, args, n_req=None, size=(10_000, 500_000), cycles=None):
     configured 1 s of simulated time is cut)."""
     from paper_2108_10565_gb300 import inputs
 
-    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING + (0 if n_req is None else 2)))
+    rng = np.random.Generator(np.random.PCG64(inputs.SEED_SERVING + seed_offset))
     meshes = {}
     reqs = []
     cycles = args.serving_cycles if cycles is None else cycles
@@ -721,7 +721,7 @@ def serving_section(L, local, args):
                                                            False)
     # many small requests (2k-20k tets, 16 steps each), all at once: the case
     # where runs sharing launches matters
-    small = _serving_trace(L, args, n_req=48, size=(2_000, 20_000), cycles=16)
+    small = _serving_trace(L, args, n_req=48, size=(2_000, 20_000), cycles=16, seed_offset=2)
     z = np.zeros(len(small))
     out["small_requests"] = {"requests": len(small), "mesh_elements": [int(r["ne"]) for r in small],
                              "degrees": [int(r["N"]) for r in small],
@@ -731,6 +731,18 @@ def serving_section(L, local, args):
     sm = out["small_requests"]
     sm["batched_over_streams"] = (sm["capacity_batched_mixed"]["element_updates_per_s"]
                                   / sm["capacity_streams_mixed"]["element_updates_per_s"])
+    # tiny requests (500-3k tets, 64 steps each), all at once: launches of a
+    # few hundred CTAs, where one launch per degree group and tick pays most
+    tiny = _serving_trace(L, args, n_req=64, size=(500, 3_000), cycles=64, seed_offset=3)
+    z = np.zeros(len(tiny))
+    out["tiny_requests"] = {"requests": len(tiny), "mesh_elements": [int(r["ne"]) for r in tiny],
+                            "degrees": [int(r["N"]) for r in tiny],
+                            "element_updates_total": int(sum(r["updates"] for r in tiny)),
+                            "capacity_batched_mixed": _serve(L, local, tiny, z, bf, 64, True),
+                            "capacity_streams_mixed": _serve(L, local, tiny, z, bf, 64, False)}
+    tn = out["tiny_requests"]
+    tn["batched_over_streams"] = (tn["capacity_batched_mixed"]["element_updates_per_s"]
+                                  / tn["capacity_streams_mixed"]["element_updates_per_s"])
     return out
 
 

@@ -356,9 +356,22 @@ void executor_main(poro_server* s) {
             if (std::find(failed.begin(), failed.end(), r) != failed.end()) continue;
             (r->done >= r->total ? finished : still).push_back(r);
         }
+        // groups that hold a leaving run go (the others keep their tables
+        // and captured cycle)
         if (!finished.empty() || !failed.empty()) {
-            for (auto& kv : groups) poro::group_destroy(kv.second);
-            groups.clear();
+            std::vector<uint64_t> gone;
+            for (Request* r : finished) gone.push_back(r->ticket);
+            for (Request* r : failed) gone.push_back(r->ticket);
+            for (auto it = groups.begin(); it != groups.end();) {
+                bool hit = false;
+                for (uint64_t t : it->first) hit = hit || std::find(gone.begin(), gone.end(), t) != gone.end();
+                if (hit) {
+                    poro::group_destroy(it->second);
+                    it = groups.erase(it);
+                } else {
+                    ++it;
+                }
+            }
         }
         for (Request* r : finished) {
             collect_request(*r);
