@@ -211,14 +211,63 @@ def cpu_dense_lu_rate(args, budget_s, n_min=1):
     return done / el, cores, done, el
 
 
+def cpu_other_systems(N, budget_s):
+    """The oracle on the other systems' workloads (bounded samples, numpy):
+    Algorithm 3 on damped-Maxwell and viscoelastic elements and the dense
+    solve of the sub-cell material system, element-updates/s."""
+    from oracle import maxwell, predictor, subcell, viscoelastic
+    from paper_2108_10565_gb300 import inputs
+
+    out = {}
+
+    def timed(name, n, prep, solve):
+        t0 = time.perf_counter()
+        done = 0
+        while done < n and (done == 0 or time.perf_counter() - t0 < budget_s):
+            solve(*prep(done))
+            done += 1
+        el = time.perf_counter() - t0
+        out[name] = {"element_updates_per_s": done / el, "sample": f"first {done} elements, {el:.1f} s"}
+
+    dm = inputs.maxwell_isolated_elements(64, N)
+
+    def prep_m(i):
+        m = inputs.maxwell_dict(dm["materials"][i])
+        As, Es = maxwell.element_operators(dm["vertices"][i], m, maxwell.cfl_dt(dm["vertices"][i], m, N))
+        return As, Es, dm["Q0"][i]
+
+    timed("damped_maxwell_alg3_numpy", 64, prep_m, lambda A, E, q: predictor.predict_alg3(N, A, E, q))
+    dv = inputs.viscoelastic_isolated_elements(16, N)
+
+    def prep_v(i):
+        m = inputs.viscoelastic_dict(dv["materials"][i])
+        As, Es = viscoelastic.element_operators(dv["vertices"][i], m, viscoelastic.cfl_dt(dv["vertices"][i], m, N))
+        return As, Es, dv["Q0"][i]
+
+    timed("viscoelastic_alg3_numpy", 16, prep_v, lambda A, E, q: predictor.predict_alg3(N, A, E, q))
+    ds = inputs.subcell_isolated_elements(2, N, spread=0.1)
+
+    def prep_s(i):
+        from oracle import geometry
+        mats = [inputs.material_dict(r) for r in ds["materials"][i]]
+        dt = min(geometry.cfl_dt(ds["vertices"][i], m, N) for m in mats)
+        As, Es = subcell.element_operators(ds["vertices"][i], mats, dt)
+        return As, Es, ds["Q0"][i]
+
+    timed("biot_subcell_dense_lu", 2, prep_s, lambda A, E, q: subcell.predict_dense(N, A, E, q))
+    return out
+
+
 def cpu_baseline(args):
     """The oracle timed on the host cores: the plain-loop C Algorithm 3 on all
-    cores (the baseline), on one core, and the dense-LU definition."""
+    cores (the baseline), on one core, and the dense-LU definition; the
+    oracle on the other systems' workloads beside them."""
     nall = args.cpu_elems
     rate, cores, k, passes, el = cpu_alg3_rate(args.degree, args.cpu_budget_s, 0, nall)
     r1, _, k1, p1, el1 = cpu_alg3_rate(args.degree, args.cpu_budget_s / 3, 1, max(64, nall // 16))
     lu, lu_cores, lu_k, lu_el = cpu_dense_lu_rate(args, args.cpu_budget_s / 3)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+    other = None if args.no_systems else cpu_other_systems(args.degree, args.cpu_budget_s / 4)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "other_systems": other,
             "sample": f"oracle Algorithm 3 as plain C loops (binary64, OpenMP over elements, no BLAS, "
                       f"-ffp-contract=off): first {k} elements of the N={args.degree} workload, {passes} passes, "
                       f"{el:.1f} s on {cores} threads",
