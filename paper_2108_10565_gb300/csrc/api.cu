@@ -170,6 +170,7 @@ void free_lu(poro_ctx* c) {
     dfree(c->lu.R);
     dfree(c->lu.C);
     dfree(c->lu.bad);
+    dfree(c->lu.x);
     c->lu_first = c->lu_count = 0;
 }
 
@@ -944,7 +945,8 @@ poro_status poro_lu_factor(poro_ctx* c, int64_t first, int64_t count) {
         (e = cudaMalloc((void**)&c->lu.perm, (size_t)count * s * sizeof(int32_t) + 16)) != cudaSuccess ||
         (e = cudaMalloc((void**)&c->lu.R, (size_t)count * s * sizeof(double) + 16)) != cudaSuccess ||
         (e = cudaMalloc((void**)&c->lu.C, (size_t)count * s * sizeof(double) + 16)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&c->lu.bad, sizeof(int32_t))) != cudaSuccess) {
+        (e = cudaMalloc((void**)&c->lu.bad, sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&c->lu.x, (size_t)count * s * sizeof(double) + 16)) != cudaSuccess) {
         free_lu(c);
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? fail(c, PORO_ENOMEM, "poro_lu_factor: factors do not fit in HBM")

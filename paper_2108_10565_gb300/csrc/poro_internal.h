@@ -282,6 +282,7 @@ struct LUScratch {
     double* R = nullptr;       // [count][s]
     double* C = nullptr;       // [count][s]
     int32_t* bad = nullptr;    // 1 if a zero pivot occurred
+    double* x = nullptr;       // [count][s] solution scratch of the blocked solve (nullable: one CTA per element)
 };
 size_t lu_scratch_bytes(int N, int64_t count);
 int launch_lu_factor(const LUReference& ref, int64_t count, const double* econst, LUScratch& w, void* stream);
