@@ -45,6 +45,29 @@ def test_lu_matches_oracle(L, N, n):
         np.testing.assert_allclose(io_lu[i], d["dt"][i] * qt_lu[i][:, :, 0], rtol=0, atol=1e-300)
 
 
+def test_lu_one_cta_form_for_many_elements(L):
+    """160 elements (at least one per SM): the triangular solves run one CTA
+    per element (fewer elements take the blocked form tested above); against
+    the block kernel on all, the dense oracle on three."""
+    N, n = 2, 160
+    d = population(n, N, seed=520)
+    ctx = L.poro_create(0, N, L.PORO_FP64)
+    try:
+        L.poro_set_isolated(ctx, d["vertices"], d["materials"], d["dt"])
+        L.poro_set_dofs(ctx, d["Q0"])
+        L.poro_lu_factor(ctx, 0, n)
+        L.poro_predict(ctx, -1, L.PORO_SOLVE_LU)
+        qt_lu = L.poro_get_predictor(ctx, 0, n)
+        L.poro_predict(ctx, -1, L.PORO_SOLVE_BLOCK)
+        qt_blk = L.poro_get_predictor(ctx, 0, n)
+    finally:
+        L.poro_destroy(ctx)
+    for i in range(n):
+        assert rel_l2(qt_lu[i], qt_blk[i]) <= TOL
+    for i in (0, 77, 159):
+        assert rel_l2(qt_lu[i], oracle_predictor(d, i, dense=True)) <= TOL
+
+
 def test_lu_sub_batch_n6_matches_block(L):
     """N = 6 (s = 7,644, 467 MB of factors per element): a sub-batch of two
     elements in the middle of the population, through the device-pointer
