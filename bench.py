@@ -569,6 +569,52 @@ def _setup_mesh_ctx(L, N, prec, mesh, mats, C, local=0, graphs=True):
     return ctx, dt, cl
 
 
+def cfg2_mesh_steps(L, local, args):
+    """The mixed predictor + corrector configuration at N = 5 and 6 on the
+    isolated population's materials: a periodic Kuhn mesh of 196,608 tets
+    (32^3 boxes) stands in for isolated elements with permutation neighbours
+    (the library's corrector needs conforming faces); each element's 10
+    material parameters are scaled by U[0.8, 1.2] (skeleton moduli tied) and
+    Q0 ~ N(0, 1), seed 2108105652.  A GTS step is the predictor and the
+    corrector of every element.  Element-updates/s over 3 steps after one
+    warm-up step, and each mixed form's relative L2 error per element after
+    one step against the FP64 form."""
+    from paper_2108_10565_gb300 import inputs
+
+    mesh = inputs.kuhn_box_mesh(32)
+    ne = mesh["tets"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(inputs.SEED_CFG2))
+    mats = inputs.perturbed_materials(rng, ne, tie_skeleton=True)
+    out = {"n_elem": ne}
+    for N in (5, 6):
+        B = (N + 1) * (N + 2) * (N + 3) // 6
+        q0 = np.random.Generator(np.random.PCG64(inputs.SEED_CFG2 + N)).standard_normal((ne, 13, B))
+        ref = None
+        row = {}
+        for name, prec in (("fp64", L.PORO_FP64), ("mixed_bf16x3_K1", L.PORO_BF16X3_REFINE)):
+            t0 = time.perf_counter()
+            ctx, dt, _ = _setup_mesh_ctx(L, N, prec, mesh, mats, 1, local)
+            setup = time.perf_counter() - t0
+            try:
+                L.poro_set_dofs(ctx, q0)
+                L.poro_advance(ctx, 1.5 * dt)  # one step (and the warm-up)
+                q1 = L.poro_get_dofs(ctx)
+                t0 = time.perf_counter()
+                L.poro_advance(ctx, 4.5 * dt)
+                el = time.perf_counter() - t0
+            finally:
+                L.poro_destroy(ctx)
+            r = {"ms_per_step": el / 3 * 1e3, "element_updates_per_s": ne * 3 / el, "host_setup_s": setup}
+            if ref is None:
+                ref = q1
+            else:
+                e = np.linalg.norm((q1 - ref).reshape(ne, -1), axis=1) / np.linalg.norm(ref.reshape(ne, -1), axis=1)
+                r["error_vs_fp64_after_one_step"] = {"median": float(np.median(e)), "max": float(e.max())}
+            row[name] = r
+        out[f"N{N}"] = row
+    return out
+
+
 def time_stepping_sections(L, local, args):
     """Full ADER-DG steps (predictor + corrector + sources + receivers) under
     global and clustered local time stepping; wall-clock time to solution of
@@ -608,6 +654,7 @@ def time_stepping_sections(L, local, args):
         L.poro_destroy(ctx)
         r[name] = {"seconds": el, "steps": nsteps, "element_updates_per_s": ne * nsteps / el}
     out[f"periodic_{ne}_N5_gts"] = r
+    out["cfg2_periodic_mesh_N5_N6"] = cfg2_mesh_steps(L, local, args)
     # clustered LTS vs GTS on the layered graded mesh, same simulated time:
     # the configured 32x grading (3 populated clusters) and a 512x grading
     # that populates all 6; per-cluster GPU time of one cycle

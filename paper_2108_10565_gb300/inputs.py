@@ -226,6 +226,7 @@ def config0_scenario():
 # layer over half-space (Table material_heterogeneous columns, viscous fluid)
 LAYER_MATERIAL = np.array([7.6e9, 2210.0, 3.96e9, 3.96e9, 1e-12, 0.16, 2.0, 2.5e9, 1040.0, 1e-3])
 HALFSPACE_MATERIAL = np.array([40e9, 2500.0, 12e9, 12e9, 6e-12, 0.2, 2.0, 2.5e9, 1040.0, 1e-3])
+SEED_CFG2 = 2108105652
 SEED_LOH = 2108105653
 SEED_SERVING = 2108105654
 
