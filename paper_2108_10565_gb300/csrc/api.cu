@@ -81,6 +81,7 @@ struct poro_ctx {
     std::vector<int32_t*> d_cl_elems;
     int32_t *d_cl = nullptr, *d_slot = nullptr;
     double* d_buf = nullptr;
+    std::vector<char> cl_has_slot;             // a cluster with elements that buffer for a larger neighbour
     bool use_graphs = true;
     int64_t* d_tick = nullptr;                 // device copy of the tick counter (graph replays)
     // persistent receiver buffers (no allocation in steady-state advances)
@@ -1380,10 +1381,14 @@ poro_status poro_set_clusters(poro_ctx* c, double cfl_c, int32_t max_clusters, d
     for (int64_t e = 0; e < ne; ++e) c->cl_elems[c->h_cl[e]].push_back((int32_t)e);
     std::vector<int32_t> slot((size_t)ne * C, -1);
     int32_t nslot = 0;
+    c->cl_has_slot.assign(C, 0);
     for (int64_t e = 0; e < ne; ++e)
         for (int f = 0; f < 4; ++f) {
             const int64_t r = c->h_nb[4 * e + f];
-            if (r >= 0 && c->h_cl[r] > c->h_cl[e] && slot[e * C + c->h_cl[r]] < 0) slot[e * C + c->h_cl[r]] = nslot++;
+            if (r >= 0 && c->h_cl[r] > c->h_cl[e] && slot[e * C + c->h_cl[r]] < 0) {
+                slot[e * C + c->h_cl[r]] = nslot++;
+                c->cl_has_slot[c->h_cl[e]] = 1;
+            }
         }
     for (int k = 0; k < C; ++k) {
         int32_t* d = nullptr;
@@ -1513,7 +1518,8 @@ static int enqueue_tick(poro_ctx* c, int64_t k, unsigned what, const double* d_r
         else if (predict)
             rc = poro::launch_stp_mixed(c->mref, c->refine, el, cnt, c->d_q0, c->d_econst,
                                         want_qt ? c->d_qt : nullptr, c->d_iout, st, c->variant);
-        if (rc == 0 && C > 1 && (what & TICK_BUFFERS))
+        // (a cluster whose elements buffer for no larger neighbour has nothing to add)
+        if (rc == 0 && C > 1 && (what & TICK_BUFFERS) && c->cl_has_slot[cl])
             rc = poro::launch_lts_buffers(c->N, C, el, cnt, c->d_slot, c->d_iout, c->d_buf, k, st);
         if (rc == 0) rc = mark(prof, cl, false, st);
     }
@@ -1687,6 +1693,12 @@ struct RunGroup {
     int32_t* d_citems = nullptr;
     int32_t* d_citem_run = nullptr;
     std::vector<int64_t> ck_off, ck_cnt;
+    // per tick residue k the point sources and the receivers of all runs
+    // due at k (built for the runs' current receiver buffers)
+    TickItem* d_src = nullptr;
+    TickItem* d_rec = nullptr;
+    int64_t** d_ticks = nullptr;     // the runs' tick counters
+    std::vector<int64_t> src_off, src_cnt, rec_off, rec_cnt;
     int64_t pending = 0;             // ticks enqueued since the last group_finish
     // captured cycle, valid while every run's receiver buffers stay the same
     cudaGraphExec_t exec = nullptr;
@@ -1714,11 +1726,11 @@ static int enqueue_group_cycle(RunGroup* g) {
         if (rc == 0 && cc > 0)
             rc = launch_corrector(lead->cd, g->d_citems + g->ck_off[k], cc, g->stream,
                                   g->d_cdata + k * (int64_t)g->runs.size(), g->d_citem_run + g->ck_off[k]);
-        for (poro_ctx* c : g->runs)
-            if (rc == 0) rc = enqueue_tick(c, k, TICK_SOURCES, c->d_rp, c->d_seis, c->seis_cap, c->d_cnt, g->stream);
+        // all runs' sources of the tick, then all their receivers (one launch each)
+        if (rc == 0) rc = launch_tick_sources(lead->N, g->d_src + g->src_off[k], g->src_cnt[k], g->stream);
+        if (rc == 0) rc = launch_tick_receivers(lead->N, g->d_rec + g->rec_off[k], g->rec_cnt[k], g->stream);
     }
-    for (poro_ctx* c : g->runs)
-        if (rc == 0) rc = launch_tick_advance(c->d_tick, g->cycle, g->stream);
+    if (rc == 0) rc = launch_ticks_advance(g->d_ticks, (int)g->runs.size(), g->cycle, g->stream);
     return rc;
 }
 
@@ -1733,6 +1745,9 @@ void group_destroy(RunGroup* g) {
     dfree(g->d_cdata);
     dfree(g->d_citems);
     dfree(g->d_citem_run);
+    dfree(g->d_src);
+    dfree(g->d_rec);
+    dfree(g->d_ticks);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1816,6 +1831,61 @@ RunGroup* group_create(poro_ctx* const* runs, int n, std::string& err) {
 
 // Enqueue n_cycles cycles of every run of the group (asynchronous on the
 // group's stream); group_finish completes them.
+// the source and receiver items of every tick residue, for the runs'
+// current receiver buffers (synchronous upload; the group's stream is idle)
+static int group_tick_items(RunGroup* g) {
+    std::vector<TickItem> src, rec;
+    g->src_off.clear();
+    g->src_cnt.clear();
+    g->rec_off.clear();
+    g->rec_cnt.clear();
+    for (int64_t k = 0; k < g->cycle; ++k) {
+        g->src_off.push_back((int64_t)src.size());
+        g->rec_off.push_back((int64_t)rec.size());
+        for (poro_ctx* c : g->runs) {
+            for (int cl = 0; cl < g->C; ++cl) {
+                const int64_t len = (int64_t)1 << cl;
+                if ((k + 1) % len || c->cl_elems[cl].empty()) continue;
+                for (auto& sr : c->sources)
+                    if (c->h_cl[sr.elem] == cl) {
+                        TickItem it;
+                        it.q = c->d_q0;
+                        it.vec = sr.d_coef;
+                        it.tick = c->d_tick;
+                        it.elem = sr.elem;
+                        it.len = len;
+                        it.k_rel = k;
+                        it.f0 = sr.f0;
+                        it.tc = sr.t0;
+                        it.dt = c->dt;
+                        src.push_back(it);
+                    }
+                for (int r = 0; r < (int)c->rec_elem.size(); ++r)
+                    if (c->h_cl[c->rec_elem[r]] == cl) {
+                        TickItem it;
+                        it.q = c->d_q0;
+                        it.vec = c->d_rp + (size_t)r * c->B;
+                        it.out = c->d_seis + (size_t)r * c->seis_cap * NQ;
+                        it.counter = c->d_cnt + r;
+                        it.elem = c->rec_elem[r];
+                        rec.push_back(it);
+                    }
+            }
+        }
+        g->src_cnt.push_back((int64_t)src.size() - g->src_off.back());
+        g->rec_cnt.push_back((int64_t)rec.size() - g->rec_off.back());
+    }
+    std::vector<int64_t*> ticks;
+    for (poro_ctx* c : g->runs) ticks.push_back(c->d_tick);
+    dfree(g->d_src);
+    dfree(g->d_rec);
+    dfree(g->d_ticks);
+    cudaError_t e = upload((void**)&g->d_src, src.data(), src.size() * sizeof(TickItem));
+    if (e == cudaSuccess) e = upload((void**)&g->d_rec, rec.data(), rec.size() * sizeof(TickItem));
+    if (e == cudaSuccess) e = upload((void**)&g->d_ticks, ticks.data(), ticks.size() * sizeof(int64_t*));
+    return (int)e;
+}
+
 int group_enqueue(RunGroup* g, int64_t n_cycles, std::string& err) {
     if (n_cycles <= 0) return 0;
     cudaSetDevice(g->device);
@@ -1836,7 +1906,8 @@ int group_enqueue(RunGroup* g, int64_t n_cycles, std::string& err) {
         // first cycle directly (sets the kernels' attributes), then capture
         if (g->exec) cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
-        rc = enqueue_group_cycle(g);
+        rc = group_tick_items(g);
+        if (rc == 0) rc = enqueue_group_cycle(g);
         done = 1;
         if (rc == 0 && n_cycles > 1) {
             cudaGraph_t graph = nullptr;

@@ -239,6 +239,38 @@ __global__ void receiver_count_kernel(int B, const double* q, int64_t elem, cons
 
 __global__ void tick_advance_kernel(int64_t* tick, int64_t n) { *tick += n; }
 
+__global__ void ticks_advance_kernel(int64_t* const* ticks, int count, int64_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) *ticks[i] += n;
+}
+
+// one CTA per source item of a batched group: the arithmetic of
+// point_source_tick_kernel
+__global__ void source_items_kernel(int QB, const TickItem* items) {
+    const TickItem& it = items[blockIdx.x];
+    const int64_t k = *it.tick + it.k_rel;
+    const double t1 = (double)(k + 1) * it.dt, t0 = (double)(k + 1 - it.len) * it.dt;
+    const double a1 = 3.14159265358979323846 * it.f0 * (t1 - it.tc), a0 = 3.14159265358979323846 * it.f0 * (t0 - it.tc);
+    const double amp = (t1 - it.tc) * exp(-a1 * a1) - (t0 - it.tc) * exp(-a0 * a0);
+    double* q = it.q + it.elem * QB;
+    for (int i = threadIdx.x; i < QB; i += blockDim.x) q[i] += amp * it.vec[i];
+}
+
+// one CTA per receiver item: the arithmetic of receiver_count_kernel
+__global__ void receiver_items_kernel(int B, const TickItem* items) {
+    const TickItem& it = items[blockIdx.x];
+    const int p = threadIdx.x;
+    const int32_t idx = *it.counter;
+    if (p < NQ) {
+        const double* qe = it.q + it.elem * (int64_t)(NQ * B) + p * B;
+        double acc = 0.0;
+        for (int l = 0; l < B; ++l) acc = fma(qe[l], it.vec[l], acc);
+        it.out[(int64_t)idx * NQ + p] = acc;
+    }
+    __syncthreads();
+    if (p == 0) *it.counter = idx + 1;
+}
+
 __global__ void point_source_kernel(int QB, double* q, int64_t elem, const double* coef, double amp) {
     for (int i = threadIdx.x; i < QB; i += blockDim.x) q[elem * QB + i] += amp * coef[i];
 }
@@ -303,6 +335,24 @@ int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef,
 int launch_receiver_count(int N, const double* q, int64_t elem, const double* phi, double* out, int32_t* counter,
                           void* stream) {
     receiver_count_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(n_modes(N), q, elem, phi, out, counter);
+    return (int)cudaGetLastError();
+}
+
+int launch_tick_sources(int N, const TickItem* items, int64_t count, void* stream) {
+    if (count <= 0) return 0;
+    source_items_kernel<<<(unsigned)count, 256, 0, (cudaStream_t)stream>>>(NQ * n_modes(N), items);
+    return (int)cudaGetLastError();
+}
+
+int launch_tick_receivers(int N, const TickItem* items, int64_t count, void* stream) {
+    if (count <= 0) return 0;
+    receiver_items_kernel<<<(unsigned)count, 32, 0, (cudaStream_t)stream>>>(n_modes(N), items);
+    return (int)cudaGetLastError();
+}
+
+int launch_ticks_advance(int64_t* const* ticks, int count, int64_t n, void* stream) {
+    if (count <= 0) return 0;
+    ticks_advance_kernel<<<(unsigned)((count + 127) / 128), 128, 0, (cudaStream_t)stream>>>(ticks, count, n);
     return (int)cudaGetLastError();
 }
 

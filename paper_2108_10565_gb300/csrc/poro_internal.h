@@ -345,6 +345,24 @@ int launch_corrector(const CorrectorData& d, const int32_t* elems, int64_t count
 int launch_corrector_dw(const CorrectorData& d, const int32_t* elems, int64_t count, void* stream,
                         const CorrectorData* runs = nullptr, const int32_t* item_run = nullptr);
 int launch_point_source(int N, double* q, int64_t elem, const double* coef, double amp, void* stream);
+// One point source or receiver of one run, for the launches of a batched
+// group that serve all its runs' sources (then receivers) of a tick.
+// Source: q[elem] += (S(t1) - S(t0)) coef over the step [(k+1-len) dt,
+// (k+1) dt], k = *tick + k_rel.  Receiver: out[*counter] = Q[elem] phi, then
+// ++*counter.
+struct TickItem {
+    double* q = nullptr;
+    const double* vec = nullptr;     // coef (source) or phi (receiver)
+    double* out = nullptr;           // receiver samples
+    int32_t* counter = nullptr;      // receiver sample counter
+    const int64_t* tick = nullptr;   // the run's tick counter (source)
+    int64_t elem = 0, len = 1, k_rel = 0;
+    double f0 = 0.0, tc = 0.0, dt = 0.0;
+};
+int launch_tick_sources(int N, const TickItem* items, int64_t count, void* stream);
+int launch_tick_receivers(int N, const TickItem* items, int64_t count, void* stream);
+// *ticks[i] += n for i < count (the tick counters of a group's runs)
+int launch_ticks_advance(int64_t* const* ticks, int count, int64_t n, void* stream);
 int launch_point_source_tick(int N, double* q, int64_t elem, const double* coef, double f0, double tc, double dt,
                              int64_t len, int64_t k_rel, const int64_t* tick, void* stream);
 int launch_receiver_count(int N, const double* q, int64_t elem, const double* phi, double* out, int32_t* counter,
