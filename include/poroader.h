@@ -248,7 +248,8 @@ poro_status poro_set_isolated_subcell(poro_ctx* ctx, int64_t n_elem, const doubl
 poro_status poro_set_subcell_tolerance(poro_ctx* ctx, double tol, int32_t max_iter);
 
 /* Iterations each element of [first, first + count) took in the last
- * sub-cell predictor (synchronises the context stream): k > 0 converged
+ * sub-cell predictor (synchronises the context stream; after a
+ * poro_predict_dev on another stream, synchronise that stream first): k > 0 converged
  * after k iterations, -k stopped at max_iter = k without converging or on a
  * non-finite iterate, 0 not run.  Errors: PORO_ESTATE (no sub-cell
  * population), PORO_EINVAL, PORO_ECUDA. */
