@@ -1021,11 +1021,18 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        per = []
         for _ in range(args.steps):
+            t1 = time.perf_counter()
             L.poro_predict_host(ctx, hq_np, out=hi_np)
+            per.append(time.perf_counter() - t1)
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+        # the value is the mean over the steps; single calls vary with the host
+        # side of the copies (reported beside it)
         e2e = {"value": job_rate(n, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 8),
-               "d2h_bytes_per_step": int(hi.numel() * 8), "form": head}
+               "d2h_bytes_per_step": int(hi.numel() * 8), "form": head,
+               "ms_per_step": {"mean": 1e3 * e2e_s, "median": 1e3 * float(np.median(per)),
+                               "min": 1e3 * min(per), "max": 1e3 * max(per)}}
     for r in res.values():
         L.poro_destroy(r["ctx"])
     steps = serving = None
