@@ -67,7 +67,7 @@ struct K1Shape : Alg3Shape<N, Sys::NQ> {
 template <int N, int NT_, class Sys = BiotSystem>
 __global__ void __launch_bounds__(NT_) stp_fp64_kernel(const K1Params P) {
     using S = K1Shape<N, NT_, Sys>;
-    constexpr int NQ = Sys::NQ, STAR_NNZ = Sys::NNZ;
+    constexpr int NQ = Sys::NQ;
     constexpr int B = S::B, T = S::T, NT = S::NT, QS = S::QS;
     extern __shared__ double sm[];
     double* bq = sm;

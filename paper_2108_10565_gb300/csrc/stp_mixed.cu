@@ -402,7 +402,7 @@ __device__ bool alg3_sweep_tc(float* bq, const float* star, const float* zuf, co
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             const int abuf = j % L.nA, slot = j % L.nB;
-            const uint32_t mma_bar = S.bar_s + 8u * (uint32_t)abuf, ld_bar = S.bar_s + 16u + 8u * (uint32_t)slot;
+            const uint32_t mma_bar = S.bar_s + 8u * (uint32_t)abuf;
             if (j >= L.nA) {  // the MMAs of direction j - nA (and all before) are done
                 tc_wait(S, (uint32_t)abuf);
                 // their slots are free: load the images not yet in flight
