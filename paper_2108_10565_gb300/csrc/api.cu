@@ -172,6 +172,8 @@ void free_lu(poro_ctx* c) {
     dfree(c->lu.C);
     dfree(c->lu.bad);
     dfree(c->lu.x);
+    if (c->lu.exec) cudaGraphExecDestroy(c->lu.exec);
+    c->lu.exec = nullptr;
     c->lu_first = c->lu_count = 0;
 }
 

@@ -266,32 +266,62 @@ __global__ void lu_bsolve_init(int N, const int32_t* perm, const double* R, cons
 }
 
 // the triangle of block [rb, rb + nr): unit lower (forward) or upper with
-// its diagonal (backward); BS threads, the block in shared memory
+// its diagonal (backward).  BS threads stage the block into shared memory
+// with asynchronous 8-byte copies (all in flight at once); then one warp
+// solves it, each lane holding rows lane + 32 i in registers and the solved
+// value broadcast by shuffles, with no CTA barrier per row.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
 __global__ void __launch_bounds__(BS) lu_bsolve_diag(int s, int rb, int nr, bool lower, const double* A, double* x) {
     extern __shared__ double blk[];  // [BS][BS + 1]
-    __shared__ double xs[BS];
+    constexpr int RPL = BS / 32;     // rows per lane
     const int64_t e = blockIdx.x;
     const double* Ae = A + (size_t)e * s * s;
     double* xe = x + e * (int64_t)s;
     const int t = threadIdx.x;
-    for (int r = 0; r < nr; ++r)
-        if (t < nr) blk[r * (BS + 1) + t] = Ae[(size_t)(rb + r) * s + rb + t];
-    if (t < nr) xs[t] = xe[rb + t];
+    if (t < nr)
+        for (int r = 0; r < nr; ++r) cp_async8(blk + r * (BS + 1) + t, Ae + (size_t)(rb + r) * s + rb + t);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
+    if (t >= 32) return;
+    double xv[RPL];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) xv[i] = t + 32 * i < nr ? xe[rb + t + 32 * i] : 0.0;
     if (lower) {
         for (int k = 0; k < nr; ++k) {
-            if (t > k && t < nr) xs[t] = fma(-blk[t * (BS + 1) + k], xs[k], xs[t]);
-            __syncthreads();
+            const int slot = k >> 5;
+            double own = xv[0];
+#pragma unroll
+            for (int i = 1; i < RPL; ++i) own = slot == i ? xv[i] : own;
+            const double xk = __shfl_sync(0xffffffffu, own, k & 31);
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+                const int r = t + 32 * i;
+                if (r > k && r < nr) xv[i] = fma(-blk[r * (BS + 1) + k], xk, xv[i]);
+            }
         }
     } else {
         for (int k = nr - 1; k >= 0; --k) {
-            if (t == k) xs[k] = xs[k] / blk[k * (BS + 1) + k];
-            __syncthreads();
-            if (t < k) xs[t] = fma(-blk[t * (BS + 1) + k], xs[k], xs[t]);
-            __syncthreads();
+            const int slot = k >> 5;
+            double own = xv[0];
+#pragma unroll
+            for (int i = 1; i < RPL; ++i) own = slot == i ? xv[i] : own;
+            if ((k & 31) == t) own = own / blk[k * (BS + 1) + k];
+            const double xk = __shfl_sync(0xffffffffu, own, k & 31);
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) {
+                const int r = t + 32 * i;
+                if (r == k) xv[i] = xk;
+                else if (r < k) xv[i] = fma(-blk[r * (BS + 1) + k], xk, xv[i]);
+            }
         }
     }
-    if (t < nr) xe[rb + t] = xs[t];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i)
+        if (t + 32 * i < nr) xe[rb + t + 32 * i] = xv[i];
 }
 
 // x[i] -= sum_{j < nr} A[i, rb + j] x[rb + j] for the rows [r0, r1) of every
@@ -328,14 +358,12 @@ __global__ void lu_bsolve_out(int N, const double* C, const double* x, const dou
     if (iout && (i % T) == 0) iout[e * (int64_t)(NQ * B) + i / T] = econst[e * stride + ec_scalars(N) + 2] * v;
 }
 
-int launch_lu_bsolve(int N, int64_t count, const LUScratch& w, int64_t offset, const double* q0, const double* econst,
-                     double* qt, double* iout, cudaStream_t st) {
+int enqueue_lu_bsolve(int N, int64_t count, const LUScratch& w, int64_t offset, const double* q0, const double* econst,
+                      double* qt, double* iout, cudaStream_t st) {
     const int B = n_modes(N), T = N + 1, s = NQ * B * T;
     const double* A = w.A + (size_t)offset * s * s;
     double* x = w.x;  // [count][s]
     const size_t smem = sizeof(double) * BS * (BS + 1);
-    cudaError_t err = cudaFuncSetAttribute(lu_bsolve_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return (int)err;
     const dim3 gv((s + 255) / 256, (unsigned)count);
     lu_bsolve_init<<<gv, 256, 0, st>>>(N, w.perm + offset * s, w.R + offset * s, q0, x);
     const int nb = (s + BS - 1) / BS;
@@ -356,6 +384,42 @@ int launch_lu_bsolve(int N, int64_t count, const LUScratch& w, int64_t offset, c
     }
     lu_bsolve_out<<<gv, 256, 0, st>>>(N, w.C + offset * s, x, econst, elem_const_stride(N), qt, iout);
     return (int)cudaGetLastError();
+}
+
+// The ~2 s / 64 launches of a solve as one CUDA graph (captured on a private
+// stream, re-captured when a pointer or the count changes), launched on st.
+int launch_lu_bsolve(int N, int64_t count, LUScratch& w, int64_t offset, const double* q0, const double* econst,
+                     double* qt, double* iout, cudaStream_t st) {
+    const int B = n_modes(N), T = N + 1, s = NQ * B * T;
+    cudaError_t err = cudaFuncSetAttribute(lu_bsolve_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * BS * (BS + 1)));
+    if (err != cudaSuccess) return (int)err;
+    const void* key[10] = {w.A + (size_t)offset * s * s, w.x, w.perm + offset * s, w.R + offset * s,
+                           w.C + offset * s, q0, econst, qt, iout, (const void*)(intptr_t)count};
+    bool same = w.exec != nullptr;
+    for (int i = 0; i < 10 && same; ++i) same = key[i] == w.key[i];
+    if (!same) {
+        if (w.exec) cudaGraphExecDestroy(w.exec);
+        w.exec = nullptr;
+        cudaStream_t cs = nullptr;
+        cudaGraph_t graph = nullptr;
+        err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (err == cudaSuccess) {
+            const int rc = enqueue_lu_bsolve(N, count, w, offset, q0, econst, qt, iout, cs);
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            err = rc != 0 ? (cudaError_t)rc : e2;
+        }
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&w.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        if (err != cudaSuccess) {
+            w.exec = nullptr;
+            return (int)err;
+        }
+        for (int i = 0; i < 10; ++i) w.key[i] = key[i];
+    }
+    return (int)cudaGraphLaunch(w.exec, st);
 }
 
 }  // namespace
@@ -391,7 +455,7 @@ int launch_lu_factor(const LUReference& ref, int64_t count, const double* econst
     return (int)cudaGetLastError();
 }
 
-int launch_lu_solve(const LUReference& ref, int64_t count, const LUScratch& w, int64_t offset, const double* q0,
+int launch_lu_solve(const LUReference& ref, int64_t count, LUScratch& w, int64_t offset, const double* q0,
                     const double* econst, double* qt, double* iout, void* stream) {
     const int N = ref.N, B = n_modes(N), T = N + 1, s = NQ * B * T;
     if (count <= 0) return 0;

@@ -8,6 +8,10 @@
 
 #include "../../include/poroader.h"
 
+// the CUDA runtime's graph-exec handle (cudaGraphExec_t points to it),
+// declared here for the host translation units built without CUDA headers
+struct CUgraphExec_st;
+
 namespace poro {
 
 constexpr int NQ = 13;
@@ -283,10 +287,14 @@ struct LUScratch {
     double* C = nullptr;       // [count][s]
     int32_t* bad = nullptr;    // 1 if a zero pivot occurred
     double* x = nullptr;       // [count][s] solution scratch of the blocked solve (nullable: one CTA per element)
+    // the blocked solve's launches captured as a CUDA graph, valid for the
+    // pointers and counts in key
+    CUgraphExec_st* exec = nullptr;  // a cudaGraphExec_t
+    const void* key[10] = {};
 };
 size_t lu_scratch_bytes(int N, int64_t count);
 int launch_lu_factor(const LUReference& ref, int64_t count, const double* econst, LUScratch& w, void* stream);
-int launch_lu_solve(const LUReference& ref, int64_t count, const LUScratch& w, int64_t offset, const double* q0,
+int launch_lu_solve(const LUReference& ref, int64_t count, LUScratch& w, int64_t offset, const double* q0,
                     const double* econst, double* qt, double* iout, void* stream);
 
 // Read-only view of the context fields the allocation-free LU entry point
