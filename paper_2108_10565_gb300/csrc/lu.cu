@@ -386,8 +386,9 @@ int enqueue_lu_bsolve(int N, int64_t count, const LUScratch& w, int64_t offset, 
     return (int)cudaGetLastError();
 }
 
-// The ~2 s / 64 launches of a solve as one CUDA graph (captured on a private
-// stream, re-captured when a pointer or the count changes), launched on st.
+// The 4 * ceil(s / BS) launches of a blocked solve (240 at N = 6) as one CUDA
+// graph (captured on a private stream, re-captured when a pointer or the count
+// changes), launched on st.
 int launch_lu_bsolve(int N, int64_t count, LUScratch& w, int64_t offset, const double* q0, const double* econst,
                      double* qt, double* iout, cudaStream_t st) {
     const int B = n_modes(N), T = N + 1, s = NQ * B * T;
@@ -461,7 +462,7 @@ int launch_lu_solve(const LUReference& ref, int64_t count, LUScratch& w, int64_t
     if (count <= 0) return 0;
     // fewer elements than SMs (one CTA per element would leave most SMs idle)
     // and a solution scratch: the blocked solve over all SMs.  Measured on
-    // GB300: N = 6, 4 elements 480 element-solves/s against 191 with one CTA
+    // GB300: N = 6, 4 elements 540 element-solves/s against 191 with one CTA
     // per element; N = 3, 1,024 elements 97k against 130k, so many elements
     // keep the one-CTA form.
     if (w.x && s > 2 * BS && count < 152)
