@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(SOLVE_NT) lu_solve_kernel(int N, const double*
 // rows (row chunks of every element spread over the GPU).  The launches
 // follow each other on the stream, so no CTA waits for another.
 constexpr int BS = 128;      // unknowns per block
-constexpr int PANEL_ROWS = 64;  // rows per CTA of the panel update
+constexpr int PANEL_ROWS = 16;  // rows per CTA of the panel update (two per warp)
 
 // x = P (R r'),  r'[(p,k,r)] = (2r+1)(-1)^r Q0[p,k]
 __global__ void lu_bsolve_init(int N, const int32_t* perm, const double* R, const double* q0, double* x) {
@@ -462,7 +462,7 @@ int launch_lu_solve(const LUReference& ref, int64_t count, LUScratch& w, int64_t
     if (count <= 0) return 0;
     // fewer elements than SMs (one CTA per element would leave most SMs idle)
     // and a solution scratch: the blocked solve over all SMs.  Measured on
-    // GB300: N = 6, 4 elements 540 element-solves/s against 191 with one CTA
+    // GB300: N = 6, 4 elements 578 element-solves/s against 191 with one CTA
     // per element; N = 3, 1,024 elements 97k against 130k, so many elements
     // keep the one-CTA form.
     if (w.x && s > 2 * BS && count < 152)
