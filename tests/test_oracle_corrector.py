@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 from scipy.special import roots_legendre
 
-from oracle import basis, corrector, flux, material
+from oracle import basis, corrector, flux, material, planewave
 from paper_2108_10565_gb300 import inputs
 
 
@@ -257,3 +257,81 @@ def test_lts_conserves_domain_integrals():
         change = np.sum(vol * (Q1[:, q, 0] - Q0[:, q, 0]))
         scale = np.sum(vol * np.abs(Q1[:, q, 0] - Q0[:, q, 0]))
         assert abs(change) <= 1e-12 * scale
+
+
+def _graded_slab_mesh():
+    """Boxes graded in x (absorbing x faces), 3 periodic boxes of 0.4 in y and
+    z.  Box widths 0.4 0.4 0.4 0.2 | 0.025 0.025 | 0.1 | 0.2 0.4 0.4 0.4 give
+    three rate-2 clusters (0.025-wide boxes in cluster 0, 0.1 in 1, the rest
+    in 2) with faces between clusters 0 | 2, 0 | 1 and 1 | 2."""
+    w = [0.4] * 3 + [0.2, 0.025, 0.025, 0.1, 0.2] + [0.4] * 3
+    cx = np.concatenate([[0.0], np.cumsum(w)])
+    cy = np.linspace(0.0, 1.2, 4)
+    return inputs.kuhn_box_mesh((len(w), 3, 3), periodic=(False, True, True), coords=[cx, cy, cy])
+
+
+def _hops_from_boundary(nb):
+    """Face-hop distance of every element from the elements with a boundary face."""
+    dist = np.where((nb < 0).any(axis=1), 0, np.iinfo(np.int64).max)
+    frontier = list(np.nonzero(dist == 0)[0])
+    while frontier:
+        nxt = []
+        for e in frontier:
+            for r in nb[e]:
+                if r >= 0 and dist[r] > dist[e] + 1:
+                    dist[r] = dist[e] + 1
+                    nxt.append(r)
+        frontier = nxt
+    return dist
+
+
+@pytest.mark.parametrize("N,C,cycles", [(1, 3, 2), (2, 3, 1), (2, 1, 4)])
+def test_lts_is_exact_for_polynomial_fields(N, C, cycles):
+    """Inviscid homogeneous medium (E = 0) and data q0(x) polynomial of degree
+    N in x: the solution is the terminating Cauchy-Kovalewski series
+    q(x, t) = sum_m (-t)^m / m! A^m q0^(m)(x) (Eq. taylor), of degree N in x.
+    The predictor reproduces it in every element and the Godunov flux of a
+    continuous state is the physical flux, so ADER-DG is exact; with clusters
+    it stays exact only if every face integrates the neighbour's trace over
+    the right sub-interval, the buffers sum the right sub-steps and are reset
+    per cycle (Section "Temporal discretisation with ADER", clustered LTS).
+    The absorbing x faces are not exact; after K ticks their error has reached
+    at most K - 1 face hops, so the elements farther than K hops are checked.
+    Planted mistakes (the larger neighbour's sub-interval mirrored, its trace
+    taken constant in time, a buffer not reset at its level's cycle start)
+    leave errors of 0.25, 0.12 and 34 there (N = 1, two cycles) and fail both
+    clustered cases."""
+    mesh = _graded_slab_mesh()
+    ne = mesh["tets"].shape[0]
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    mats[:, 9] = 0.0  # inviscid
+    m = inputs.material_dict(mats[0])
+    assert not material.source_matrix(m).any()
+    Ax = material.jacobians(m)[0]
+    coef = np.random.default_rng(40 + N).standard_normal((N + 1, 13))  # q0 = sum_d coef_d x^d
+
+    def field(t):
+        def q(x):
+            out = np.zeros((len(x), 13))
+            for mm in range(N + 1):
+                der = sum((factorial(d) / factorial(d - mm)) * x[:, :1] ** (d - mm) * coef[d][None, :]
+                          for d in range(mm, N + 1))
+                out += ((-t) ** mm / factorial(mm)) * der @ np.linalg.matrix_power(Ax, mm).T
+            return out
+        return q
+
+    sim = corrector.LTSSimulation(mesh, mats, N, C)
+    if C == 3:
+        assert np.bincount(sim.cl, minlength=3).min() > 0
+        pairs = {(int(sim.cl[e]), int(sim.cl[r])) for e in range(ne) for r in mesh["neighbors"][e] if r >= 0}
+        assert {(0, 1), (0, 2), (1, 2)} <= pairs
+    vert = mesh["vertices"][mesh["tets"]]
+    ticks = cycles * 2 ** (C - 1)
+    Q1, _ = sim.run(planewave.project(vert, N, field(0.0)), cycles)
+    exact = planewave.project(vert, N, field(ticks * sim.dt_min))
+    keep = _hops_from_boundary(mesh["neighbors"]) > ticks
+    assert set(sim.cl[keep].tolist()) == set(range(C))
+    err = np.abs(Q1[keep] - exact[keep]).max() / np.abs(exact).max()
+    assert err <= 1e-11, err
+    # the boundary error is real (the check is not vacuous)
+    assert np.abs(Q1 - exact).max() / np.abs(exact).max() > 1e-3
