@@ -285,7 +285,7 @@ def _hops_from_boundary(nb):
     return dist
 
 
-@pytest.mark.parametrize("N,C,cycles", [(1, 3, 2), (2, 3, 1), (2, 1, 4)])
+@pytest.mark.parametrize("N,C,cycles", [(1, 3, 2), (2, 3, 1), (3, 3, 1), (4, 3, 1), (2, 1, 4), (5, 1, 1), (6, 1, 1)])
 def test_lts_is_exact_for_polynomial_fields(N, C, cycles):
     """Inviscid homogeneous medium (E = 0) and data q0(x) polynomial of degree
     N in x: the solution is the terminating Cauchy-Kovalewski series
@@ -297,6 +297,8 @@ def test_lts_is_exact_for_polynomial_fields(N, C, cycles):
     per cycle (Section "Temporal discretisation with ADER", clustered LTS).
     The absorbing x faces are not exact; after K ticks their error has reached
     at most K - 1 face hops, so the elements farther than K hops are checked.
+    With C = 1 the test runs GTSSimulation and pins its corrector's volume
+    and face terms at N = 2, 5 and 6 as well.
     Planted mistakes (the larger neighbour's sub-interval mirrored, its trace
     taken constant in time, a buffer not reset at its level's cycle start)
     leave errors of 0.25, 0.12 and 34 there (N = 1, two cycles) and fail both
@@ -320,17 +322,23 @@ def test_lts_is_exact_for_polynomial_fields(N, C, cycles):
             return out
         return q
 
-    sim = corrector.LTSSimulation(mesh, mats, N, C)
-    if C == 3:
+    vert = mesh["vertices"][mesh["tets"]]
+    Q0 = planewave.project(vert, N, field(0.0))
+    if C == 1:  # global time stepping: cycles steps of GTSSimulation
+        sim = corrector.GTSSimulation(mesh, mats, N)
+        ticks, dt = cycles, sim.dt
+        Q1, _ = sim.run(Q0, cycles)
+    else:
+        sim = corrector.LTSSimulation(mesh, mats, N, C)
         assert np.bincount(sim.cl, minlength=3).min() > 0
         pairs = {(int(sim.cl[e]), int(sim.cl[r])) for e in range(ne) for r in mesh["neighbors"][e] if r >= 0}
         assert {(0, 1), (0, 2), (1, 2)} <= pairs
-    vert = mesh["vertices"][mesh["tets"]]
-    ticks = cycles * 2 ** (C - 1)
-    Q1, _ = sim.run(planewave.project(vert, N, field(0.0)), cycles)
-    exact = planewave.project(vert, N, field(ticks * sim.dt_min))
+        ticks, dt = cycles * 2 ** (C - 1), sim.dt_min
+        Q1, _ = sim.run(Q0, cycles)
+    exact = planewave.project(vert, N, field(ticks * dt))
     keep = _hops_from_boundary(mesh["neighbors"]) > ticks
-    assert set(sim.cl[keep].tolist()) == set(range(C))
+    if C > 1:
+        assert set(sim.cl[keep].tolist()) == set(range(C))
     err = np.abs(Q1[keep] - exact[keep]).max() / np.abs(exact).max()
     assert err <= 1e-11, err
     # the boundary error is real (the check is not vacuous)
