@@ -324,22 +324,32 @@ def test_lts_is_exact_for_polynomial_fields(N, C, cycles):
 
     vert = mesh["vertices"][mesh["tets"]]
     Q0 = planewave.project(vert, N, field(0.0))
+    # receivers in a 0.2-, a 0.025- and a 0.1-wide box (clusters 2, 0, 1)
+    rec = [np.array([1.3, 0.37, 0.81]), np.array([1.43, 0.9, 0.15]), np.array([1.5, 0.52, 0.6])]
     if C == 1:  # global time stepping: cycles steps of GTSSimulation
-        sim = corrector.GTSSimulation(mesh, mats, N)
+        sim = corrector.GTSSimulation(mesh, mats, N, receivers=rec)
         ticks, dt = cycles, sim.dt
-        Q1, _ = sim.run(Q0, cycles)
+        Q1, seis = sim.run(Q0, cycles)
+        seis = [(dt * np.arange(1, cycles + 1), seis[i]) for i in range(len(rec))]
     else:
-        sim = corrector.LTSSimulation(mesh, mats, N, C)
+        sim = corrector.LTSSimulation(mesh, mats, N, C, receivers=rec)
         assert np.bincount(sim.cl, minlength=3).min() > 0
         pairs = {(int(sim.cl[e]), int(sim.cl[r])) for e in range(ne) for r in mesh["neighbors"][e] if r >= 0}
         assert {(0, 1), (0, 2), (1, 2)} <= pairs
         ticks, dt = cycles * 2 ** (C - 1), sim.dt_min
-        Q1, _ = sim.run(Q0, cycles)
+        Q1, seis = sim.run(Q0, cycles)
+        # each receiver samples at the end of every step of its element's cluster
+        assert [len(t) for t, _ in seis] == [cycles * 2 ** (C - 1 - sim.cl[e]) for e, _ in sim.rec]
     exact = planewave.project(vert, N, field(ticks * dt))
     keep = _hops_from_boundary(mesh["neighbors"]) > ticks
     if C > 1:
         assert set(sim.cl[keep].tolist()) == set(range(C))
+        assert sorted(int(sim.cl[e]) for e, _ in sim.rec) == [0, 1, 2]
     err = np.abs(Q1[keep] - exact[keep]).max() / np.abs(exact).max()
     assert err <= 1e-11, err
+    for (e, _), x, (times, samples) in zip(sim.rec, rec, seis):
+        assert keep[e]
+        ref = np.stack([field(t)(x[None, :])[0] for t in times])
+        assert np.abs(samples - ref).max() <= 1e-11 * np.abs(exact).max()
     # the boundary error is real (the check is not vacuous)
     assert np.abs(Q1 - exact).max() / np.abs(exact).max() > 1e-3
