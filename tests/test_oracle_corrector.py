@@ -259,6 +259,36 @@ def test_lts_conserves_domain_integrals():
         assert abs(change) <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("cluster", [0, 2])
+def test_lts_source_injects_its_time_integral(cluster):
+    """A point source in an element of cluster 0 or 2 of the graded periodic
+    inviscid mesh, zero initial data: the fluxes telescope, so after two
+    cycles the domain integral of every quantity p is w_p (S(T) - S(0)), S
+    the Ricker antiderivative, whatever steps the source element takes
+    (Section "Temporal discretisation with ADER": each element integrates its
+    source over its own steps; Section "Homogeneous full-space": Ricker
+    point source)."""
+    mesh = _graded_mesh()
+    ne = mesh["tets"].shape[0]
+    mats = np.tile(inputs.REFERENCE_MATERIAL, (ne, 1))
+    mats[:, 9] = 0.0
+    probe = corrector.LTSSimulation(mesh, mats, 2, 3)
+    e = int(np.nonzero(probe.cl == cluster)[0][0])
+    x = mesh["vertices"][mesh["tets"][e]].mean(axis=0)
+    T = 2 * 4 * probe.dt_min
+    w = np.random.default_rng(9).standard_normal(13)
+    src = {"x": x, "w": w, "f0": 1.0 / T, "t0": 0.6 * T}
+    sim = corrector.LTSSimulation(mesh, mats, 2, 3, source=src)
+    assert sim.cl[sim.src[0]] == cluster
+    Q1, _ = sim.run(np.zeros((ne, 13, sim.B)), 2)
+    vol = sim.detJ / 6
+    injected = w * (corrector.ricker_antiderivative(T, src["f0"], src["t0"])
+                    - corrector.ricker_antiderivative(0.0, src["f0"], src["t0"]))
+    total = np.einsum("e,eq->q", vol, Q1[:, :, 0])
+    scale = np.einsum("e,eq->q", vol, np.abs(Q1[:, :, 0]))
+    assert np.all(np.abs(total - injected) <= 1e-12 * scale + 1e-15 * np.abs(injected)), (total, injected)
+    assert abs(injected[0] / w[0]) > 0.05 * T  # the wavelet's integral over the run is not small
+
 def _graded_slab_mesh():
     """Boxes graded in x (absorbing x faces), 3 periodic boxes of 0.4 in y and
     z.  Box widths 0.4 0.4 0.4 0.2 | 0.025 0.025 | 0.1 | 0.2 0.4 0.4 0.4 give
